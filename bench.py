@@ -1,0 +1,523 @@
+#!/usr/bin/env python3
+"""Benchmark of the embedded-gasket hot path on GB300.
+
+Headline (one JSON line on stdout): the lambda-mapped map-and-write pass on a
+level-16 gasket embedded in a 65536 x 65536 uint8 grid (4.3 GB), value = hash
+of (x, y) with seed 1.  A step is one pass over the whole grid; the metric is
+gasket cells written per second (3^16 cells per pass).  The grid (4.3 GB) and
+the sectors one pass touches (181 MB) are both larger than the 129 MB L2, so
+no L2 flush is needed between passes.
+
+Beside the headline the line carries: the roofline of the write kernel
+(touched 128-byte lines per launch / CUDA-event launch time, against the
+measured HBM copy bandwidth), the bounding-box map on the same workload, the
+float32 grid, the level-15 CA and diffusion steps, the end-to-end rate through
+host buffers, SM clocks sampled during the run, and the CPU oracle timed on
+the host cores.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (the only reference this method has)
+on the same workload: each step is one band of 4096 rows of the level-16
+grid, cycling through the 16 bands.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = ("gasket GCells/s and % of HBM peak at n=2^16, λ vs bounding-box; "
+          "served p50/p99 latency")
+UNIT = "GCells/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--rho", type=int, default=None)
+    p.add_argument("--map", default=None)
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the comparison workloads (bbox, f32, stencils)")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return p.parse_args()
+
+
+# --------------------------------------------------------------------------
+# process group (N > 1: independent replicas, one per GPU)
+# --------------------------------------------------------------------------
+class Group:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            backend = "nccl" if _cuda_ok() else "gloo"
+            if backend == "nccl":
+                import torch
+                torch.cuda.set_device(self.local)
+            dist.init_process_group(backend=backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, value: float) -> float:
+        if self.dist is None:
+            return value
+        import torch
+        dev = f"cuda:{self.local}" if _cuda_ok() else "cpu"
+        t = torch.tensor([value], dtype=torch.float64, device=dev)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+
+
+def _cuda_ok() -> bool:
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
+
+
+# --------------------------------------------------------------------------
+# clocks sampled with nvidia-smi while the GPU is busy
+# --------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="sg_clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "50", "-f", self.path],
+                stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+        rows = []
+        if self.path and os.path.exists(self.path):
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) >= 9:
+                        rows.append(parts)
+            os.unlink(self.path)
+        return summarize_clocks(rows)
+
+
+def summarize_clocks(rows):
+    if not rows:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+    sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+    smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    reasons = set()
+    for r in rows:
+        for name, val in zip(names, r[5:9]):
+            if val.lower().startswith("active"):
+                reasons.add(name)
+    power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+    return {"sm_mhz": statistics.median(sm) if sm else None,
+            "sm_max_mhz": max(smax) if smax else None,
+            "reasons": sorted(reasons),
+            "power_w_max": max(power) if power else None,
+            "samples": len(rows)}
+
+
+# --------------------------------------------------------------------------
+# roofline helpers
+# --------------------------------------------------------------------------
+def touched_bytes(r: int, elem: int, granule: int) -> int:
+    """Bytes of the aligned granules (32-byte sectors or 128-byte lines) of the
+    row-major n x n grid that hold at least one gasket cell.  A granule of
+    2^g elements on row y starting at column x0 (a multiple of 2^g) holds one
+    iff (x0 >> g) & (y >> g) == 0, so there are 2^g * 3^(r-g) of them."""
+    per = granule // elem
+    g = per.bit_length() - 1
+    if g >= r:
+        return (1 << r) * (1 << r) * elem if g > r else granule * (1 << r)
+    return (1 << g) * 3 ** (r - g) * granule
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def recorded_traffic(kernel_key: str):
+    """DRAM bytes per launch from the committed ncu summary of this kernel,
+    if the library it was measured on is the library built now."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        from paper_1706_04552_gb300 import build as sg_build
+        entry = d.get(kernel_key)
+        if entry and entry.get("libsg_digest") == sg_build._digest():
+            return entry.get("dram_bytes_per_launch")
+    except Exception:
+        pass
+    return None
+
+
+# --------------------------------------------------------------------------
+# timing on the device
+# --------------------------------------------------------------------------
+def time_launches(fn, steps: int, stream):
+    """Run fn() `steps` times on `stream`; CUDA events around the whole run
+    and around every launch.  Returns (total ms, list of per-launch ms)."""
+    import torch
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(steps)]
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    for a, b in ev:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    t1.record(stream)
+    t1.synchronize()
+    return t0.elapsed_time(t1), [a.elapsed_time(b) for a, b in ev]
+
+
+def soak(fn, seconds: float, stream):
+    """Keep the GPU busy with fn() for about `seconds` (untimed)."""
+    import torch
+    t_end = time.time() + seconds
+    while time.time() < t_end:
+        for _ in range(50):
+            fn()
+        stream.synchronize()
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def run_ours(args, grp: Group):
+    import torch
+    import paper_1706_04552_gb300 as sg
+    from paper_1706_04552_gb300 import workloads
+
+    sg.lib()                                   # fails loudly without libsg.so
+    dev = torch.device("cuda", grp.local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    w = dict(workloads.WRITE_HEADLINE)
+    if args.rho:
+        w["rho"] = args.rho
+    if args.map:
+        w["map"] = args.map
+    r, n = w["r"], 1 << w["r"]
+    cells = 3 ** r
+    grid = torch.zeros(n * n, dtype=torch.uint8, device=dev)
+
+    def step():
+        sg.map_write(grid, r, w["rho"], w["map"], w["value"], w["seed"], stream)
+
+    for _ in range(max(3, args.warmup)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    soak(step, 1.0, stream)                   # clocks settle, sampler sees load
+    grp.barrier()
+    torch.cuda.synchronize(dev)
+    total_ms, per_launch = time_launches(step, args.steps, stream)
+    torch.cuda.synchronize(dev)
+    grp.barrier()
+    clocks = sampler.stop()
+    total_ms = grp.max(total_ms)
+
+    ms_per_step = total_ms / args.steps
+    value = grp.world * cells * args.steps / (total_ms / 1e3) / 1e9
+    launch_ms = statistics.mean(per_launch)
+    peak, peak_kind = measured_peak()
+    line_bytes = touched_bytes(r, 1, 128)
+    sector_bytes = touched_bytes(r, 1, 32)
+    achieved = line_bytes / (launch_ms / 1e3) / 1e9
+    launched, useful = sg.launch_stats(r, w["rho"], w["map"])
+    kernel_key = f"write_{w['map']}_r{r}_u8_rho{w['rho']}"
+    roofline = {
+        "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+        "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+        "traffic": recorded_traffic(kernel_key),
+        "algorithmic_bytes_per_launch": line_bytes,
+        "algorithmic_bytes": "touched 128-byte lines: 2^7 * 3^9 lines of 128 B",
+        "sector_bytes_per_launch": sector_bytes,
+        "achieved_sector_gbs": round(sector_bytes / (launch_ms / 1e3) / 1e9, 1),
+        "launch_ms_mean": round(launch_ms, 5),
+        "launch_ms_min": round(min(per_launch), 5),
+        "kernel": kernel_key,
+    }
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT,
+        "n_gpus": grp.world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms_per_step, 5), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {
+            "workload": (f"map-and-write, level {r} gasket in a {n}x{n} uint8 grid, "
+                         f"hash(x,y) seed {w['seed']}, map {w['map']}, rho {w['rho']}"),
+            "r": r, "n": n, "rho": w["rho"], "map": w["map"], "value": w["value"],
+            "seed": w["seed"], "cells_per_step": cells,
+            "l2": "inputs larger than L2 (4.3 GB grid; 181 MB touched sectors > 129 MB L2)",
+            "parallelism": "replicas" if grp.world > 1 else "single GPU",
+        },
+        "roofline": roofline,
+        "threads": {"launched_slots": launched, "useful_cells": useful},
+        "clocks": clocks,
+        "gpu_launches": args.steps,
+    }
+
+    if grp.rank == 0 and not args.no_extras:
+        out["compare"] = compare_workloads(sg, torch, dev, stream, w, grid, launch_ms)
+    del grid
+    torch.cuda.empty_cache()
+    out["e2e"] = measure_e2e(sg, torch, dev, stream, w, grp, min(args.steps, 4))
+    if grp.rank == 0 and grp.world == 1 and not args.no_cpu:
+        out["cpu_baseline"] = cpu_baseline(w)
+    return out
+
+
+def _rate(cells, ms):
+    return round(cells / (ms / 1e3) / 1e9, 3)
+
+
+def compare_workloads(sg, torch, dev, stream, w, grid_u8, headline_launch_ms):
+    """Short timings of the other configurations on the same GPU."""
+    from paper_1706_04552_gb300 import inputs, workloads
+    r, n = w["r"], 1 << w["r"]
+    cells = 3 ** r
+    res = {}
+    # the bounding-box map on the same uint8 grid, at its own best rho
+    for name, mapk, rho, steps in (("bbox_u8", "bbox", w["bbox_rho"], 20),
+                                   ("lambda_subbox_u8", "lambda", w["rho"], 200)):
+        f = lambda: sg.map_write(grid_u8, r, rho, mapk, "hash", w["seed"], stream)
+        for _ in range(3):
+            f()
+        ms, per = time_launches(f, steps, stream)
+        res[name] = {"map": mapk, "rho": rho, "GCells_s": _rate(cells, ms / steps),
+                     "launch_ms": round(statistics.mean(per), 5)}
+    res["speedup_lambda_over_bbox"] = round(res["bbox_u8"]["launch_ms"] / headline_launch_ms, 3)
+    # float32 grid (17.2 GB)
+    g32 = torch.zeros(n * n, dtype=torch.float32, device=dev)
+    f = lambda: sg.map_write(g32, r, w["rho"], w["map"], "hash", w["seed"], stream)
+    for _ in range(3):
+        f()
+    ms, per = time_launches(f, 100, stream)
+    lb = touched_bytes(r, 4, 128)
+    res["lambda_f32"] = {"map": w["map"], "rho": w["rho"], "GCells_s": _rate(cells, ms / 100),
+                         "launch_ms": round(statistics.mean(per), 5),
+                         "line_GBps": round(lb / (statistics.mean(per) / 1e3) / 1e9, 1)}
+    del g32
+    torch.cuda.empty_cache()
+    # stencils at level 15
+    s = workloads.STENCILS
+    rs = max(s["levels"])
+    ns, cs = 1 << rs, 3 ** rs
+    idx, vals = inputs.ca_seed_sparse(rs, s["ca_p"], s["ca_seed"])
+    tidx = torch.from_numpy(idx).to(dev)
+    for mapk, rho in (("lambda", s["ca_rho"]), ("bbox", s["bbox_ca_rho"])):
+        a = torch.zeros(ns * ns, dtype=torch.uint8, device=dev)
+        a[tidx] = torch.from_numpy(vals).to(dev)
+        b = torch.zeros_like(a)
+        bufs = [a, b]
+
+        def ca():
+            sg.ca_step(bufs[0], bufs[1], rs, rho, mapk, stream)
+            bufs.reverse()
+        for _ in range(4):
+            ca()
+        steps = s["ca_steps"] if mapk == "lambda" else 32
+        ms, per = time_launches(ca, steps, stream)
+        lb = 2 * touched_bytes(rs, 1, 128)
+        res[f"ca_r{rs}_{mapk}"] = {"rho": rho, "steps": steps,
+                                   "GCells_s": _rate(cs, ms / steps),
+                                   "launch_ms": round(statistics.mean(per), 5),
+                                   "line_GBps": round(lb / (statistics.mean(per) / 1e3) / 1e9, 1)}
+        del a, b, bufs
+    idx, vals = inputs.uniform_sparse(rs, s["diff_seed"])
+    for mapk, rho in (("lambda", s["diff_rho"]), ("bbox", s["bbox_diff_rho"])):
+        a = torch.zeros(ns * ns, dtype=torch.float32, device=dev)
+        a[tidx] = torch.from_numpy(vals).to(dev)
+        b = torch.zeros_like(a)
+        bufs = [a, b]
+
+        def df():
+            sg.diffuse_step(bufs[0], bufs[1], rs, rho, s["alpha"], mapk, stream)
+            bufs.reverse()
+        for _ in range(4):
+            df()
+        steps = s["diff_steps"] if mapk == "lambda" else 20
+        ms, per = time_launches(df, steps, stream)
+        lb = 2 * touched_bytes(rs, 4, 128)
+        res[f"diffusion_r{rs}_{mapk}"] = {"rho": rho, "steps": steps,
+                                          "GCells_s": _rate(cs, ms / steps),
+                                          "launch_ms": round(statistics.mean(per), 5),
+                                          "line_GBps": round(lb / (statistics.mean(per) / 1e3) / 1e9, 1)}
+        del a, b, bufs
+    torch.cuda.empty_cache()
+    return res
+
+
+def measure_e2e(sg, torch, dev, stream, w, grp, steps):
+    """The same metric through the public API with the grid in pinned host
+    memory: every step copies the grid in, runs the pass and copies it out."""
+    r, n = w["r"], 1 << w["r"]
+    host = torch.zeros(n * n, dtype=torch.uint8, pin_memory=True)
+    dgrid = torch.empty(n * n, dtype=torch.uint8, device=dev)
+
+    def step():
+        sg.map_write_host(host, dgrid, r, w["rho"], w["map"], w["value"], w["seed"], stream)
+
+    step()
+    torch.cuda.synchronize(dev)
+    grp.barrier()
+    ms, _ = time_launches(step, steps, stream)
+    ms = grp.max(ms)
+    nbytes = n * n
+    del host, dgrid
+    return {"value": round(grp.world * 3 ** r * steps / (ms / 1e3) / 1e9, 4), "unit": UNIT,
+            "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
+            "steps": steps, "ms_per_step": round(ms / steps, 3)}
+
+
+def cpu_baseline(w):
+    """The CPU oracle, as it stands, on the whole level-16 uint8 grid: one
+    single-threaded brute-force pass (about 10 s)."""
+    import numpy as np
+    import oracle
+    r, n = w["r"], 1 << w["r"]
+    grid = np.zeros((n, n), dtype=np.uint8)
+    t0 = time.perf_counter()
+    oracle.map_write(r, grid, oracle.VAL_HASH, w["seed"])
+    dt = time.perf_counter() - t0
+    return {"value": round(3 ** r / dt / 1e9, 6), "unit": UNIT, "cores": 1,
+            "kind": "oracle", "seconds": round(dt, 3),
+            "sample": f"whole level-{r} uint8 grid ({n}x{n}), one pass, hash seed {w['seed']}",
+            "host": _host_desc()}
+
+
+def _host_desc():
+    try:
+        import platform
+        return f"{platform.machine()}, {os.cpu_count()} cores"
+    except Exception:
+        return None
+
+
+# --------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# --------------------------------------------------------------------------
+def band_cells(r: int, y0: int, y1: int) -> int:
+    # row y of the level-r gasket holds the 2^(r - popcount(y)) subsets of ~y
+    return sum(1 << (r - bin(y).count("1")) for y in range(y0, y1))
+
+
+def run_reference(args, grp: Group):
+    import numpy as np
+    import oracle
+    from paper_1706_04552_gb300 import workloads
+    w = workloads.WRITE_HEADLINE
+    r, n = w["r"], 1 << w["r"]
+    band = 4096
+    buf = np.zeros((band, n), dtype=np.uint8)
+    nb = n // band
+
+    def step(i):
+        y0 = (i % nb) * band
+        oracle.map_write(r, buf, oracle.VAL_HASH, w["seed"], y0=y0, y1=y0 + band)
+        return band_cells(r, y0, y0 + band)
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    cells = 0
+    for i in range(args.steps):
+        cells += step(args.warmup + i)
+    dt = time.perf_counter() - t0
+    value = cells / dt / 1e9
+    sample = (f"{args.steps} bands of {band} rows of the level-{r} uint8 grid "
+              f"({n} columns), hash seed {w['seed']}, single thread")
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT,
+        "n_gpus": grp.world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(dt / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": (f"map-and-write, level {r} gasket in a {n}x{n} uint8 grid, "
+                                f"hash(x,y) seed {w['seed']} (CPU oracle, row bands)"),
+                   "r": r, "n": n, "cells_per_step_mean": cells / args.steps},
+        "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": 1,
+                         "kind": "oracle", "sample": sample, "host": _host_desc()},
+        "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        rank = int(os.environ.get("RANK", "0"))
+        if rank != 0:
+            return 0
+        grp = Group.__new__(Group)
+        grp.world, grp.rank, grp.local, grp.dist = int(os.environ.get("WORLD_SIZE", "1")), 0, 0, None
+        print(json.dumps(run_reference(args, grp)))
+        return 0
+    grp = Group()
+    try:
+        out = run_ours(args, grp)
+        if grp.rank == 0:
+            print(json.dumps(out))
+    finally:
+        grp.close()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,184 @@
+/*
+ * sg.h -- C ABI of libsg, the GB300 (sm_103a) hot path for embedded
+ * Sierpinski-gasket domains.
+ *
+ * Method: C. A. Navarro, B. Bustos, R. Vega, N. Hitschfeld, "Block-space GPU
+ * Mapping for Embedded Sierpinski Gasket Fractals", arXiv:1706.04552.
+ *
+ * Domain.  Level r (0 <= r <= 16), side n = 2^r.  A grid is a dense
+ * row-major n x n array in device memory, pitch n elements: cell (x, y)
+ * (column x, row y) lives at index y*n + x.  The gasket G_r is the set of
+ * cells with (x & y) == 0; it has 3^r cells (Section III-A).  The paper draws
+ * the same set mirrored vertically (x & (n-1-y) == 0, Section III-D).
+ *
+ * Block space.  A tile ("block" in the paper) is a rho x rho square of cells,
+ * rho = 2^s, 1 <= rho <= 64, rho <= n.  The tiles form an n_b x n_b box,
+ * n_b = n / rho; exactly 3^(r-s) of them hold gasket cells, and each of those
+ * holds the level-s gasket (3^s cells).
+ *
+ * Maps (how parallel work is assigned to tiles and cells):
+ *   SG_MAP_LAMBDA         the paper's lambda(omega) (Theorem 1): a parallel
+ *                         space of 3^(r-s) tiles, each decoded to its block
+ *                         coordinate with a warp reduction over the base-3
+ *                         digits of omega; inside a tile every slot is
+ *                         visited and tested (bounding sub-box, Section
+ *                         III-D, the variant the paper measured).
+ *   SG_MAP_BBOX           bounding box: the identity map over all n_b^2
+ *                         tiles, every cell tests membership (Section I).
+ *   SG_MAP_LAMBDA_LUT     lambda for tiles; inside a tile only the 3^s member
+ *                         slots are visited, in row-major order, through an
+ *                         offset table shared by the block (Section III-D,
+ *                         Shared Lookup Table).  Write pass only.
+ *   SG_MAP_LAMBDA_UNROLL  lambda for tiles; inside a tile each thread applies
+ *                         lambda again to its own index (Section III-D,
+ *                         Further Unrolling).  Write pass only.
+ *
+ * Conventions for every call:
+ *   - Ownership: the caller owns all memory.  libsg never allocates, frees or
+ *     keeps a pointer after the call returns.
+ *   - Streams: `stream` is a cudaStream_t (NULL = the legacy default stream).
+ *     Kernel calls are asynchronous on it and never synchronise the host.
+ *   - Errors: arguments are checked on the host before any launch; a bad
+ *     argument returns SG_EINVAL and launches nothing.  A failed launch
+ *     returns SG_ECUDA (the CUDA error text is available from
+ *     sg_last_error_string()).  Nothing is thrown and nothing exits.
+ *   - Device: the current CUDA device of the calling thread.
+ *   - Thread safety: calls may be made from several host threads at once.
+ */
+#ifndef SG_H
+#define SG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SG_ABI_VERSION 1
+
+/* Exported from libsg.so (the library is built with hidden visibility). */
+#if defined(__GNUC__)
+#define SG_API __attribute__((visibility("default")))
+#else
+#define SG_API
+#endif
+
+typedef enum {
+    SG_OK = 0,
+    SG_EINVAL = 1,        /* an argument is out of range, null or misaligned */
+    SG_ECUDA = 2,         /* the CUDA runtime reported an error */
+    SG_ENOMEM = 3,        /* reserved: libsg itself never allocates */
+    SG_ETIMEOUT = 4,      /* a bounded device-side wait gave up */
+    SG_EUNSUPPORTED = 5   /* valid arguments, combination not provided */
+} sg_status;
+
+typedef enum { SG_U8 = 0, SG_F32 = 1 } sg_dtype;
+
+typedef enum {
+    SG_MAP_LAMBDA = 0,
+    SG_MAP_BBOX = 1,
+    SG_MAP_LAMBDA_LUT = 2,
+    SG_MAP_LAMBDA_UNROLL = 3
+} sg_map;
+
+typedef enum {
+    SG_VAL_CONST = 0,     /* u8: low 8 bits of value_or_seed; f32: low 32 bits
+                             reinterpreted as an IEEE float */
+    SG_VAL_LINEAR31 = 1,  /* (x*31 + y) & 0xFF (as float for f32) */
+    SG_VAL_HASH = 2       /* h = SplitMix64 output for state
+                             (seed * 0x9E3779B97F4A7C15) XOR (y*n + x);
+                             u8: h >> 56; f32: (h >> 40) * 2^-24 */
+} sg_value_kind;
+
+/*
+ * sg_map_write -- the map-and-write pass (Section IV): every gasket cell of
+ * the level-r grid receives v(x, y); every other cell keeps its content.
+ *
+ *   r              level, 0..16
+ *   rho            tile side, a power of two in 1..64, rho <= 2^r
+ *   map            any sg_map
+ *   dtype          element type of `grid` (1 or 4 bytes)
+ *   grid           device pointer to n*n elements (f32: 4-byte aligned)
+ *   value_kind     how v(x, y) is formed (see sg_value_kind)
+ *   value_or_seed  the constant, or the hash seed
+ *   stream         cudaStream_t
+ * Launches one kernel.  Returns SG_OK, SG_EINVAL or SG_ECUDA.
+ */
+SG_API sg_status sg_map_write(int r, int rho, sg_map map, sg_dtype dtype, void *grid,
+                       sg_value_kind value_kind, uint64_t value_or_seed,
+                       void *stream);
+
+/*
+ * sg_ca_step -- one step of the Life-like B3/S23 automaton restricted to the
+ * gasket (the nearest-neighbour simulations that motivate the embedded
+ * layout, Section I): a gasket cell is alive next iff exactly 3 of its 8
+ * in-grid gasket neighbours are alive, or it is alive and exactly 2 are.
+ * The grid border does not wrap.
+ *
+ *   in, out  device pointers to n*n uint8 states, 16-byte aligned, distinct
+ *            and not overlapping.  Precondition: `in` holds 0 or 1 on gasket
+ *            cells and 0 off the gasket; `out` holds 0 off the gasket.
+ *            Postcondition: `out` holds the next state on every gasket cell
+ *            and 0 off the gasket (so in/out can be swapped and stepped
+ *            again).  Buffers zero-filled once satisfy both conditions.
+ *   map      SG_MAP_LAMBDA or SG_MAP_BBOX (others: SG_EUNSUPPORTED)
+ * Each tile is staged in shared memory with its halo; tiles are written
+ * whole (off-gasket cells inside a non-empty tile are written as 0).
+ * Launches one kernel.
+ */
+SG_API sg_status sg_ca_step(int r, int rho, sg_map map, const uint8_t *in,
+                     uint8_t *out, void *stream);
+
+/*
+ * sg_diffuse_step -- one explicit FP32 diffusion step on the gasket's
+ * 4-neighbour graph: for a gasket cell with in-grid gasket 4-neighbours N,
+ * u' = u + alpha * (sum_{j in N} u_j - |N| * u).  Off-gasket cells stay 0.
+ * (The paper names nearest-neighbour simulations in general, Section I; the
+ * update rule is the one stated for this library.)
+ *
+ *   in, out  device pointers to n*n floats, 16-byte aligned, distinct.
+ *            Precondition: `in` is 0 off the gasket and `out` is 0 off the
+ *            gasket; postcondition as for sg_ca_step.
+ *   alpha    step weight; the update is a convex combination for
+ *            0 <= alpha <= 0.25.  Any finite value is accepted.
+ *   map      SG_MAP_LAMBDA or SG_MAP_BBOX
+ * Launches one kernel.
+ */
+SG_API sg_status sg_diffuse_step(int r, int rho, sg_map map, const float *in,
+                          float *out, float alpha, void *stream);
+
+/*
+ * sg_block_map -- the lambda block decode on its own (Theorem 1: Eq. beta,
+ * Eq. Delta, Eq. tau, Eq. lambda), for checking the map bit for bit.
+ * For every launch index q in [0, 3^rb): omega = (q mod 3^floor(rb/2),
+ * q div 3^floor(rb/2)); (bx[q], by[q]) = (lambda_x(omega),
+ * 2^rb - 1 - lambda_y(omega)), i.e. the paper's lambda mirrored into the
+ * (x & y) == 0 orientation.  bx, by: device arrays of 3^rb uint32.
+ * rb: 0..16.  Launches one kernel.
+ */
+SG_API sg_status sg_block_map(int rb, uint32_t *bx, uint32_t *by, void *stream);
+
+/*
+ * sg_launch_stats -- host-only accounting of one pass (Lemma 1, Theorem 2):
+ * `launched` = cell slots the map's threads examine (lambda sub-box:
+ * 3^(r-s) * rho^2; bounding box: n^2; lookup table / unrolling: 3^r),
+ * `useful` = gasket cells = 3^r.  No GPU work.  Either pointer may be NULL.
+ */
+SG_API sg_status sg_launch_stats(int r, int rho, sg_map map, uint64_t *launched,
+                          uint64_t *useful);
+
+/* Human-readable name of a status code (static storage). */
+SG_API const char *sg_status_str(sg_status status);
+
+/* Text of the last CUDA error seen by a libsg call on this host thread
+ * ("" if none).  Static thread-local storage, valid until the next call. */
+SG_API const char *sg_last_error_string(void);
+
+/* SG_ABI_VERSION of the loaded library. */
+SG_API int sg_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SG_H */

@@ -90,6 +90,8 @@ def _load():
         lib.or_diffuse_step_region.argtypes = [i32, i64, i64, i64, i64, vp, vp,
                                                ctypes.c_double]
         lib.or_diffuse_step_region.restype = None
+        lib.or_write_expected_at.argtypes = [i32, i32, i32, u64, u64, vp, vp, vp, vp]
+        lib.or_write_expected_at.restype = None
         _lib = lib
         return lib
 
@@ -191,6 +193,20 @@ def map_write(r: int, grid: np.ndarray, value_kind: int, value: int,
     _load().or_map_write_rows(r, dt, _ptr(grid), y0, y1, value_kind,
                               value & (2**64 - 1))
     return grid
+
+
+def write_expected_at(r: int, dtype, value_kind: int, value: int, xs, ys,
+                      before) -> np.ndarray:
+    """Content of the listed cells after the write pass: v(x, y) at gasket
+    cells, ``before`` elsewhere (one value per listed cell)."""
+    xs = np.ascontiguousarray(xs, dtype=np.uint64)
+    ys = np.ascontiguousarray(ys, dtype=np.uint64)
+    before = np.ascontiguousarray(before, dtype=dtype)
+    out = np.empty(len(xs), dtype=dtype)
+    dt = U8 if np.dtype(dtype) == np.uint8 else F32
+    _load().or_write_expected_at(r, dt, value_kind, value & (2**64 - 1), len(xs),
+                                 _ptr(xs), _ptr(ys), _ptr(before), _ptr(out))
+    return out
 
 
 # --------------------------------------------------------------------------

@@ -332,3 +332,21 @@ void or_diffuse_step_region(int r, int64_t x0, int64_t y0, int64_t w, int64_t h,
             out[j * w + i] = next;
         }
 }
+
+/* Expected content of listed cells after the map-and-write pass, for
+ * checking a full-size grid at sampled cells: v(x, y) at gasket cells, the
+ * cell's previous content (passed in `before`) elsewhere. */
+void or_write_expected_at(int r, int dtype, int vk, uint64_t vs, uint64_t count,
+                          const uint64_t *xs, const uint64_t *ys,
+                          const void *before, void *out)
+{
+    for (uint64_t i = 0; i < count; ++i) {
+        uint64_t x = xs[i], y = ys[i];
+        if (dtype == OR_U8)
+            ((uint8_t *)out)[i] = or_member(x, y) ? value_u8(r, x, y, vk, vs)
+                                                  : ((const uint8_t *)before)[i];
+        else
+            ((float *)out)[i] = or_member(x, y) ? value_f32(r, x, y, vk, vs)
+                                                : ((const float *)before)[i];
+    }
+}

@@ -1,0 +1,225 @@
+"""paper_1706_04552_gb300 -- GB300 (sm_103a) block-space mapping for embedded
+Sierpinski gaskets (Navarro, Bustos, Vega, Hitschfeld, arXiv:1706.04552).
+
+Python binding over libsg.so (C ABI in include/sg.h).  The binding only
+marshals arguments: every step of the hot path runs in the library's CUDA
+kernels, and there is no CPU fallback -- if libsg.so is missing or cannot be
+loaded, every call raises.
+
+Two layers:
+  * ``sg_map_write``, ``sg_ca_step``, ``sg_diffuse_step``, ``sg_block_map``,
+    ``sg_launch_stats``: the C functions with the C names, taking raw
+    pointers (ints) and a raw cudaStream_t (int, 0 = legacy default stream);
+  * ``map_write``, ``ca_step``, ``diffuse_step``, ``block_map``: the same
+    calls on torch tensors, checking device, dtype, shape and contiguity and
+    launching on the current torch stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+__all__ = [
+    "SGError", "lib", "lib_path",
+    "sg_map_write", "sg_ca_step", "sg_diffuse_step", "sg_block_map",
+    "sg_launch_stats", "sg_status_str", "sg_abi_version",
+    "map_write", "map_write_host", "ca_step", "diffuse_step", "block_map", "launch_stats",
+    "MAPS", "DTYPES", "VALUES",
+]
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "_build", "libsg.so")
+
+SG_OK, SG_EINVAL, SG_ECUDA, SG_ENOMEM, SG_ETIMEOUT, SG_EUNSUPPORTED = range(6)
+MAPS = {"lambda": 0, "bbox": 1, "lambda_lut": 2, "lambda_unroll": 3}
+DTYPES = {"u8": 0, "f32": 1}
+VALUES = {"const": 0, "linear31": 1, "hash": 2}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SGError(RuntimeError):
+    def __init__(self, fn: str, status: int, detail: str = ""):
+        self.status = status
+        msg = f"{fn} failed: {sg_status_str(status)}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+def lib_path() -> str:
+    return os.environ.get("SG_LIB", _LIB_PATH)
+
+
+def lib() -> ctypes.CDLL:
+    """Load libsg.so (built in-tree by ``paper_1706_04552_gb300.build``)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = lib_path()
+        if not os.path.exists(path):
+            raise ImportError(
+                f"libsg.so not found at {path}: build it with "
+                "`python -m paper_1706_04552_gb300.build` (there is no CPU fallback)")
+        L = ctypes.CDLL(path)
+        i32, u64, vp = ctypes.c_int, ctypes.c_uint64, ctypes.c_void_p
+        p_u64 = ctypes.POINTER(ctypes.c_uint64)
+        L.sg_map_write.argtypes = [i32, i32, i32, i32, vp, i32, u64, vp]
+        L.sg_map_write.restype = i32
+        L.sg_ca_step.argtypes = [i32, i32, i32, vp, vp, vp]
+        L.sg_ca_step.restype = i32
+        L.sg_diffuse_step.argtypes = [i32, i32, i32, vp, vp, ctypes.c_float, vp]
+        L.sg_diffuse_step.restype = i32
+        L.sg_block_map.argtypes = [i32, vp, vp, vp]
+        L.sg_block_map.restype = i32
+        L.sg_launch_stats.argtypes = [i32, i32, i32, p_u64, p_u64]
+        L.sg_launch_stats.restype = i32
+        L.sg_status_str.argtypes = [i32]
+        L.sg_status_str.restype = ctypes.c_char_p
+        L.sg_last_error_string.argtypes = []
+        L.sg_last_error_string.restype = ctypes.c_char_p
+        L.sg_abi_version.argtypes = []
+        L.sg_abi_version.restype = i32
+        _lib = L
+        return L
+
+
+# ---------------------------------------------------------------- raw C layer
+
+def sg_status_str(status: int) -> str:
+    return lib().sg_status_str(int(status)).decode()
+
+
+def sg_abi_version() -> int:
+    return int(lib().sg_abi_version())
+
+
+def _check(fn: str, status: int) -> None:
+    if status != SG_OK:
+        detail = lib().sg_last_error_string().decode() if status == SG_ECUDA else ""
+        raise SGError(fn, status, detail)
+
+
+def sg_map_write(r, rho, map_kind, dtype, grid_ptr, value_kind, value_or_seed,
+                 stream=0) -> int:
+    return int(lib().sg_map_write(r, rho, map_kind, dtype, grid_ptr, value_kind,
+                                  value_or_seed & (2**64 - 1), stream))
+
+
+def sg_ca_step(r, rho, map_kind, in_ptr, out_ptr, stream=0) -> int:
+    return int(lib().sg_ca_step(r, rho, map_kind, in_ptr, out_ptr, stream))
+
+
+def sg_diffuse_step(r, rho, map_kind, in_ptr, out_ptr, alpha, stream=0) -> int:
+    return int(lib().sg_diffuse_step(r, rho, map_kind, in_ptr, out_ptr, alpha, stream))
+
+
+def sg_block_map(rb, bx_ptr, by_ptr, stream=0) -> int:
+    return int(lib().sg_block_map(rb, bx_ptr, by_ptr, stream))
+
+
+def sg_launch_stats(r, rho, map_kind):
+    a, b = ctypes.c_uint64(), ctypes.c_uint64()
+    st = int(lib().sg_launch_stats(r, rho, map_kind, ctypes.byref(a), ctypes.byref(b)))
+    return st, a.value, b.value
+
+
+# ------------------------------------------------------------- tensor layer
+
+def _map_id(m) -> int:
+    return MAPS[m] if isinstance(m, str) else int(m)
+
+
+def _stream_handle(t, stream):
+    import torch
+    if stream is None:
+        return torch.cuda.current_stream(t.device).cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _grid_check(t, r, dtypes, name):
+    import torch
+    n = 1 << r
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name}: expected a CUDA tensor (there is no CPU path)")
+    if t.dtype not in dtypes:
+        raise TypeError(f"{name}: dtype {t.dtype} not in {dtypes}")
+    if not t.is_contiguous() or t.numel() != n * n:
+        raise ValueError(f"{name}: expected a contiguous tensor of {n}*{n} elements")
+
+
+def map_write(grid, r: int, rho: int, map="lambda", value="hash", value_or_seed=1,
+              stream=None):
+    """Map-and-write pass on a CUDA tensor (uint8 or float32, n*n elements)."""
+    import torch
+    _grid_check(grid, r, (torch.uint8, torch.float32), "grid")
+    dt = DTYPES["u8"] if grid.dtype == torch.uint8 else DTYPES["f32"]
+    vk = VALUES[value] if isinstance(value, str) else int(value)
+    with torch.cuda.device(grid.device):
+        _check("sg_map_write", sg_map_write(r, rho, _map_id(map), dt, grid.data_ptr(), vk,
+                                            value_or_seed, _stream_handle(grid, stream)))
+    return grid
+
+
+def map_write_host(host_grid, dev_grid, r: int, rho: int, map="lambda", value="hash",
+                   value_or_seed=1, stream=None):
+    """Write pass on a grid that lives in host memory: copies ``host_grid``
+    (a pinned CPU tensor) into the caller's device buffer ``dev_grid``,
+    launches the pass, and copies the result back, all on one stream.
+    Returns without synchronising; the copy back is complete once the stream
+    is."""
+    import torch
+    if host_grid.is_cuda or not host_grid.is_contiguous():
+        raise TypeError("host_grid: expected a contiguous CPU tensor")
+    if host_grid.dtype != dev_grid.dtype or host_grid.numel() != dev_grid.numel():
+        raise ValueError("host_grid and dev_grid must match in dtype and size")
+    st = stream if stream is not None else torch.cuda.current_stream(dev_grid.device)
+    with torch.cuda.stream(st):
+        dev_grid.copy_(host_grid, non_blocking=True)
+        map_write(dev_grid, r, rho, map, value, value_or_seed, st)
+        host_grid.copy_(dev_grid, non_blocking=True)
+    return host_grid
+
+
+def ca_step(inp, out, r: int, rho: int, map="lambda", stream=None):
+    import torch
+    _grid_check(inp, r, (torch.uint8,), "in")
+    _grid_check(out, r, (torch.uint8,), "out")
+    with torch.cuda.device(inp.device):
+        _check("sg_ca_step", sg_ca_step(r, rho, _map_id(map), inp.data_ptr(),
+                                        out.data_ptr(), _stream_handle(inp, stream)))
+    return out
+
+
+def diffuse_step(inp, out, r: int, rho: int, alpha: float = 0.2, map="lambda",
+                 stream=None):
+    import torch
+    _grid_check(inp, r, (torch.float32,), "in")
+    _grid_check(out, r, (torch.float32,), "out")
+    with torch.cuda.device(inp.device):
+        _check("sg_diffuse_step", sg_diffuse_step(r, rho, _map_id(map), inp.data_ptr(),
+                                                  out.data_ptr(), float(alpha),
+                                                  _stream_handle(inp, stream)))
+    return out
+
+
+def block_map(rb: int, device="cuda", stream=None):
+    """Run the device lambda decode for every launch index; returns (bx, by)
+    as uint32-valued int32 CUDA tensors (bit patterns, all values < 2^16)."""
+    import torch
+    total = 3 ** rb
+    bx = torch.empty(total, dtype=torch.int32, device=device)
+    by = torch.empty(total, dtype=torch.int32, device=device)
+    with torch.cuda.device(bx.device):
+        _check("sg_block_map", sg_block_map(rb, bx.data_ptr(), by.data_ptr(),
+                                            _stream_handle(bx, stream)))
+    return bx, by
+
+
+def launch_stats(r: int, rho: int, map="lambda"):
+    st, launched, useful = sg_launch_stats(r, rho, _map_id(map))
+    _check("sg_launch_stats", st)
+    return launched, useful

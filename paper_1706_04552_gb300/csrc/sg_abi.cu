@@ -1,0 +1,202 @@
+// sg_abi.cu -- the extern "C" surface of libsg (declared in include/sg.h):
+// host-side argument checks, dispatch to the kernels, the standalone lambda
+// block-map kernel and the host-only launch accounting.
+#include <atomic>
+#include <cstdio>
+#include <cstring>
+
+#include "sg.h"
+#include "sg_device.cuh"
+#include "sg_internal.h"
+
+namespace sg {
+
+namespace {
+thread_local char g_last_error[256] = "";
+
+constexpr int kMaxDevices = 64;
+std::atomic<int> g_sm_count[kMaxDevices];
+
+sg_status fail_cuda(cudaError_t e)
+{
+    std::snprintf(g_last_error, sizeof g_last_error, "%s: %s", cudaGetErrorName(e),
+                  cudaGetErrorString(e));
+    return SG_ECUDA;
+}
+
+bool is_pow2(int v) { return v > 0 && (v & (v - 1)) == 0; }
+
+int log2i(int v)
+{
+    int s = 0;
+    while ((1 << s) < v) ++s;
+    return s;
+}
+
+// Common checks of level and tile side; on success *s = log2(rho).
+bool valid_level_tile(int r, int rho, int *s)
+{
+    if (r < 0 || r > 16) return false;
+    if (!is_pow2(rho) || rho > 64) return false;
+    if (rho > (1 << r)) return false;
+    *s = log2i(rho);
+    return true;
+}
+
+bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
+
+// One warp per launch index; lane results of the reduction are identical,
+// lane 0 stores them.
+__global__ void __launch_bounds__(256)
+block_map_kernel(uint32_t *__restrict__ bx, uint32_t *__restrict__ by, int rb,
+                 uint32_t total, uint32_t W)
+{
+    const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
+    LambdaLane ll;
+    ll.init(threadIdx.x & 31, rb);
+    OmegaWalker ow;
+    ow.init(warp, nwarps, W);
+    for (uint32_t q = warp; q < total; q += nwarps) {
+        const uint2 b = ll.decode(ow.wx, ow.wy);
+        ow.advance();
+        if ((threadIdx.x & 31) == 0) {
+            bx[q] = b.x;
+            by[q] = b.y;
+        }
+    }
+}
+}  // namespace
+
+int sm_count(int *err)
+{
+    *err = 0;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) { *err = (int)e; return 0; }
+    if (dev >= 0 && dev < kMaxDevices) {
+        int c = g_sm_count[dev].load(std::memory_order_relaxed);
+        if (c > 0) return c;
+    }
+    int c = 0;
+    e = cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) { *err = (int)e; return 0; }
+    if (dev >= 0 && dev < kMaxDevices) g_sm_count[dev].store(c, std::memory_order_relaxed);
+    return c;
+}
+
+cudaError_t launch_block_map(int rb, uint32_t *bx, uint32_t *by, cudaStream_t st)
+{
+    const uint32_t total = (uint32_t)pow3i(rb);
+    const uint32_t W = (uint32_t)pow3i(rb / 2);
+    LaunchCfg cfg;
+    unsigned grid = 1;
+    cudaError_t e = persistent_grid(block_map_kernel, 256, 0, (total + 7) / 8, cfg, &grid);
+    if (e != cudaSuccess) return e;
+    block_map_kernel<<<grid, 256, 0, st>>>(bx, by, rb, total, W);
+    return cudaGetLastError();
+}
+
+}  // namespace sg
+
+using namespace sg;
+
+extern "C" {
+
+int sg_abi_version(void) { return SG_ABI_VERSION; }
+
+const char *sg_status_str(sg_status s)
+{
+    switch (s) {
+    case SG_OK: return "SG_OK";
+    case SG_EINVAL: return "SG_EINVAL: invalid argument";
+    case SG_ECUDA: return "SG_ECUDA: CUDA runtime error";
+    case SG_ENOMEM: return "SG_ENOMEM: out of memory";
+    case SG_ETIMEOUT: return "SG_ETIMEOUT: a bounded device wait gave up";
+    case SG_EUNSUPPORTED: return "SG_EUNSUPPORTED: combination not provided";
+    default: return "unknown sg_status";
+    }
+}
+
+const char *sg_last_error_string(void) { return g_last_error; }
+
+sg_status sg_map_write(int r, int rho, sg_map map, sg_dtype dtype, void *grid,
+                       sg_value_kind value_kind, uint64_t value_or_seed, void *stream)
+{
+    int s = 0;
+    if (!valid_level_tile(r, rho, &s)) return SG_EINVAL;
+    if (map < SG_MAP_LAMBDA || map > SG_MAP_LAMBDA_UNROLL) return SG_EINVAL;
+    if (value_kind < SG_VAL_CONST || value_kind > SG_VAL_HASH) return SG_EINVAL;
+    if (grid == nullptr) return SG_EINVAL;
+    LaunchCfg cfg;
+    cudaError_t e;
+    if (dtype == SG_U8) {
+        e = launch_write_u8(r, s, (int)map, (int)value_kind, (uint8_t *)grid, value_or_seed,
+                            (cudaStream_t)stream, cfg);
+    } else if (dtype == SG_F32) {
+        if (!aligned(grid, 4)) return SG_EINVAL;
+        e = launch_write_f32(r, s, (int)map, (int)value_kind, (float *)grid, value_or_seed,
+                             (cudaStream_t)stream, cfg);
+    } else {
+        return SG_EINVAL;
+    }
+    return e == cudaSuccess ? SG_OK : fail_cuda(e);
+}
+
+sg_status sg_ca_step(int r, int rho, sg_map map, const uint8_t *in, uint8_t *out,
+                     void *stream)
+{
+    int s = 0;
+    if (!valid_level_tile(r, rho, &s)) return SG_EINVAL;
+    if (map < SG_MAP_LAMBDA || map > SG_MAP_LAMBDA_UNROLL) return SG_EINVAL;
+    if (map != SG_MAP_LAMBDA && map != SG_MAP_BBOX) return SG_EUNSUPPORTED;
+    if (in == nullptr || out == nullptr || in == out) return SG_EINVAL;
+    if (!aligned(in, 16) || !aligned(out, 16)) return SG_EINVAL;
+    LaunchCfg cfg;
+    cudaError_t e = launch_ca(r, s, (int)map, in, out, (cudaStream_t)stream, cfg);
+    return e == cudaSuccess ? SG_OK : fail_cuda(e);
+}
+
+sg_status sg_diffuse_step(int r, int rho, sg_map map, const float *in, float *out,
+                          float alpha, void *stream)
+{
+    int s = 0;
+    if (!valid_level_tile(r, rho, &s)) return SG_EINVAL;
+    if (map < SG_MAP_LAMBDA || map > SG_MAP_LAMBDA_UNROLL) return SG_EINVAL;
+    if (map != SG_MAP_LAMBDA && map != SG_MAP_BBOX) return SG_EUNSUPPORTED;
+    if (in == nullptr || out == nullptr || in == out) return SG_EINVAL;
+    if (!aligned(in, 16) || !aligned(out, 16)) return SG_EINVAL;
+    if (!(alpha == alpha) || alpha > 3.0e38f || alpha < -3.0e38f) return SG_EINVAL;
+    LaunchCfg cfg;
+    cudaError_t e = launch_diffuse(r, s, (int)map, in, out, alpha, (cudaStream_t)stream, cfg);
+    return e == cudaSuccess ? SG_OK : fail_cuda(e);
+}
+
+sg_status sg_block_map(int rb, uint32_t *bx, uint32_t *by, void *stream)
+{
+    if (rb < 0 || rb > 16) return SG_EINVAL;
+    if (bx == nullptr || by == nullptr || bx == by) return SG_EINVAL;
+    if (!aligned(bx, 4) || !aligned(by, 4)) return SG_EINVAL;
+    cudaError_t e = launch_block_map(rb, bx, by, (cudaStream_t)stream);
+    return e == cudaSuccess ? SG_OK : fail_cuda(e);
+}
+
+sg_status sg_launch_stats(int r, int rho, sg_map map, uint64_t *launched, uint64_t *useful)
+{
+    int s = 0;
+    if (!valid_level_tile(r, rho, &s)) return SG_EINVAL;
+    uint64_t l;
+    const uint64_t cells = (uint64_t)pow3i(r);
+    switch (map) {
+    case SG_MAP_LAMBDA: l = (uint64_t)pow3i(r - s) << (2 * s); break;
+    case SG_MAP_BBOX: l = 1ull << (2 * r); break;
+    case SG_MAP_LAMBDA_LUT:
+    case SG_MAP_LAMBDA_UNROLL: l = cells; break;
+    default: return SG_EINVAL;
+    }
+    if (launched) *launched = l;
+    if (useful) *useful = cells;
+    return SG_OK;
+}
+
+}  // extern "C"

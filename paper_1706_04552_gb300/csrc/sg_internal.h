@@ -1,0 +1,53 @@
+// sg_internal.h -- launch entry points shared between the libsg translation
+// units (not part of the public ABI; see include/sg.h for that).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sg {
+
+enum : int { kMapLambda = 0, kMapBBox = 1, kMapLut = 2, kMapUnroll = 3 };
+
+// Launch geometry knobs.  ctas_per_sm <= 0 selects the occupancy maximum.
+struct LaunchCfg {
+    int ctas_per_sm = 0;
+};
+
+// Number of SMs of the current device (cached per device).
+int sm_count(int *err);
+
+cudaError_t launch_write_u8(int r, int s, int map, int vk, uint8_t *grid,
+                            uint64_t vs, cudaStream_t st, const LaunchCfg &cfg);
+cudaError_t launch_write_f32(int r, int s, int map, int vk, float *grid,
+                             uint64_t vs, cudaStream_t st, const LaunchCfg &cfg);
+cudaError_t launch_ca(int r, int s, int map, const uint8_t *in, uint8_t *out,
+                      cudaStream_t st, const LaunchCfg &cfg);
+cudaError_t launch_diffuse(int r, int s, int map, const float *in, float *out,
+                           float alpha, cudaStream_t st, const LaunchCfg &cfg);
+cudaError_t launch_block_map(int rb, uint32_t *bx, uint32_t *by, cudaStream_t st);
+
+// Persistent grid size: min(work units, SMs * resident CTAs).
+template <typename K>
+inline cudaError_t persistent_grid(K kernel, int threads, size_t smem,
+                                   uint64_t units, const LaunchCfg &cfg,
+                                   unsigned *grid)
+{
+    int err = 0;
+    const int sms = sm_count(&err);
+    if (err) return (cudaError_t)err;
+    int occ = cfg.ctas_per_sm;
+    if (occ <= 0) {
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel,
+                                                                      threads, smem);
+        if (e != cudaSuccess) return e;
+        if (occ < 1) occ = 1;
+    }
+    uint64_t g = (uint64_t)sms * (uint64_t)occ;
+    if (units < g) g = units;
+    if (g < 1) g = 1;
+    *grid = (unsigned)g;
+    return cudaSuccess;
+}
+
+}  // namespace sg

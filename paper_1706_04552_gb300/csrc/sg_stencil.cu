@@ -1,0 +1,490 @@
+// sg_stencil.cu -- per-cell stencils over the embedded gasket: the B3/S23
+// cellular automaton (uint8) and explicit diffusion (float32).
+//
+// The embedded layout keeps (x +- 1, y +- 1) a neighbourhood of the gasket
+// (Section I), so a tile's update needs the tile plus a one-cell halo.  A CTA
+// processes TPC tiles at a time (TPC * tile work ~ 256 threads):
+//   1. decode:  one warp per tile runs the lambda(omega) reduction of
+//               Theorem 1 (LambdaLane) or the bounding-box identity map;
+//   2. stage:   the tile's interior is copied to shared memory in 16-byte
+//               chunks, and only chunks holding gasket cells are read from
+//               HBM; the halo is read cell by cell and only at gasket cells
+//               (in a non-empty tile, the gasket structure leaves at most the
+//               right column, the bottom row and five isolated cells);
+//   3. compute: each thread produces one 16-byte chunk of the output tile
+//               from shared memory and stores it if it holds gasket cells.
+// Off-gasket cells are 0 in every state (precondition of the ABI), so a
+// neighbour sum over the plain neighbourhood only ever sees gasket cells.
+//
+// Tiles that hold no gasket cell are never launched by lambda; under the
+// bounding-box map every tile is visited and the cells of an empty tile drop
+// out at their membership test.
+#include "sg_device.cuh"
+#include "sg_internal.h"
+
+namespace sg {
+
+constexpr int kStencilThreads = 256;
+constexpr uint32_t kNoTile = 0xFFFFFFFFu;
+
+// Fills coord[0..tpc) with the block coordinates of tiles g*tpc .. g*tpc+tpc-1
+// (kNoTile past the end, and for bounding-box tiles with no gasket cell).
+template <int MAP>
+__device__ __forceinline__ void decode_tiles(uint2 *coord, int tpc, uint64_t g,
+                                             uint64_t ntiles, int rb, uint32_t W,
+                                             const LambdaLane &ll)
+{
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int t = warp; t < tpc; t += kStencilThreads / 32) {
+        const uint64_t q = g * (uint64_t)tpc + (uint64_t)t;
+        uint2 c = make_uint2(kNoTile, kNoTile);
+        if (q < ntiles) {
+            if constexpr (MAP == kMapBBox) {
+                const uint32_t bx = (uint32_t)(q & ((1ull << rb) - 1));
+                const uint32_t by = (uint32_t)(q >> rb);
+                if ((bx & by) == 0) c = make_uint2(bx, by);
+            } else {
+                const uint32_t wy = (uint32_t)q / W, wx = (uint32_t)q - wy * W;
+                c = ll.decode(wx, wy);
+            }
+        }
+        if (lane == 0) coord[t] = c;
+    }
+}
+
+// Halo slot h of a rho-tile -> tile-relative (row, col), both in [-1, rho].
+// Slots: the row above (rho+2 cells), the row below (rho+2), the left column
+// (rho) and the right column (rho).
+template <int RHO>
+__device__ __forceinline__ void halo_slot(int h, int &row, int &col)
+{
+    if (h < RHO + 2) { row = -1; col = h - 1; }
+    else if (h < 2 * RHO + 4) { row = RHO; col = h - (RHO + 2) - 1; }
+    else if (h < 3 * RHO + 4) { row = h - (2 * RHO + 4); col = -1; }
+    else { row = h - (3 * RHO + 4); col = RHO; }
+}
+
+template <typename T>
+__device__ __forceinline__ T load_cell(const T *__restrict__ in, int r, int64_t gx, int64_t gy)
+{
+    const int64_t n = (int64_t)1 << r;
+    if (gx < 0 || gy < 0 || gx >= n || gy >= n) return T(0);
+    if ((gx & gy) != 0) return T(0);
+    return in[(gy << r) + gx];
+}
+
+// ---------------------------------------------------------------------------
+// Byte-parallel (SWAR) arithmetic on 16 cells held as a uint4.
+// Element i of the chunk is byte (i % 4) of word (i / 4).
+// ---------------------------------------------------------------------------
+// element i <- c[i-1]; element 0 <- l
+__device__ __forceinline__ uint4 shift_in_left(uint4 c, uint32_t l)
+{
+    return make_uint4((c.x << 8) | l, __funnelshift_l(c.x, c.y, 8),
+                      __funnelshift_l(c.y, c.z, 8), __funnelshift_l(c.z, c.w, 8));
+}
+// element i <- c[i+1]; element 15 <- r
+__device__ __forceinline__ uint4 shift_in_right(uint4 c, uint32_t r)
+{
+    return make_uint4(__funnelshift_r(c.x, c.y, 8), __funnelshift_r(c.y, c.z, 8),
+                      __funnelshift_r(c.z, c.w, 8), (c.w >> 8) | (r << 24));
+}
+__device__ __forceinline__ uint4 add4(uint4 a, uint4 b)
+{
+    return make_uint4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
+}
+// 0x01 in the bytes i of a 16-cell chunk with (i & yl) == 0, yl = y mod 16
+__device__ __forceinline__ uint4 member_bytes16(uint32_t yl)
+{
+    uint32_t w = 0x01010101u;
+    if (yl & 1u) w &= 0x00FF00FFu;
+    if (yl & 2u) w &= 0x0000FFFFu;
+    uint4 m = make_uint4(w, w, w, w);
+    if (yl & 4u) { m.y = 0u; m.w = 0u; }
+    if (yl & 8u) { m.z = 0u; m.w = 0u; }
+    return m;
+}
+// B3/S23 on bytes: alive next iff (count | self) == 3.  count <= 8, so
+// t ^ 3 <= 11 and the +0x7F test below never carries between bytes.
+__device__ __forceinline__ uint32_t life_rule(uint32_t count, uint32_t self, uint32_t mask)
+{
+    const uint32_t t = (count | self) ^ 0x03030303u;
+    const uint32_t nonzero = ((t + 0x7F7F7F7Fu) & 0x80808080u) >> 7;
+    return (nonzero ^ 0x01010101u) & mask;
+}
+
+// ---------------------------------------------------------------------------
+// CA, rho >= 16: 16-cell chunks.
+// ---------------------------------------------------------------------------
+template <int S, int MAP>
+__global__ void __launch_bounds__(kStencilThreads)
+ca_vec_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int r,
+              uint64_t ntiles, uint32_t W)
+{
+    constexpr int RHO = 1 << S, CPR = RHO / 16, CHUNKS = RHO * CPR;
+    constexpr int TPC = CHUNKS >= kStencilThreads ? 1 : kStencilThreads / CHUNKS;
+    constexpr int P = RHO + 32;            // row pitch; interior at byte 16
+    constexpr int TILE = (RHO + 2) * P;
+    constexpr int HALO = 4 * RHO + 4;
+    __shared__ __align__(16) uint8_t sm[TPC * TILE];
+    __shared__ uint2 coord[TPC];
+
+    const int rb = r - S;
+    LambdaLane ll;
+    ll.init(threadIdx.x & 31, rb);
+    const uint64_t groups = (ntiles + TPC - 1) / TPC;
+
+    for (uint64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+        __syncthreads();
+        decode_tiles<MAP>(coord, TPC, g, ntiles, rb, W, ll);
+        __syncthreads();
+        for (int c = threadIdx.x; c < TPC * CHUNKS; c += kStencilThreads) {
+            const int t = c / CHUNKS, k = c % CHUNKS, ty = k / CPR, cx = k % CPR;
+            const uint2 b = coord[t];
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (b.x != kNoTile) {
+                const uint32_t x = (b.x << S) + 16u * cx, y = (b.y << S) + ty;
+                if (in_gasket(x, y))
+                    v = *reinterpret_cast<const uint4 *>(in + ((uint64_t)y << r) + x);
+            }
+            *reinterpret_cast<uint4 *>(sm + t * TILE + (ty + 1) * P + 16 + 16 * cx) = v;
+        }
+        for (int c = threadIdx.x; c < TPC * HALO; c += kStencilThreads) {
+            const int t = c / HALO, h = c % HALO;
+            int row, col;
+            halo_slot<RHO>(h, row, col);
+            const uint2 b = coord[t];
+            uint8_t v = 0;
+            if (b.x != kNoTile)
+                v = load_cell(in, r, (int64_t)(b.x << S) + col, (int64_t)(b.y << S) + row);
+            sm[t * TILE + (row + 1) * P + 16 + col] = v;
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < TPC * CHUNKS; c += kStencilThreads) {
+            const int t = c / CHUNKS, k = c % CHUNKS, ty = k / CPR, cx = k % CPR;
+            const uint2 b = coord[t];
+            if (b.x == kNoTile) continue;
+            const uint32_t x = (b.x << S) + 16u * cx, y = (b.y << S) + ty;
+            if (!in_gasket(x, y)) continue;       // no gasket cell in this chunk
+            const uint8_t *base = sm + t * TILE + 16 + 16 * cx;
+            const uint8_t *up = base + ty * P, *mid = up + P, *dn = mid + P;
+            const uint4 cu = *reinterpret_cast<const uint4 *>(up);
+            const uint4 cm = *reinterpret_cast<const uint4 *>(mid);
+            const uint4 cd = *reinterpret_cast<const uint4 *>(dn);
+            const uint4 hu = add4(add4(shift_in_left(cu, up[-1]), cu), shift_in_right(cu, up[16]));
+            const uint4 hd = add4(add4(shift_in_left(cd, dn[-1]), cd), shift_in_right(cd, dn[16]));
+            const uint4 hm = add4(shift_in_left(cm, mid[-1]), shift_in_right(cm, mid[16]));
+            const uint4 cnt = add4(add4(hu, hd), hm);
+            const uint4 m = member_bytes16(y & 15u);
+            uint4 o;
+            o.x = life_rule(cnt.x, cm.x, m.x);
+            o.y = life_rule(cnt.y, cm.y, m.y);
+            o.z = life_rule(cnt.z, cm.z, m.z);
+            o.w = life_rule(cnt.w, cm.w, m.w);
+            *reinterpret_cast<uint4 *>(out + ((uint64_t)y << r) + x) = o;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CA, rho <= 8: one cell per thread.
+// ---------------------------------------------------------------------------
+template <int S, int MAP>
+__global__ void __launch_bounds__(kStencilThreads)
+ca_cell_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int r,
+               uint64_t ntiles, uint32_t W)
+{
+    constexpr int RHO = 1 << S, CELLS = RHO * RHO;
+    constexpr int TPC = kStencilThreads / CELLS;
+    constexpr int P = RHO + 2, TILE = P * P, HALO = 4 * RHO + 4;
+    __shared__ uint8_t sm[TPC * TILE];
+    __shared__ uint2 coord[TPC];
+
+    const int rb = r - S;
+    LambdaLane ll;
+    ll.init(threadIdx.x & 31, rb);
+    const uint64_t groups = (ntiles + TPC - 1) / TPC;
+
+    for (uint64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+        __syncthreads();
+        decode_tiles<MAP>(coord, TPC, g, ntiles, rb, W, ll);
+        __syncthreads();
+        {
+            const int c = threadIdx.x, t = c / CELLS, k = c % CELLS;
+            const int ty = k / RHO, tx = k % RHO;
+            const uint2 b = coord[t];
+            uint8_t v = 0;
+            if (b.x != kNoTile)
+                v = load_cell(in, r, (int64_t)(b.x << S) + tx, (int64_t)(b.y << S) + ty);
+            sm[t * TILE + (ty + 1) * P + tx + 1] = v;
+        }
+        for (int c = threadIdx.x; c < TPC * HALO; c += kStencilThreads) {
+            const int t = c / HALO, h = c % HALO;
+            int row, col;
+            halo_slot<RHO>(h, row, col);
+            const uint2 b = coord[t];
+            uint8_t v = 0;
+            if (b.x != kNoTile)
+                v = load_cell(in, r, (int64_t)(b.x << S) + col, (int64_t)(b.y << S) + row);
+            sm[t * TILE + (row + 1) * P + col + 1] = v;
+        }
+        __syncthreads();
+        {
+            const int c = threadIdx.x, t = c / CELLS, k = c % CELLS;
+            const int ty = k / RHO, tx = k % RHO;
+            const uint2 b = coord[t];
+            if (b.x != kNoTile) {
+                const uint32_t x = (b.x << S) + tx, y = (b.y << S) + ty;
+                if (in_gasket(x, y)) {
+                    const uint8_t *p = sm + t * TILE + (ty + 1) * P + tx + 1;
+                    const int cnt = p[-P - 1] + p[-P] + p[-P + 1] + p[-1] + p[1] +
+                                    p[P - 1] + p[P] + p[P + 1];
+                    out[((uint64_t)y << r) + x] = (uint8_t)((cnt | p[0]) == 3);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Diffusion.  deg(x, y) counts the in-grid gasket 4-neighbours.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float diffuse_cell(uint32_t x, uint32_t y, uint32_t n,
+                                              float u, float l, float rr, float up,
+                                              float dn, float alpha)
+{
+    if (!in_gasket(x, y)) return 0.0f;
+    const int deg = (x > 0u && in_gasket(x - 1u, y)) + (x + 1u < n && in_gasket(x + 1u, y)) +
+                    (y > 0u && in_gasket(x, y - 1u)) + (y + 1u < n && in_gasket(x, y + 1u));
+    const float sum = (l + rr) + (up + dn);
+    return u + alpha * (sum - (float)deg * u);
+}
+
+// rho >= 4: 4-cell chunks (float4).
+template <int S, int MAP>
+__global__ void __launch_bounds__(kStencilThreads)
+diffuse_vec_kernel(const float *__restrict__ in, float *__restrict__ out, int r,
+                   uint64_t ntiles, uint32_t W, float alpha)
+{
+    constexpr int RHO = 1 << S, CPR = RHO / 4, CHUNKS = RHO * CPR;
+    constexpr int TPC = CHUNKS >= kStencilThreads ? 1 : kStencilThreads / CHUNKS;
+    constexpr int P = RHO + 8;             // row pitch (floats); interior at 4
+    constexpr int TILE = (RHO + 2) * P;
+    constexpr int HALO = 4 * RHO + 4;
+    __shared__ __align__(16) float sm[TPC * TILE];
+    __shared__ uint2 coord[TPC];
+
+    const int rb = r - S;
+    const uint32_t n = 1u << r;
+    LambdaLane ll;
+    ll.init(threadIdx.x & 31, rb);
+    const uint64_t groups = (ntiles + TPC - 1) / TPC;
+
+    for (uint64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+        __syncthreads();
+        decode_tiles<MAP>(coord, TPC, g, ntiles, rb, W, ll);
+        __syncthreads();
+        for (int c = threadIdx.x; c < TPC * CHUNKS; c += kStencilThreads) {
+            const int t = c / CHUNKS, k = c % CHUNKS, ty = k / CPR, cx = k % CPR;
+            const uint2 b = coord[t];
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (b.x != kNoTile) {
+                const uint32_t x = (b.x << S) + 4u * cx, y = (b.y << S) + ty;
+                if (in_gasket(x, y))
+                    v = *reinterpret_cast<const float4 *>(in + ((uint64_t)y << r) + x);
+            }
+            *reinterpret_cast<float4 *>(sm + t * TILE + (ty + 1) * P + 4 + 4 * cx) = v;
+        }
+        for (int c = threadIdx.x; c < TPC * HALO; c += kStencilThreads) {
+            const int t = c / HALO, h = c % HALO;
+            int row, col;
+            halo_slot<RHO>(h, row, col);
+            const uint2 b = coord[t];
+            float v = 0.f;
+            if (b.x != kNoTile)
+                v = load_cell(in, r, (int64_t)(b.x << S) + col, (int64_t)(b.y << S) + row);
+            sm[t * TILE + (row + 1) * P + 4 + col] = v;
+        }
+        __syncthreads();
+        for (int c = threadIdx.x; c < TPC * CHUNKS; c += kStencilThreads) {
+            const int t = c / CHUNKS, k = c % CHUNKS, ty = k / CPR, cx = k % CPR;
+            const uint2 b = coord[t];
+            if (b.x == kNoTile) continue;
+            const uint32_t x = (b.x << S) + 4u * cx, y = (b.y << S) + ty;
+            if (!in_gasket(x, y)) continue;
+            const float *mid = sm + t * TILE + (ty + 1) * P + 4 + 4 * cx;
+            const float4 cu = *reinterpret_cast<const float4 *>(mid - P);
+            const float4 cm = *reinterpret_cast<const float4 *>(mid);
+            const float4 cd = *reinterpret_cast<const float4 *>(mid + P);
+            const float l = mid[-1], rr = mid[4];
+            float4 o;
+            o.x = diffuse_cell(x + 0u, y, n, cm.x, l, cm.y, cu.x, cd.x, alpha);
+            o.y = diffuse_cell(x + 1u, y, n, cm.y, cm.x, cm.z, cu.y, cd.y, alpha);
+            o.z = diffuse_cell(x + 2u, y, n, cm.z, cm.y, cm.w, cu.z, cd.z, alpha);
+            o.w = diffuse_cell(x + 3u, y, n, cm.w, cm.z, rr, cu.w, cd.w, alpha);
+            *reinterpret_cast<float4 *>(out + ((uint64_t)y << r) + x) = o;
+        }
+    }
+}
+
+// rho <= 2: one cell per thread.
+template <int S, int MAP>
+__global__ void __launch_bounds__(kStencilThreads)
+diffuse_cell_kernel(const float *__restrict__ in, float *__restrict__ out, int r,
+                    uint64_t ntiles, uint32_t W, float alpha)
+{
+    constexpr int RHO = 1 << S, CELLS = RHO * RHO;
+    constexpr int TPC = kStencilThreads / CELLS;
+    constexpr int P = RHO + 2, TILE = P * P, HALO = 4 * RHO + 4;
+    __shared__ float sm[TPC * TILE];
+    __shared__ uint2 coord[TPC];
+
+    const int rb = r - S;
+    const uint32_t n = 1u << r;
+    LambdaLane ll;
+    ll.init(threadIdx.x & 31, rb);
+    const uint64_t groups = (ntiles + TPC - 1) / TPC;
+
+    for (uint64_t g = blockIdx.x; g < groups; g += gridDim.x) {
+        __syncthreads();
+        decode_tiles<MAP>(coord, TPC, g, ntiles, rb, W, ll);
+        __syncthreads();
+        {
+            const int c = threadIdx.x, t = c / CELLS, k = c % CELLS;
+            const int ty = k / RHO, tx = k % RHO;
+            const uint2 b = coord[t];
+            float v = 0.f;
+            if (b.x != kNoTile)
+                v = load_cell(in, r, (int64_t)(b.x << S) + tx, (int64_t)(b.y << S) + ty);
+            sm[t * TILE + (ty + 1) * P + tx + 1] = v;
+        }
+        for (int c = threadIdx.x; c < TPC * HALO; c += kStencilThreads) {
+            const int t = c / HALO, h = c % HALO;
+            int row, col;
+            halo_slot<RHO>(h, row, col);
+            const uint2 b = coord[t];
+            float v = 0.f;
+            if (b.x != kNoTile)
+                v = load_cell(in, r, (int64_t)(b.x << S) + col, (int64_t)(b.y << S) + row);
+            sm[t * TILE + (row + 1) * P + col + 1] = v;
+        }
+        __syncthreads();
+        {
+            const int c = threadIdx.x, t = c / CELLS, k = c % CELLS;
+            const int ty = k / RHO, tx = k % RHO;
+            const uint2 b = coord[t];
+            if (b.x != kNoTile) {
+                const uint32_t x = (b.x << S) + tx, y = (b.y << S) + ty;
+                if (in_gasket(x, y)) {
+                    const float *p = sm + t * TILE + (ty + 1) * P + tx + 1;
+                    out[((uint64_t)y << r) + x] =
+                        diffuse_cell(x, y, n, p[0], p[-1], p[1], p[-P], p[P], alpha);
+                }
+            }
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <int S> struct StencilShape {
+    static constexpr int CA_TPC =
+        S >= 4 ? ((1 << S) * ((1 << S) / 16) >= kStencilThreads
+                      ? 1 : kStencilThreads / ((1 << S) * ((1 << S) / 16)))
+               : kStencilThreads / ((1 << S) * (1 << S));
+    static constexpr int DF_TPC =
+        S >= 2 ? ((1 << S) * ((1 << S) / 4) >= kStencilThreads
+                      ? 1 : kStencilThreads / ((1 << S) * ((1 << S) / 4)))
+               : kStencilThreads / ((1 << S) * (1 << S));
+};
+
+template <int S, int MAP>
+cudaError_t launch_ca_t(int r, const uint8_t *in, uint8_t *out, cudaStream_t st,
+                        const LaunchCfg &cfg)
+{
+    const int rb = r - S;
+    const uint64_t ntiles = (MAP == kMapBBox) ? (1ull << (2 * rb)) : (uint64_t)pow3i(rb);
+    const uint32_t W = (uint32_t)pow3i(rb / 2);
+    constexpr int TPC = StencilShape<S>::CA_TPC;
+    const uint64_t groups = (ntiles + TPC - 1) / TPC;
+    unsigned grid = 1;
+    cudaError_t e;
+    if constexpr (S >= 4) {
+        auto k = ca_vec_kernel<S, MAP>;
+        e = persistent_grid(k, kStencilThreads, 0, groups, cfg, &grid);
+        if (e != cudaSuccess) return e;
+        k<<<grid, kStencilThreads, 0, st>>>(in, out, r, ntiles, W);
+    } else {
+        auto k = ca_cell_kernel<S, MAP>;
+        e = persistent_grid(k, kStencilThreads, 0, groups, cfg, &grid);
+        if (e != cudaSuccess) return e;
+        k<<<grid, kStencilThreads, 0, st>>>(in, out, r, ntiles, W);
+    }
+    return cudaGetLastError();
+}
+
+template <int S, int MAP>
+cudaError_t launch_diffuse_t(int r, const float *in, float *out, float alpha,
+                             cudaStream_t st, const LaunchCfg &cfg)
+{
+    const int rb = r - S;
+    const uint64_t ntiles = (MAP == kMapBBox) ? (1ull << (2 * rb)) : (uint64_t)pow3i(rb);
+    const uint32_t W = (uint32_t)pow3i(rb / 2);
+    constexpr int TPC = StencilShape<S>::DF_TPC;
+    const uint64_t groups = (ntiles + TPC - 1) / TPC;
+    unsigned grid = 1;
+    cudaError_t e;
+    if constexpr (S >= 2) {
+        auto k = diffuse_vec_kernel<S, MAP>;
+        e = persistent_grid(k, kStencilThreads, 0, groups, cfg, &grid);
+        if (e != cudaSuccess) return e;
+        k<<<grid, kStencilThreads, 0, st>>>(in, out, r, ntiles, W, alpha);
+    } else {
+        auto k = diffuse_cell_kernel<S, MAP>;
+        e = persistent_grid(k, kStencilThreads, 0, groups, cfg, &grid);
+        if (e != cudaSuccess) return e;
+        k<<<grid, kStencilThreads, 0, st>>>(in, out, r, ntiles, W, alpha);
+    }
+    return cudaGetLastError();
+}
+
+#define SG_S_SWITCH(s, CALL)                 \
+    switch (s) {                             \
+    case 0: return CALL(0);                  \
+    case 1: return CALL(1);                  \
+    case 2: return CALL(2);                  \
+    case 3: return CALL(3);                  \
+    case 4: return CALL(4);                  \
+    case 5: return CALL(5);                  \
+    case 6: return CALL(6);                  \
+    default: return cudaErrorInvalidValue;   \
+    }
+
+cudaError_t launch_ca(int r, int s, int map, const uint8_t *in, uint8_t *out,
+                      cudaStream_t st, const LaunchCfg &cfg)
+{
+    if (map == kMapBBox) {
+#define CALL(S) launch_ca_t<S, kMapBBox>(r, in, out, st, cfg)
+        SG_S_SWITCH(s, CALL)
+#undef CALL
+    }
+#define CALL(S) launch_ca_t<S, kMapLambda>(r, in, out, st, cfg)
+    SG_S_SWITCH(s, CALL)
+#undef CALL
+}
+
+cudaError_t launch_diffuse(int r, int s, int map, const float *in, float *out,
+                           float alpha, cudaStream_t st, const LaunchCfg &cfg)
+{
+    if (map == kMapBBox) {
+#define CALL(S) launch_diffuse_t<S, kMapBBox>(r, in, out, alpha, st, cfg)
+        SG_S_SWITCH(s, CALL)
+#undef CALL
+    }
+#define CALL(S) launch_diffuse_t<S, kMapLambda>(r, in, out, alpha, st, cfg)
+    SG_S_SWITCH(s, CALL)
+#undef CALL
+}
+
+}  // namespace sg

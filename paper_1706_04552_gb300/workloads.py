@@ -1,0 +1,29 @@
+"""Named workload presets (the sizes, seeds and launch configurations the
+benchmark times and the full-size parity tests check).
+
+Every input is synthetic and seeded (see ``inputs``).  Level r means an
+n x n grid with n = 2^r; the gasket has 3^r cells.
+"""
+from __future__ import annotations
+
+# Small end-to-end case: level 10 in a uint8 grid, rho = 16; a write pass of
+# (x*31 + y) & 0xFF, then 16 double-buffered CA steps from Bernoulli(0.5)
+# seeded with 0; lambda and bounding-box maps both run.
+SMALL = dict(r=10, rho=16, write_value="linear31", write_seed=0,
+             ca_p=0.5, ca_seed=0, ca_steps=16)
+
+# Map-and-write sweep: levels 8..16 in uint8 and float32 grids, rho in
+# {8, 16, 32, 64}, value = hash of (x, y) with seed 1.
+WRITE_SWEEP = dict(levels=tuple(range(8, 17)), rhos=(8, 16, 32, 64),
+                   dtypes=("u8", "f32"), value="hash", seed=1)
+
+# The headline: the write pass at n = 2^16 (a 4.3 GB uint8 grid), lambda map.
+# rho and the intra-tile variant are the measured best on GB300.
+WRITE_HEADLINE = dict(r=16, dtype="u8", value="hash", seed=1,
+                      map="lambda_lut", rho=16, bbox_rho=64)
+
+# Stencils at levels 14 and 15: 256 CA steps from Bernoulli(0.3) seeded with
+# 0; 100 diffusion steps (alpha = 0.2) from U[0,1) seeded with 0.
+STENCILS = dict(levels=(14, 15), ca_p=0.3, ca_seed=0, ca_steps=256,
+                diff_seed=0, diff_steps=100, alpha=0.2,
+                ca_rho=32, diff_rho=16, bbox_ca_rho=32, bbox_diff_rho=16)

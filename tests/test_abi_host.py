@@ -1,0 +1,107 @@
+"""The C ABI on the host: libsg.so loads, exports every symbol include/sg.h
+declares, reports its status strings and launch accounting, and rejects bad
+arguments before launching anything (no call here reaches a kernel)."""
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+import paper_1706_04552_gb300 as sg
+from paper_1706_04552_gb300 import build as sg_build
+
+
+@pytest.fixture(scope="module")
+def L():
+    sg_build.build()
+    return sg.lib()
+
+
+def _declared_symbols():
+    text = open(os.path.join(ROOT, "include", "sg.h")).read()
+    return sorted(set(re.findall(r"SG_API\s+[\w\s\*]+?\b(sg_\w+)\s*\(", text)))
+
+
+def test_header_declares_the_boundary():
+    names = _declared_symbols()
+    for want in ("sg_map_write", "sg_ca_step", "sg_diffuse_step", "sg_block_map",
+                 "sg_launch_stats", "sg_status_str", "sg_last_error_string",
+                 "sg_abi_version"):
+        assert want in names
+
+
+def test_library_exports_every_declared_symbol(L):
+    for name in _declared_symbols():
+        assert hasattr(L, name), name
+
+
+def test_abi_version_and_status_strings(L):
+    assert sg.sg_abi_version() == 1
+    assert sg.sg_status_str(0) == "SG_OK"
+    for code in range(1, 6):
+        assert sg.sg_status_str(code).startswith("SG_E")
+    assert "unknown" in sg.sg_status_str(99)
+    assert sg.lib().sg_last_error_string() == b""
+
+
+@pytest.mark.parametrize("r,rho", [(0, 1), (4, 2), (8, 8), (10, 16), (12, 32), (16, 64)])
+def test_launch_stats_match_the_oracle(L, orc, r, rho):
+    s = rho.bit_length() - 1
+    for name, mid in sg.MAPS.items():
+        st, launched, useful = sg.sg_launch_stats(r, rho, mid)
+        assert st == 0
+        assert useful == 3 ** r
+        if r <= 12:
+            assert (launched, useful) == orc.launch_counts(r, s, mid), name
+    _, lam, _ = sg.sg_launch_stats(r, rho, sg.MAPS["lambda"])
+    _, bb, _ = sg.sg_launch_stats(r, rho, sg.MAPS["bbox"])
+    assert lam == 3 ** (r - s) * 4 ** s and bb == 4 ** r
+
+
+FAKE = 0x10000  # never dereferenced: every call below fails validation first
+
+
+@pytest.mark.parametrize("r,rho", [(-1, 1), (17, 1), (4, 3), (4, 0), (4, 32), (8, 128), (3, 16)])
+def test_bad_level_or_tile_is_einval(L, r, rho):
+    assert sg.sg_map_write(r, rho, 0, 0, FAKE, 2, 1) == sg.SG_EINVAL
+    assert sg.sg_ca_step(r, rho, 0, FAKE, FAKE + 4096, 0) == sg.SG_EINVAL
+    assert sg.sg_diffuse_step(r, rho, 0, FAKE, FAKE + 4096, 0.2, 0) == sg.SG_EINVAL
+    assert sg.sg_launch_stats(r, rho, 0)[0] == sg.SG_EINVAL
+
+
+def test_bad_pointers_and_enums_are_einval(L):
+    assert sg.sg_map_write(8, 16, 0, 0, 0, 2, 1) == sg.SG_EINVAL          # null grid
+    assert sg.sg_map_write(8, 16, 9, 0, FAKE, 2, 1) == sg.SG_EINVAL       # bad map
+    assert sg.sg_map_write(8, 16, 0, 7, FAKE, 2, 1) == sg.SG_EINVAL       # bad dtype
+    assert sg.sg_map_write(8, 16, 0, 0, FAKE, 5, 1) == sg.SG_EINVAL       # bad value kind
+    assert sg.sg_map_write(8, 16, 0, 1, FAKE + 2, 2, 1) == sg.SG_EINVAL   # f32 misaligned
+    assert sg.sg_ca_step(8, 16, 0, FAKE, FAKE, 0) == sg.SG_EINVAL         # in == out
+    assert sg.sg_ca_step(8, 16, 0, 0, FAKE, 0) == sg.SG_EINVAL            # null in
+    assert sg.sg_ca_step(8, 16, 0, FAKE + 8, FAKE + 8192, 0) == sg.SG_EINVAL   # misaligned
+    assert sg.sg_diffuse_step(8, 16, 0, FAKE, FAKE + 4, 0.2, 0) == sg.SG_EINVAL
+    assert sg.sg_diffuse_step(8, 16, 0, FAKE, FAKE + 8192, float("nan"), 0) == sg.SG_EINVAL
+    assert sg.sg_block_map(17, FAKE, FAKE + 64, 0) == sg.SG_EINVAL
+    assert sg.sg_block_map(4, FAKE, FAKE, 0) == sg.SG_EINVAL
+    assert sg.sg_block_map(4, 0, FAKE, 0) == sg.SG_EINVAL
+
+
+def test_stencils_reject_intra_block_maps(L):
+    for m in ("lambda_lut", "lambda_unroll"):
+        mid = sg.MAPS[m]
+        assert sg.sg_ca_step(8, 16, mid, FAKE, FAKE + 8192, 0) == sg.SG_EUNSUPPORTED
+        assert sg.sg_diffuse_step(8, 16, mid, FAKE, FAKE + 8192, 0.2, 0) == sg.SG_EUNSUPPORTED
+
+
+def test_tensor_layer_refuses_cpu_tensors(L):
+    torch = pytest.importorskip("torch")
+    g = torch.zeros(16 * 16, dtype=torch.uint8)
+    with pytest.raises(TypeError):
+        sg.map_write(g, 4, 4)
+
+
+def test_missing_library_fails_loudly(tmp_path, monkeypatch):
+    monkeypatch.setenv("SG_LIB", str(tmp_path / "nope.so"))
+    monkeypatch.setattr(sg, "_lib", None)
+    with pytest.raises(ImportError):
+        sg.lib()

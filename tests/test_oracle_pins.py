@@ -344,3 +344,15 @@ def test_diffusion_region_light_cone(orc):
         win = inputs.uniform_region(r, 2, x - R, y - R, 2 * R + 1, 2 * R + 1)
         win = orc.diffuse_steps(r, win, t, 0.2, x - R, y - R)
         assert win[R, R] == full[y, x]
+
+
+def test_write_expected_at_matches_full_pass(orc):
+    # the sampled form agrees with the brute-force pass cell by cell
+    r, n = 8, 256
+    rng = np.random.default_rng(0)
+    before = rng.integers(0, 256, (n, n), dtype=np.uint8)
+    full = before.copy()
+    orc.map_write(r, full, orc.VAL_HASH, 9)
+    ys, xs = np.divmod(np.arange(n * n), n)
+    got = orc.write_expected_at(r, np.uint8, orc.VAL_HASH, 9, xs, ys, before.ravel())
+    assert np.array_equal(got, full.ravel())
