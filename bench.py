@@ -51,9 +51,14 @@ def parse_args():
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--rho", type=int, default=None)
     p.add_argument("--map", default=None)
+    p.add_argument("--order", default=None, choices=("rowmajor", "interleaved"))
+    p.add_argument("--store", default=None, choices=("auto", "scatter", "staged"))
     p.add_argument("--no-extras", action="store_true",
                    help="skip the comparison workloads (bbox, f32, stencils)")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--quick", action="store_true",
+                   help="headline launches only (no clock soak, extras, e2e or CPU "
+                        "baseline): the form used under ncu")
     return p.parse_args()
 
 
@@ -251,20 +256,26 @@ def run_ours(args, grp: Group):
         w["rho"] = args.rho
     if args.map:
         w["map"] = args.map
+    if args.order:
+        w["order"] = args.order
+    if args.store:
+        w["store"] = args.store
     r, n = w["r"], 1 << w["r"]
     cells = 3 ** r
     grid = torch.zeros(n * n, dtype=torch.uint8, device=dev)
 
     def step():
-        sg.map_write(grid, r, w["rho"], w["map"], w["value"], w["seed"], stream)
+        sg.map_write(grid, r, w["rho"], w["map"], w["value"], w["seed"], stream,
+                     order=w["order"], store=w["store"])
 
     for _ in range(max(3, args.warmup)):
         step()
     torch.cuda.synchronize(dev)
 
     sampler = ClockSampler(torch.cuda.current_device())
-    sampler.start()
-    soak(step, 1.0, stream)                   # clocks settle, sampler sees load
+    if not args.quick:
+        sampler.start()
+        soak(step, 1.0, stream)               # clocks settle, sampler sees load
     grp.barrier()
     torch.cuda.synchronize(dev)
     total_ms, per_launch = time_launches(step, args.steps, stream)
@@ -281,7 +292,7 @@ def run_ours(args, grp: Group):
     sector_bytes = touched_bytes(r, 1, 32)
     achieved = line_bytes / (launch_ms / 1e3) / 1e9
     launched, useful = sg.launch_stats(r, w["rho"], w["map"])
-    kernel_key = f"write_{w['map']}_r{r}_u8_rho{w['rho']}"
+    kernel_key = f"write_{w['map']}_{w['store']}_{w['order']}_r{r}_u8_rho{w['rho']}"
     roofline = {
         "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
         "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
@@ -301,8 +312,10 @@ def run_ours(args, grp: Group):
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {
             "workload": (f"map-and-write, level {r} gasket in a {n}x{n} uint8 grid, "
-                         f"hash(x,y) seed {w['seed']}, map {w['map']}, rho {w['rho']}"),
-            "r": r, "n": n, "rho": w["rho"], "map": w["map"], "value": w["value"],
+                         f"hash(x,y) seed {w['seed']}, map {w['map']}, rho {w['rho']}, "
+                         f"{w['order']} order, {w['store']} stores"),
+            "r": r, "n": n, "rho": w["rho"], "map": w["map"], "order": w["order"],
+            "store": w["store"], "value": w["value"],
             "seed": w["seed"], "cells_per_step": cells,
             "l2": "inputs larger than L2 (4.3 GB grid; 181 MB touched sectors > 129 MB L2)",
             "parallelism": "replicas" if grp.world > 1 else "single GPU",
@@ -313,6 +326,8 @@ def run_ours(args, grp: Group):
         "gpu_launches": args.steps,
     }
 
+    if args.quick:
+        return out
     if grp.rank == 0 and not args.no_extras:
         out["compare"] = compare_workloads(sg, torch, dev, stream, w, grid, launch_ms)
     del grid
@@ -412,7 +427,8 @@ def measure_e2e(sg, torch, dev, stream, w, grp, steps):
     dgrid = torch.empty(n * n, dtype=torch.uint8, device=dev)
 
     def step():
-        sg.map_write_host(host, dgrid, r, w["rho"], w["map"], w["value"], w["seed"], stream)
+        sg.map_write_host(host, dgrid, r, w["rho"], w["map"], w["value"], w["seed"], stream,
+                          order=w["order"], store=w["store"])
 
     step()
     torch.cuda.synchronize(dev)

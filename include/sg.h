@@ -81,6 +81,32 @@ typedef enum {
     SG_MAP_LAMBDA_UNROLL = 3
 } sg_map;
 
+/* Order in which the lambda block space Pi is walked.  lambda(omega) itself
+ * is the same in both; only which tile a given launch index q names differs.
+ *   SG_ORDER_ROWMAJOR:    omega = (q mod 3^floor(rb/2), q div 3^floor(rb/2)),
+ *                         the paper's two-dimensional grid row by row.
+ *   SG_ORDER_INTERLEAVED: the base-3 digits of q are dealt alternately to
+ *                         omega_y (digits 0, 2, 4, ...) and omega_x (digits
+ *                         1, 3, 5, ...), so digit mu-1 of q is beta_mu and
+ *                         consecutive q are neighbouring tiles. */
+typedef enum { SG_ORDER_ROWMAJOR = 0, SG_ORDER_INTERLEAVED = 1 } sg_order;
+
+/* How the write pass stores (see sg_map_write). */
+typedef enum {
+    SG_STORE_AUTO = 0,      /* the library's choice for dtype and rho */
+    SG_STORE_SCATTER = 1,   /* one store per gasket cell */
+    SG_STORE_STAGED = 2     /* whole 16-byte chunks merged in shared memory;
+                               needs rho * element size >= 16 bytes */
+} sg_store;
+
+/* Launch options of the *_ex calls.  Zero-initialise, then set fields. */
+typedef struct {
+    int order;          /* sg_order; -1 = library default */
+    int store;          /* sg_store (write pass only) */
+    int ctas_per_sm;    /* CTAs per SM of the persistent grid; 0 = occupancy maximum */
+    int reserved[5];    /* must be 0 */
+} sg_launch_opts;
+
 typedef enum {
     SG_VAL_CONST = 0,     /* u8: low 8 bits of value_or_seed; f32: low 32 bits
                              reinterpreted as an IEEE float */
@@ -103,10 +129,15 @@ typedef enum {
  *   value_or_seed  the constant, or the hash seed
  *   stream         cudaStream_t
  * Launches one kernel.  Returns SG_OK, SG_EINVAL or SG_ECUDA.
+ *
+ * With SG_STORE_STAGED (the default where rho * element size >= 16 bytes)
+ * off-gasket cells that share a 16-byte chunk with gasket cells are read and
+ * written back unchanged, so no other kernel may write `grid` while the pass
+ * runs; with SG_STORE_SCATTER only gasket cells are ever stored.
  */
 SG_API sg_status sg_map_write(int r, int rho, sg_map map, sg_dtype dtype, void *grid,
-                       sg_value_kind value_kind, uint64_t value_or_seed,
-                       void *stream);
+                              sg_value_kind value_kind, uint64_t value_or_seed,
+                              void *stream);
 
 /*
  * sg_ca_step -- one step of the Life-like B3/S23 automaton restricted to the
@@ -127,7 +158,7 @@ SG_API sg_status sg_map_write(int r, int rho, sg_map map, sg_dtype dtype, void *
  * Launches one kernel.
  */
 SG_API sg_status sg_ca_step(int r, int rho, sg_map map, const uint8_t *in,
-                     uint8_t *out, void *stream);
+                            uint8_t *out, void *stream);
 
 /*
  * sg_diffuse_step -- one explicit FP32 diffusion step on the gasket's
@@ -145,18 +176,29 @@ SG_API sg_status sg_ca_step(int r, int rho, sg_map map, const uint8_t *in,
  * Launches one kernel.
  */
 SG_API sg_status sg_diffuse_step(int r, int rho, sg_map map, const float *in,
-                          float *out, float alpha, void *stream);
+                                 float *out, float alpha, void *stream);
+
+/* sg_map_write / sg_ca_step / sg_diffuse_step with launch options (NULL =
+ * defaults).  A store mode the tile shape cannot use returns SG_EUNSUPPORTED;
+ * a bad option value returns SG_EINVAL. */
+SG_API sg_status sg_map_write_ex(int r, int rho, sg_map map, sg_dtype dtype, void *grid,
+                                 sg_value_kind value_kind, uint64_t value_or_seed,
+                                 const sg_launch_opts *opts, void *stream);
+SG_API sg_status sg_ca_step_ex(int r, int rho, sg_map map, const uint8_t *in, uint8_t *out,
+                               const sg_launch_opts *opts, void *stream);
+SG_API sg_status sg_diffuse_step_ex(int r, int rho, sg_map map, const float *in, float *out,
+                                    float alpha, const sg_launch_opts *opts, void *stream);
 
 /*
  * sg_block_map -- the lambda block decode on its own (Theorem 1: Eq. beta,
  * Eq. Delta, Eq. tau, Eq. lambda), for checking the map bit for bit.
- * For every launch index q in [0, 3^rb): omega = (q mod 3^floor(rb/2),
- * q div 3^floor(rb/2)); (bx[q], by[q]) = (lambda_x(omega),
- * 2^rb - 1 - lambda_y(omega)), i.e. the paper's lambda mirrored into the
- * (x & y) == 0 orientation.  bx, by: device arrays of 3^rb uint32.
- * rb: 0..16.  Launches one kernel.
+ * For every launch index q in [0, 3^rb), omega(q) as `order` defines it
+ * (sg_order); (bx[q], by[q]) = (lambda_x(omega), 2^rb - 1 - lambda_y(omega)),
+ * i.e. the paper's lambda mirrored into the (x & y) == 0 orientation.
+ * bx, by: device arrays of 3^rb uint32.  rb: 0..16.  Launches one kernel.
  */
-SG_API sg_status sg_block_map(int rb, uint32_t *bx, uint32_t *by, void *stream);
+SG_API sg_status sg_block_map(int rb, sg_order order, uint32_t *bx, uint32_t *by,
+                              void *stream);
 
 /*
  * sg_launch_stats -- host-only accounting of one pass (Lemma 1, Theorem 2):
@@ -165,7 +207,7 @@ SG_API sg_status sg_block_map(int rb, uint32_t *bx, uint32_t *by, void *stream);
  * `useful` = gasket cells = 3^r.  No GPU work.  Either pointer may be NULL.
  */
 SG_API sg_status sg_launch_stats(int r, int rho, sg_map map, uint64_t *launched,
-                          uint64_t *useful);
+                                 uint64_t *useful);
 
 /* Human-readable name of a status code (static storage). */
 SG_API const char *sg_status_str(sg_status status);

@@ -73,9 +73,11 @@ def _load():
         lib.or_pi_extent.restype = None
         lib.or_lambda_paper.argtypes = [i32, u64, u64, p_u64, p_u64]
         lib.or_lambda_paper.restype = None
-        lib.or_block_of_index.argtypes = [i32, u64, p_u64, p_u64]
+        lib.or_omega_of_index.argtypes = [i32, i32, u64, p_u64, p_u64]
+        lib.or_omega_of_index.restype = None
+        lib.or_block_of_index.argtypes = [i32, i32, u64, p_u64, p_u64]
         lib.or_block_of_index.restype = None
-        lib.or_block_map.argtypes = [i32, vp, vp]
+        lib.or_block_map.argtypes = [i32, i32, vp, vp]
         lib.or_block_map.restype = None
         lib.or_launch_counts.argtypes = [i32, i32, i32, p_u64, p_u64]
         lib.or_launch_counts.restype = None
@@ -149,17 +151,26 @@ def lambda_paper(rb: int, wx: int, wy: int) -> tuple[int, int]:
     return a.value, b.value
 
 
-def block_of_index(rb: int, q: int) -> tuple[int, int]:
+ORDER_ROWMAJOR, ORDER_INTERLEAVED = 0, 1
+
+
+def omega_of_index(rb: int, q: int, order: int = ORDER_ROWMAJOR) -> tuple[int, int]:
     a, b = ctypes.c_uint64(), ctypes.c_uint64()
-    _load().or_block_of_index(rb, q, ctypes.byref(a), ctypes.byref(b))
+    _load().or_omega_of_index(rb, order, q, ctypes.byref(a), ctypes.byref(b))
     return a.value, b.value
 
 
-def block_map(rb: int) -> tuple[np.ndarray, np.ndarray]:
+def block_of_index(rb: int, q: int, order: int = ORDER_ROWMAJOR) -> tuple[int, int]:
+    a, b = ctypes.c_uint64(), ctypes.c_uint64()
+    _load().or_block_of_index(rb, order, q, ctypes.byref(a), ctypes.byref(b))
+    return a.value, b.value
+
+
+def block_map(rb: int, order: int = ORDER_ROWMAJOR) -> tuple[np.ndarray, np.ndarray]:
     total = 3 ** rb
     bx = np.zeros(total, dtype=np.uint32)
     by = np.zeros(total, dtype=np.uint32)
-    _load().or_block_map(rb, _ptr(bx), _ptr(by))
+    _load().or_block_map(rb, order, _ptr(bx), _ptr(by))
     return bx, by
 
 

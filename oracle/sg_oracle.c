@@ -131,25 +131,50 @@ void or_lambda_paper(int rb, uint64_t wx, uint64_t wy, uint64_t *lx, uint64_t *l
     *ly = sy;
 }
 
-/* Block coordinate of launch index q in the (x & y) == 0 orientation.
- * The launch index walks Pi row by row: omega = (q mod Wx, q div Wx).
- * The paper's lambda is then mirrored vertically: by = n_b - 1 - lambda_y. */
-void or_block_of_index(int rb, uint64_t q, uint64_t *bx, uint64_t *by)
+/* The point omega of Pi that launch index q names, for two walking orders.
+ *   order 0 (row-major): omega = (q mod Wx, q div Wx), the paper's 2-D grid
+ *     read row by row.
+ *   order 1 (interleaved): the base-3 digits of q, least significant first,
+ *     are dealt alternately to omega_y (digits 0, 2, 4, ...) and omega_x
+ *     (digits 1, 3, 5, ...). */
+void or_omega_of_index(int rb, int order, uint64_t q, uint64_t *wx, uint64_t *wy)
 {
-    uint64_t wxe, wye, lx, ly;
-    or_pi_extent(rb, &wxe, &wye);
-    or_lambda_paper(rb, q % wxe, q / wxe, &lx, &ly);
+    if (order == 0) {
+        uint64_t wxe, wye;
+        or_pi_extent(rb, &wxe, &wye);
+        *wx = q % wxe;
+        *wy = q / wxe;
+        return;
+    }
+    uint64_t x = 0, y = 0, px = 1, py = 1;
+    for (int d = 0; d < rb; ++d) {
+        uint64_t digit = q % 3;
+        q /= 3;
+        if (d % 2 == 0) { y += digit * py; py *= 3; }
+        else            { x += digit * px; px *= 3; }
+    }
+    *wx = x;
+    *wy = y;
+}
+
+/* Block coordinate of launch index q in the (x & y) == 0 orientation: the
+ * paper's lambda of omega(q), mirrored vertically: by = n_b - 1 - lambda_y. */
+void or_block_of_index(int rb, int order, uint64_t q, uint64_t *bx, uint64_t *by)
+{
+    uint64_t wx, wy, lx, ly;
+    or_omega_of_index(rb, order, q, &wx, &wy);
+    or_lambda_paper(rb, wx, wy, &lx, &ly);
     *bx = lx;
     *by = (((uint64_t)1 << rb) - 1) - ly;
 }
 
 /* All 3^rb block coordinates in launch order (the map the GPU decodes). */
-void or_block_map(int rb, uint32_t *bx, uint32_t *by)
+void or_block_map(int rb, int order, uint32_t *bx, uint32_t *by)
 {
     uint64_t total = ipow3(rb);
     for (uint64_t q = 0; q < total; ++q) {
         uint64_t a, b;
-        or_block_of_index(rb, q, &a, &b);
+        or_block_of_index(rb, order, q, &a, &b);
         bx[q] = (uint32_t)a;
         by[q] = (uint32_t)b;
     }
@@ -179,7 +204,7 @@ void or_launch_counts(int r, int s, int map, uint64_t *launched, uint64_t *usefu
         uint64_t blocks = ipow3(rb);
         for (uint64_t q = 0; q < blocks; ++q) {
             uint64_t bx, by;
-            or_block_of_index(rb, q, &bx, &by);
+            or_block_of_index(rb, 0, q, &bx, &by);
             for (uint64_t ty = 0; ty < rho; ++ty)
                 for (uint64_t tx = 0; tx < rho; ++tx) {
                     int m = or_member(bx * rho + tx, by * rho + ty);

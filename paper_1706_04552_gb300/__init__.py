@@ -23,9 +23,10 @@ import threading
 __all__ = [
     "SGError", "lib", "lib_path",
     "sg_map_write", "sg_ca_step", "sg_diffuse_step", "sg_block_map",
+    "sg_map_write_ex", "sg_ca_step_ex", "sg_diffuse_step_ex", "LaunchOpts", "launch_opts",
     "sg_launch_stats", "sg_status_str", "sg_abi_version",
     "map_write", "map_write_host", "ca_step", "diffuse_step", "block_map", "launch_stats",
-    "MAPS", "DTYPES", "VALUES",
+    "MAPS", "DTYPES", "VALUES", "ORDERS", "STORES",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -35,6 +36,25 @@ SG_OK, SG_EINVAL, SG_ECUDA, SG_ENOMEM, SG_ETIMEOUT, SG_EUNSUPPORTED = range(6)
 MAPS = {"lambda": 0, "bbox": 1, "lambda_lut": 2, "lambda_unroll": 3}
 DTYPES = {"u8": 0, "f32": 1}
 VALUES = {"const": 0, "linear31": 1, "hash": 2}
+ORDERS = {"rowmajor": 0, "interleaved": 1}
+STORES = {"auto": 0, "scatter": 1, "staged": 2}
+
+
+class LaunchOpts(ctypes.Structure):
+    """sg_launch_opts of include/sg.h."""
+    _fields_ = [("order", ctypes.c_int), ("store", ctypes.c_int),
+                ("ctas_per_sm", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+
+
+def launch_opts(order=None, store=None, ctas_per_sm=None):
+    """An sg_launch_opts (or None when every field is the default)."""
+    if order is None and store is None and ctas_per_sm is None:
+        return None
+    o = LaunchOpts()
+    o.order = -1 if order is None else (ORDERS[order] if isinstance(order, str) else int(order))
+    o.store = 0 if store is None else (STORES[store] if isinstance(store, str) else int(store))
+    o.ctas_per_sm = 0 if ctas_per_sm is None else int(ctas_per_sm)
+    return o
 
 _lock = threading.Lock()
 _lib = None
@@ -73,8 +93,15 @@ def lib() -> ctypes.CDLL:
         L.sg_ca_step.restype = i32
         L.sg_diffuse_step.argtypes = [i32, i32, i32, vp, vp, ctypes.c_float, vp]
         L.sg_diffuse_step.restype = i32
-        L.sg_block_map.argtypes = [i32, vp, vp, vp]
+        L.sg_block_map.argtypes = [i32, i32, vp, vp, vp]
         L.sg_block_map.restype = i32
+        p_opts = ctypes.POINTER(LaunchOpts)
+        L.sg_map_write_ex.argtypes = [i32, i32, i32, i32, vp, i32, u64, p_opts, vp]
+        L.sg_map_write_ex.restype = i32
+        L.sg_ca_step_ex.argtypes = [i32, i32, i32, vp, vp, p_opts, vp]
+        L.sg_ca_step_ex.restype = i32
+        L.sg_diffuse_step_ex.argtypes = [i32, i32, i32, vp, vp, ctypes.c_float, p_opts, vp]
+        L.sg_diffuse_step_ex.restype = i32
         L.sg_launch_stats.argtypes = [i32, i32, i32, p_u64, p_u64]
         L.sg_launch_stats.restype = i32
         L.sg_status_str.argtypes = [i32]
@@ -117,8 +144,27 @@ def sg_diffuse_step(r, rho, map_kind, in_ptr, out_ptr, alpha, stream=0) -> int:
     return int(lib().sg_diffuse_step(r, rho, map_kind, in_ptr, out_ptr, alpha, stream))
 
 
-def sg_block_map(rb, bx_ptr, by_ptr, stream=0) -> int:
-    return int(lib().sg_block_map(rb, bx_ptr, by_ptr, stream))
+def sg_map_write_ex(r, rho, map_kind, dtype, grid_ptr, value_kind, value_or_seed,
+                    opts=None, stream=0) -> int:
+    return int(lib().sg_map_write_ex(r, rho, map_kind, dtype, grid_ptr, value_kind,
+                                     value_or_seed & (2**64 - 1), _opts_ref(opts), stream))
+
+
+def sg_ca_step_ex(r, rho, map_kind, in_ptr, out_ptr, opts=None, stream=0) -> int:
+    return int(lib().sg_ca_step_ex(r, rho, map_kind, in_ptr, out_ptr, _opts_ref(opts), stream))
+
+
+def sg_diffuse_step_ex(r, rho, map_kind, in_ptr, out_ptr, alpha, opts=None, stream=0) -> int:
+    return int(lib().sg_diffuse_step_ex(r, rho, map_kind, in_ptr, out_ptr, alpha,
+                                        _opts_ref(opts), stream))
+
+
+def sg_block_map(rb, order, bx_ptr, by_ptr, stream=0) -> int:
+    return int(lib().sg_block_map(rb, order, bx_ptr, by_ptr, stream))
+
+
+def _opts_ref(opts):
+    return None if opts is None else ctypes.byref(opts)
 
 
 def sg_launch_stats(r, rho, map_kind):
@@ -140,6 +186,22 @@ def _stream_handle(t, stream):
     return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
 
 
+class _NoDeviceSwitch:
+    def __enter__(self):
+        return None
+
+    def __exit__(self, *exc):
+        return False
+
+
+def _on_device(t):
+    """Make t's device current for the call (skipped when it already is)."""
+    import torch
+    if t.device.index is None or t.device.index == torch.cuda.current_device():
+        return _NoDeviceSwitch()
+    return torch.cuda.device(t.device)
+
+
 def _grid_check(t, r, dtypes, name):
     import torch
     n = 1 << r
@@ -152,20 +214,22 @@ def _grid_check(t, r, dtypes, name):
 
 
 def map_write(grid, r: int, rho: int, map="lambda", value="hash", value_or_seed=1,
-              stream=None):
+              stream=None, order=None, store=None, ctas_per_sm=None):
     """Map-and-write pass on a CUDA tensor (uint8 or float32, n*n elements)."""
     import torch
     _grid_check(grid, r, (torch.uint8, torch.float32), "grid")
     dt = DTYPES["u8"] if grid.dtype == torch.uint8 else DTYPES["f32"]
     vk = VALUES[value] if isinstance(value, str) else int(value)
-    with torch.cuda.device(grid.device):
-        _check("sg_map_write", sg_map_write(r, rho, _map_id(map), dt, grid.data_ptr(), vk,
-                                            value_or_seed, _stream_handle(grid, stream)))
+    opts = launch_opts(order, store, ctas_per_sm)
+    with _on_device(grid):
+        _check("sg_map_write", sg_map_write_ex(r, rho, _map_id(map), dt, grid.data_ptr(), vk,
+                                               value_or_seed, opts,
+                                               _stream_handle(grid, stream)))
     return grid
 
 
 def map_write_host(host_grid, dev_grid, r: int, rho: int, map="lambda", value="hash",
-                   value_or_seed=1, stream=None):
+                   value_or_seed=1, stream=None, order=None, store=None):
     """Write pass on a grid that lives in host memory: copies ``host_grid``
     (a pinned CPU tensor) into the caller's device buffer ``dev_grid``,
     launches the pass, and copies the result back, all on one stream.
@@ -179,42 +243,46 @@ def map_write_host(host_grid, dev_grid, r: int, rho: int, map="lambda", value="h
     st = stream if stream is not None else torch.cuda.current_stream(dev_grid.device)
     with torch.cuda.stream(st):
         dev_grid.copy_(host_grid, non_blocking=True)
-        map_write(dev_grid, r, rho, map, value, value_or_seed, st)
+        map_write(dev_grid, r, rho, map, value, value_or_seed, st, order=order, store=store)
         host_grid.copy_(dev_grid, non_blocking=True)
     return host_grid
 
 
-def ca_step(inp, out, r: int, rho: int, map="lambda", stream=None):
+def ca_step(inp, out, r: int, rho: int, map="lambda", stream=None, order=None,
+            ctas_per_sm=None):
     import torch
     _grid_check(inp, r, (torch.uint8,), "in")
     _grid_check(out, r, (torch.uint8,), "out")
-    with torch.cuda.device(inp.device):
-        _check("sg_ca_step", sg_ca_step(r, rho, _map_id(map), inp.data_ptr(),
-                                        out.data_ptr(), _stream_handle(inp, stream)))
+    opts = launch_opts(order, None, ctas_per_sm)
+    with _on_device(inp):
+        _check("sg_ca_step", sg_ca_step_ex(r, rho, _map_id(map), inp.data_ptr(),
+                                           out.data_ptr(), opts, _stream_handle(inp, stream)))
     return out
 
 
 def diffuse_step(inp, out, r: int, rho: int, alpha: float = 0.2, map="lambda",
-                 stream=None):
+                 stream=None, order=None, ctas_per_sm=None):
     import torch
     _grid_check(inp, r, (torch.float32,), "in")
     _grid_check(out, r, (torch.float32,), "out")
-    with torch.cuda.device(inp.device):
-        _check("sg_diffuse_step", sg_diffuse_step(r, rho, _map_id(map), inp.data_ptr(),
-                                                  out.data_ptr(), float(alpha),
-                                                  _stream_handle(inp, stream)))
+    opts = launch_opts(order, None, ctas_per_sm)
+    with _on_device(inp):
+        _check("sg_diffuse_step", sg_diffuse_step_ex(r, rho, _map_id(map), inp.data_ptr(),
+                                                     out.data_ptr(), float(alpha), opts,
+                                                     _stream_handle(inp, stream)))
     return out
 
 
-def block_map(rb: int, device="cuda", stream=None):
+def block_map(rb: int, order="interleaved", device="cuda", stream=None):
     """Run the device lambda decode for every launch index; returns (bx, by)
     as uint32-valued int32 CUDA tensors (bit patterns, all values < 2^16)."""
     import torch
     total = 3 ** rb
     bx = torch.empty(total, dtype=torch.int32, device=device)
     by = torch.empty(total, dtype=torch.int32, device=device)
-    with torch.cuda.device(bx.device):
-        _check("sg_block_map", sg_block_map(rb, bx.data_ptr(), by.data_ptr(),
+    oid = ORDERS[order] if isinstance(order, str) else int(order)
+    with _on_device(bx):
+        _check("sg_block_map", sg_block_map(rb, oid, bx.data_ptr(), by.data_ptr(),
                                             _stream_handle(bx, stream)))
     return bx, by
 

@@ -45,20 +45,50 @@ bool valid_level_tile(int r, int rho, int *s)
 
 bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0; }
 
+// Library defaults: the measured best on GB300.
+constexpr int kDefaultOrder = kOrderInterleaved;
+
+// Translate sg_launch_opts (NULL = defaults) into a LaunchCfg.
+bool read_opts(const sg_launch_opts *o, LaunchCfg *cfg)
+{
+    cfg->order = kDefaultOrder;
+    cfg->store = kStoreAuto;
+    cfg->ctas_per_sm = 0;
+    if (o == nullptr) return true;
+    for (int v : o->reserved)
+        if (v != 0) return false;
+    if (o->order != -1) {
+        if (o->order != SG_ORDER_ROWMAJOR && o->order != SG_ORDER_INTERLEAVED) return false;
+        cfg->order = o->order;
+    }
+    if (o->store < SG_STORE_AUTO || o->store > SG_STORE_STAGED) return false;
+    cfg->store = o->store;
+    if (o->ctas_per_sm < 0 || o->ctas_per_sm > 64) return false;
+    cfg->ctas_per_sm = o->ctas_per_sm;
+    return true;
+}
+
+sg_status finish(cudaError_t e)
+{
+    if (e == cudaSuccess) return SG_OK;
+    if (e == cudaErrorNotSupported) return SG_EUNSUPPORTED;
+    return fail_cuda(e);
+}
+
 // One warp per launch index; lane results of the reduction are identical,
 // lane 0 stores them.
 __global__ void __launch_bounds__(256)
 block_map_kernel(uint32_t *__restrict__ bx, uint32_t *__restrict__ by, int rb,
-                 uint32_t total, uint32_t W)
+                 int order, uint32_t total)
 {
     const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
     LambdaLane ll;
-    ll.init(threadIdx.x & 31, rb);
+    ll.init(threadIdx.x & 31, rb, order);
     OmegaWalker ow;
-    ow.init(warp, nwarps, W);
+    ow.init(warp, nwarps, pi_word(order, rb));
     for (uint32_t q = warp; q < total; q += nwarps) {
-        const uint2 b = ll.decode(ow.wx, ow.wy);
+        const uint2 b = ll.decode(ow.a, ow.b);
         ow.advance();
         if ((threadIdx.x & 31) == 0) {
             bx[q] = b.x;
@@ -85,15 +115,15 @@ int sm_count(int *err)
     return c;
 }
 
-cudaError_t launch_block_map(int rb, uint32_t *bx, uint32_t *by, cudaStream_t st)
+cudaError_t launch_block_map(int rb, int order, uint32_t *bx, uint32_t *by, cudaStream_t st)
 {
     const uint32_t total = (uint32_t)pow3i(rb);
-    const uint32_t W = (uint32_t)pow3i(rb / 2);
     LaunchCfg cfg;
     unsigned grid = 1;
-    cudaError_t e = persistent_grid(block_map_kernel, 256, 0, (total + 7) / 8, cfg, &grid);
+    static std::atomic<int> occ{0};
+    cudaError_t e = persistent_grid(block_map_kernel, 256, 0, (total + 7) / 8, cfg, &grid, &occ);
     if (e != cudaSuccess) return e;
-    block_map_kernel<<<grid, 256, 0, st>>>(bx, by, rb, total, W);
+    block_map_kernel<<<grid, 256, 0, st>>>(bx, by, rb, order, total);
     return cudaGetLastError();
 }
 
@@ -120,8 +150,9 @@ const char *sg_status_str(sg_status s)
 
 const char *sg_last_error_string(void) { return g_last_error; }
 
-sg_status sg_map_write(int r, int rho, sg_map map, sg_dtype dtype, void *grid,
-                       sg_value_kind value_kind, uint64_t value_or_seed, void *stream)
+sg_status sg_map_write_ex(int r, int rho, sg_map map, sg_dtype dtype, void *grid,
+                          sg_value_kind value_kind, uint64_t value_or_seed,
+                          const sg_launch_opts *opts, void *stream)
 {
     int s = 0;
     if (!valid_level_tile(r, rho, &s)) return SG_EINVAL;
@@ -129,22 +160,34 @@ sg_status sg_map_write(int r, int rho, sg_map map, sg_dtype dtype, void *grid,
     if (value_kind < SG_VAL_CONST || value_kind > SG_VAL_HASH) return SG_EINVAL;
     if (grid == nullptr) return SG_EINVAL;
     LaunchCfg cfg;
-    cudaError_t e;
-    if (dtype == SG_U8) {
-        e = launch_write_u8(r, s, (int)map, (int)value_kind, (uint8_t *)grid, value_or_seed,
-                            (cudaStream_t)stream, cfg);
-    } else if (dtype == SG_F32) {
-        if (!aligned(grid, 4)) return SG_EINVAL;
-        e = launch_write_f32(r, s, (int)map, (int)value_kind, (float *)grid, value_or_seed,
-                             (cudaStream_t)stream, cfg);
-    } else {
-        return SG_EINVAL;
+    if (!read_opts(opts, &cfg)) return SG_EINVAL;
+    if (dtype != SG_U8 && dtype != SG_F32) return SG_EINVAL;
+    const int elem = dtype == SG_U8 ? 1 : 4;
+    if (!aligned(grid, (uintptr_t)elem)) return SG_EINVAL;
+    // staged stores move whole 16-byte chunks: tile rows of >= 16 bytes and a
+    // 16-byte aligned grid; AUTO falls back to per-cell stores otherwise
+    const bool can_stage = rho * elem >= 16;
+    if (cfg.store == SG_STORE_STAGED) {
+        if (!can_stage) return SG_EUNSUPPORTED;
+        if (!aligned(grid, 16)) return SG_EINVAL;
+    } else if (cfg.store == SG_STORE_AUTO) {
+        cfg.store = (can_stage && aligned(grid, 16)) ? kStoreStaged : kStoreScatter;
     }
-    return e == cudaSuccess ? SG_OK : fail_cuda(e);
+    if (dtype == SG_U8)
+        return finish(launch_write_u8(r, s, (int)map, (int)value_kind, (uint8_t *)grid,
+                                      value_or_seed, (cudaStream_t)stream, cfg));
+    return finish(launch_write_f32(r, s, (int)map, (int)value_kind, (float *)grid,
+                                   value_or_seed, (cudaStream_t)stream, cfg));
 }
 
-sg_status sg_ca_step(int r, int rho, sg_map map, const uint8_t *in, uint8_t *out,
-                     void *stream)
+sg_status sg_map_write(int r, int rho, sg_map map, sg_dtype dtype, void *grid,
+                       sg_value_kind value_kind, uint64_t value_or_seed, void *stream)
+{
+    return sg_map_write_ex(r, rho, map, dtype, grid, value_kind, value_or_seed, nullptr, stream);
+}
+
+sg_status sg_ca_step_ex(int r, int rho, sg_map map, const uint8_t *in, uint8_t *out,
+                        const sg_launch_opts *opts, void *stream)
 {
     int s = 0;
     if (!valid_level_tile(r, rho, &s)) return SG_EINVAL;
@@ -153,12 +196,18 @@ sg_status sg_ca_step(int r, int rho, sg_map map, const uint8_t *in, uint8_t *out
     if (in == nullptr || out == nullptr || in == out) return SG_EINVAL;
     if (!aligned(in, 16) || !aligned(out, 16)) return SG_EINVAL;
     LaunchCfg cfg;
-    cudaError_t e = launch_ca(r, s, (int)map, in, out, (cudaStream_t)stream, cfg);
-    return e == cudaSuccess ? SG_OK : fail_cuda(e);
+    if (!read_opts(opts, &cfg)) return SG_EINVAL;
+    return finish(launch_ca(r, s, (int)map, in, out, (cudaStream_t)stream, cfg));
 }
 
-sg_status sg_diffuse_step(int r, int rho, sg_map map, const float *in, float *out,
-                          float alpha, void *stream)
+sg_status sg_ca_step(int r, int rho, sg_map map, const uint8_t *in, uint8_t *out,
+                     void *stream)
+{
+    return sg_ca_step_ex(r, rho, map, in, out, nullptr, stream);
+}
+
+sg_status sg_diffuse_step_ex(int r, int rho, sg_map map, const float *in, float *out,
+                             float alpha, const sg_launch_opts *opts, void *stream)
 {
     int s = 0;
     if (!valid_level_tile(r, rho, &s)) return SG_EINVAL;
@@ -168,17 +217,23 @@ sg_status sg_diffuse_step(int r, int rho, sg_map map, const float *in, float *ou
     if (!aligned(in, 16) || !aligned(out, 16)) return SG_EINVAL;
     if (!(alpha == alpha) || alpha > 3.0e38f || alpha < -3.0e38f) return SG_EINVAL;
     LaunchCfg cfg;
-    cudaError_t e = launch_diffuse(r, s, (int)map, in, out, alpha, (cudaStream_t)stream, cfg);
-    return e == cudaSuccess ? SG_OK : fail_cuda(e);
+    if (!read_opts(opts, &cfg)) return SG_EINVAL;
+    return finish(launch_diffuse(r, s, (int)map, in, out, alpha, (cudaStream_t)stream, cfg));
 }
 
-sg_status sg_block_map(int rb, uint32_t *bx, uint32_t *by, void *stream)
+sg_status sg_diffuse_step(int r, int rho, sg_map map, const float *in, float *out,
+                          float alpha, void *stream)
+{
+    return sg_diffuse_step_ex(r, rho, map, in, out, alpha, nullptr, stream);
+}
+
+sg_status sg_block_map(int rb, sg_order order, uint32_t *bx, uint32_t *by, void *stream)
 {
     if (rb < 0 || rb > 16) return SG_EINVAL;
+    if (order != SG_ORDER_ROWMAJOR && order != SG_ORDER_INTERLEAVED) return SG_EINVAL;
     if (bx == nullptr || by == nullptr || bx == by) return SG_EINVAL;
     if (!aligned(bx, 4) || !aligned(by, 4)) return SG_EINVAL;
-    cudaError_t e = launch_block_map(rb, bx, by, (cudaStream_t)stream);
-    return e == cudaSuccess ? SG_OK : fail_cuda(e);
+    return finish(launch_block_map(rb, (int)order, bx, by, (cudaStream_t)stream));
 }
 
 sg_status sg_launch_stats(int r, int rho, sg_map map, uint64_t *launched, uint64_t *useful)

@@ -15,43 +15,65 @@ __host__ __device__ constexpr int pow3i(int k) { return k == 0 ? 1 : 3 * pow3i(k
 // ---------------------------------------------------------------------------
 // lambda(omega), Theorem 1, decoded by one warp.
 //
-// Lane l (l < 16) owns level mu = l + 1.  Eq. beta reads omega_y at odd mu
-// (even l) and omega_x at even mu (odd l), digit ceil(mu/2)-1 = l/2 in base
-// 3; Eq. Delta turns the digit into the offset weights (Dx, Dy) =
-// (beta/2, beta - beta/2); Eq. tau scales them by 2^(mu-1); Eq. lambda sums
-// the tau over all levels, which one warp reduction (redux.sync) does: the
-// x part is packed in the low 16 bits and the y part in the high 16 bits of
-// one word, and since every tau is a distinct power of two no carry crosses
-// between lanes or halves.  The result is mirrored into the (x & y) == 0
+// Lane l (l < 16) owns level mu = l + 1.  Eq. beta takes, at level mu, the
+// base-3 digit ceil(mu/2)-1 of omega_y (odd mu) or omega_x (even mu); Eq.
+// Delta turns the digit into the offset weights (Dx, Dy) = (beta/2,
+// beta - beta/2); Eq. tau scales them by 2^(mu-1); Eq. lambda sums the tau
+// over all levels, which one warp reduction (redux.sync) does: the x part is
+// packed in the low 16 bits and the y part in the high 16 bits of one word,
+// and since every tau is a distinct power of two no carry crosses between
+// lanes or halves.  The result is mirrored into the (x & y) == 0
 // orientation: by = n_b - 1 - lambda_y.
 //
-// The per-lane divisor 3^(l/2) is replaced by a fixed-point reciprocal
-// m = ceil(2^32 / 3^k): for w < 3^8 and 3^k <= 3^7, floor(w * m / 2^32) is
-// exactly floor(w / 3^k) because w * (m * 3^k - 2^32) < 2^32.
+// The warp is handed two base-3 words (a, b), each below 3^8, and lane l
+// reads one digit of one of them:
+//   kOrderRowMajor:    (a, b) = (omega_x, omega_y), the paper's Pi walked row
+//                      by row; lane l reads digit l/2 of b (l even) or a.
+//   kOrderInterleaved: (a, b) = (q mod 3^8, q div 3^8) for launch index q, and
+//                      omega is q with its base-3 digits dealt alternately to
+//                      omega_y (even positions) and omega_x (odd positions);
+//                      lane l then reads digit l mod 8 of a (l < 8) or b.
+// Both give beta_mu = the digit Eq. beta names; the second walks Pi so that
+// consecutive launch indices are neighbouring tiles (finest level fastest).
+//
+// The per-lane divisor 3^k (k <= 7) is replaced by a fixed-point reciprocal
+// m = ceil(2^32 / 3^k): for w < 3^8, floor(w * m / 2^32) is exactly
+// floor(w / 3^k) because w * (m * 3^k - 2^32) < 2^32.
 // ---------------------------------------------------------------------------
+enum : int { kOrderRowMajor = 0, kOrderInterleaved = 1 };
+
+constexpr uint32_t kPow3_8 = 6561;   // 3^8: the interleaved order's word size
+
+__host__ __device__ inline uint32_t pi_word(int order, int rb)
+{
+    // the divisor that splits a launch index q into the two words (a, b)
+    return order == kOrderInterleaved ? kPow3_8 : (uint32_t)pow3i(rb / 2);
+}
+
 struct LambdaLane {
-    uint64_t recip;    // ceil(2^32 / 3^(l/2))
+    uint64_t recip;    // ceil(2^32 / 3^digit)
     uint32_t shift;    // mu - 1
-    uint32_t reads_y;  // 1 at odd mu
+    uint32_t reads_b;  // this lane's digit comes from word b
     uint32_t active;   // mu <= rb
     uint32_t nb_m1;    // n_b - 1
 
-    __device__ __forceinline__ void init(int lane, int rb)
+    __device__ __forceinline__ void init(int lane, int rb, int order)
     {
         const int l = lane & 15;
+        const int digit = order == kOrderInterleaved ? (l & 7) : (l >> 1);
         uint64_t p = 1;
-        for (int i = 0; i < (l >> 1); ++i) p *= 3;
+        for (int i = 0; i < digit; ++i) p *= 3;
         recip = ((1ull << 32) + p - 1) / p;
         shift = (uint32_t)l;
-        reads_y = (l & 1) == 0;
+        reads_b = order == kOrderInterleaved ? (l >= 8) : ((l & 1) == 0);
         active = (lane < 16) && (l < rb);
         nb_m1 = (1u << rb) - 1u;
     }
 
-    // Every lane of the warp must call this with the same (wx, wy).
-    __device__ __forceinline__ uint2 decode(uint32_t wx, uint32_t wy) const
+    // Every lane of the warp must call this with the same (a, b).
+    __device__ __forceinline__ uint2 decode(uint32_t a, uint32_t b) const
     {
-        const uint32_t w = reads_y ? wy : wx;
+        const uint32_t w = reads_b ? b : a;
         const uint32_t d = (uint32_t)(((uint64_t)w * recip) >> 32);
         const uint32_t beta = d - 3u * ((d * 0xAAABu) >> 17);   // d mod 3, d < 2^16
         const uint32_t dx = beta >> 1, dy = beta - dx;
@@ -61,25 +83,25 @@ struct LambdaLane {
     }
 };
 
-// The parallel space Pi is walked row by row: q -> omega = (q mod W, q div W)
-// with W = 3^floor(rb/2).  A persistent loop advances q by a fixed stride, so
-// omega is stepped incrementally instead of divided every time.
+// A persistent loop advances the launch index q by a fixed stride; the two
+// words (a, b) = (q mod W, q div W) are stepped incrementally instead of
+// divided every time.
 struct OmegaWalker {
-    uint32_t wx, wy, W, step_x, step_y;
+    uint32_t a, b, W, step_a, step_b;
 
     __device__ __forceinline__ void init(uint32_t q0, uint32_t stride, uint32_t W_)
     {
         W = W_;
-        wy = q0 / W;
-        wx = q0 - wy * W;
-        step_y = stride / W;
-        step_x = stride - step_y * W;
+        b = q0 / W;
+        a = q0 - b * W;
+        step_b = stride / W;
+        step_a = stride - step_b * W;
     }
     __device__ __forceinline__ void advance()
     {
-        wx += step_x;
-        wy += step_y;
-        if (wx >= W) { wx -= W; wy += 1; }
+        a += step_a;
+        b += step_b;
+        if (a >= W) { a -= W; b += 1; }
     }
 };
 

@@ -32,7 +32,7 @@ constexpr uint32_t kNoTile = 0xFFFFFFFFu;
 template <int MAP>
 __device__ __forceinline__ void decode_tiles(uint2 *coord, int tpc, uint64_t g,
                                              uint64_t ntiles, int rb, uint32_t W,
-                                             const LambdaLane &ll)
+                                             const LambdaLane &ll)  // W = pi_word()
 {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int t = warp; t < tpc; t += kStencilThreads / 32) {
@@ -44,8 +44,8 @@ __device__ __forceinline__ void decode_tiles(uint2 *coord, int tpc, uint64_t g,
                 const uint32_t by = (uint32_t)(q >> rb);
                 if ((bx & by) == 0) c = make_uint2(bx, by);
             } else {
-                const uint32_t wy = (uint32_t)q / W, wx = (uint32_t)q - wy * W;
-                c = ll.decode(wx, wy);
+                const uint32_t b = (uint32_t)q / W, a = (uint32_t)q - b * W;
+                c = ll.decode(a, b);
             }
         }
         if (lane == 0) coord[t] = c;
@@ -119,7 +119,7 @@ __device__ __forceinline__ uint32_t life_rule(uint32_t count, uint32_t self, uin
 template <int S, int MAP>
 __global__ void __launch_bounds__(kStencilThreads)
 ca_vec_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int r,
-              uint64_t ntiles, uint32_t W)
+              int order, uint64_t ntiles)
 {
     constexpr int RHO = 1 << S, CPR = RHO / 16, CHUNKS = RHO * CPR;
     constexpr int TPC = CHUNKS >= kStencilThreads ? 1 : kStencilThreads / CHUNKS;
@@ -131,7 +131,8 @@ ca_vec_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int r,
 
     const int rb = r - S;
     LambdaLane ll;
-    ll.init(threadIdx.x & 31, rb);
+    ll.init(threadIdx.x & 31, rb, order);
+    const uint32_t W = pi_word(order, rb);
     const uint64_t groups = (ntiles + TPC - 1) / TPC;
 
     for (uint64_t g = blockIdx.x; g < groups; g += gridDim.x) {
@@ -192,7 +193,7 @@ ca_vec_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int r,
 template <int S, int MAP>
 __global__ void __launch_bounds__(kStencilThreads)
 ca_cell_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int r,
-               uint64_t ntiles, uint32_t W)
+               int order, uint64_t ntiles)
 {
     constexpr int RHO = 1 << S, CELLS = RHO * RHO;
     constexpr int TPC = kStencilThreads / CELLS;
@@ -202,7 +203,8 @@ ca_cell_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int r,
 
     const int rb = r - S;
     LambdaLane ll;
-    ll.init(threadIdx.x & 31, rb);
+    ll.init(threadIdx.x & 31, rb, order);
+    const uint32_t W = pi_word(order, rb);
     const uint64_t groups = (ntiles + TPC - 1) / TPC;
 
     for (uint64_t g = blockIdx.x; g < groups; g += gridDim.x) {
@@ -264,7 +266,7 @@ __device__ __forceinline__ float diffuse_cell(uint32_t x, uint32_t y, uint32_t n
 template <int S, int MAP>
 __global__ void __launch_bounds__(kStencilThreads)
 diffuse_vec_kernel(const float *__restrict__ in, float *__restrict__ out, int r,
-                   uint64_t ntiles, uint32_t W, float alpha)
+                   int order, uint64_t ntiles, float alpha)
 {
     constexpr int RHO = 1 << S, CPR = RHO / 4, CHUNKS = RHO * CPR;
     constexpr int TPC = CHUNKS >= kStencilThreads ? 1 : kStencilThreads / CHUNKS;
@@ -277,7 +279,8 @@ diffuse_vec_kernel(const float *__restrict__ in, float *__restrict__ out, int r,
     const int rb = r - S;
     const uint32_t n = 1u << r;
     LambdaLane ll;
-    ll.init(threadIdx.x & 31, rb);
+    ll.init(threadIdx.x & 31, rb, order);
+    const uint32_t W = pi_word(order, rb);
     const uint64_t groups = (ntiles + TPC - 1) / TPC;
 
     for (uint64_t g = blockIdx.x; g < groups; g += gridDim.x) {
@@ -331,7 +334,7 @@ diffuse_vec_kernel(const float *__restrict__ in, float *__restrict__ out, int r,
 template <int S, int MAP>
 __global__ void __launch_bounds__(kStencilThreads)
 diffuse_cell_kernel(const float *__restrict__ in, float *__restrict__ out, int r,
-                    uint64_t ntiles, uint32_t W, float alpha)
+                    int order, uint64_t ntiles, float alpha)
 {
     constexpr int RHO = 1 << S, CELLS = RHO * RHO;
     constexpr int TPC = kStencilThreads / CELLS;
@@ -342,7 +345,8 @@ diffuse_cell_kernel(const float *__restrict__ in, float *__restrict__ out, int r
     const int rb = r - S;
     const uint32_t n = 1u << r;
     LambdaLane ll;
-    ll.init(threadIdx.x & 31, rb);
+    ll.init(threadIdx.x & 31, rb, order);
+    const uint32_t W = pi_word(order, rb);
     const uint64_t groups = (ntiles + TPC - 1) / TPC;
 
     for (uint64_t g = blockIdx.x; g < groups; g += gridDim.x) {
@@ -405,21 +409,22 @@ cudaError_t launch_ca_t(int r, const uint8_t *in, uint8_t *out, cudaStream_t st,
 {
     const int rb = r - S;
     const uint64_t ntiles = (MAP == kMapBBox) ? (1ull << (2 * rb)) : (uint64_t)pow3i(rb);
-    const uint32_t W = (uint32_t)pow3i(rb / 2);
     constexpr int TPC = StencilShape<S>::CA_TPC;
     const uint64_t groups = (ntiles + TPC - 1) / TPC;
     unsigned grid = 1;
     cudaError_t e;
     if constexpr (S >= 4) {
+        static std::atomic<int> occ{0};
         auto k = ca_vec_kernel<S, MAP>;
-        e = persistent_grid(k, kStencilThreads, 0, groups, cfg, &grid);
+        e = persistent_grid(k, kStencilThreads, 0, groups, cfg, &grid, &occ);
         if (e != cudaSuccess) return e;
-        k<<<grid, kStencilThreads, 0, st>>>(in, out, r, ntiles, W);
+        k<<<grid, kStencilThreads, 0, st>>>(in, out, r, cfg.order, ntiles);
     } else {
+        static std::atomic<int> occ{0};
         auto k = ca_cell_kernel<S, MAP>;
-        e = persistent_grid(k, kStencilThreads, 0, groups, cfg, &grid);
+        e = persistent_grid(k, kStencilThreads, 0, groups, cfg, &grid, &occ);
         if (e != cudaSuccess) return e;
-        k<<<grid, kStencilThreads, 0, st>>>(in, out, r, ntiles, W);
+        k<<<grid, kStencilThreads, 0, st>>>(in, out, r, cfg.order, ntiles);
     }
     return cudaGetLastError();
 }
@@ -430,21 +435,22 @@ cudaError_t launch_diffuse_t(int r, const float *in, float *out, float alpha,
 {
     const int rb = r - S;
     const uint64_t ntiles = (MAP == kMapBBox) ? (1ull << (2 * rb)) : (uint64_t)pow3i(rb);
-    const uint32_t W = (uint32_t)pow3i(rb / 2);
     constexpr int TPC = StencilShape<S>::DF_TPC;
     const uint64_t groups = (ntiles + TPC - 1) / TPC;
     unsigned grid = 1;
     cudaError_t e;
     if constexpr (S >= 2) {
+        static std::atomic<int> occ{0};
         auto k = diffuse_vec_kernel<S, MAP>;
-        e = persistent_grid(k, kStencilThreads, 0, groups, cfg, &grid);
+        e = persistent_grid(k, kStencilThreads, 0, groups, cfg, &grid, &occ);
         if (e != cudaSuccess) return e;
-        k<<<grid, kStencilThreads, 0, st>>>(in, out, r, ntiles, W, alpha);
+        k<<<grid, kStencilThreads, 0, st>>>(in, out, r, cfg.order, ntiles, alpha);
     } else {
+        static std::atomic<int> occ{0};
         auto k = diffuse_cell_kernel<S, MAP>;
-        e = persistent_grid(k, kStencilThreads, 0, groups, cfg, &grid);
+        e = persistent_grid(k, kStencilThreads, 0, groups, cfg, &grid, &occ);
         if (e != cudaSuccess) return e;
-        k<<<grid, kStencilThreads, 0, st>>>(in, out, r, ntiles, W, alpha);
+        k<<<grid, kStencilThreads, 0, st>>>(in, out, r, cfg.order, ntiles, alpha);
     }
     return cudaGetLastError();
 }

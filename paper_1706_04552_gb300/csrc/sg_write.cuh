@@ -1,11 +1,12 @@
 // sg_write.cuh -- the map-and-write pass (Section IV of the paper): every
-// gasket cell of a level-r grid receives v(x, y), nothing else is touched.
+// gasket cell of a level-r grid receives v(x, y), nothing else changes.
 //
-// One persistent kernel template serves the four maps.  A "team" (one warp
-// for rho <= 16, the whole 256-thread CTA for rho >= 32) owns one tile at a
-// time and walks its share of the tile list with a fixed stride:
+// Persistent kernels serve the four maps.  A "team" (one warp, or the whole
+// 256-thread CTA for big tiles) owns one tile at a time and walks its share
+// of the tile list with a fixed stride:
 //   lambda (all three intra-tile variants): the team decodes its tile with
-//     the warp-parallel lambda(omega) of Theorem 1 (LambdaLane);
+//     the warp-parallel lambda(omega) of Theorem 1 (LambdaLane), walking the
+//     block space in the row-major or the digit-interleaved order;
 //   bounding box: tile q is (q mod n_b, q div n_b), the identity map.
 // Inside a tile each thread visits a fixed list of tile-relative offsets,
 // which does not depend on the tile, so it is computed once and kept in
@@ -16,10 +17,20 @@
 //     CTA in shared memory (Section III-D, Shared Lookup Table);
 //   further unrolling: slot e is mapped by lambda applied at thread level
 //     (Section III-D, Further Unrolling).
-// Threads of a warp visit consecutive slots of a tile row, so stores of
-// a warp fall in few 32-byte sectors; u8 stores are byte stores merged by
-// the coalescer (only gasket bytes may change, so a wider store would
-// overwrite cells the pass must leave alone).
+//
+// Two ways to store:
+//   scatter: each thread stores its cells directly.  Only gasket bytes may
+//     change, so stores are per cell and the L2 merges them into partially
+//     written 32-byte sectors, which it must fill from DRAM before writing
+//     back (a read-modify-write per touched sector done by the memory system).
+//   staged: the team loads the tile's touched 16-byte chunks (coalesced),
+//     computes the new values into a shared-memory copy of the tile, merges
+//     them into the loaded chunks under the gasket mask and stores whole
+//     chunks.  Off-gasket bytes are written back with the value just read, so
+//     no other kernel may write the same grid concurrently (the usual rule
+//     for a read-modify-write).  Chunks of one sector are handled together
+//     whenever the sector lies inside one tile, so the L2 sees whole-sector
+//     writes and needs no fill.
 #pragma once
 
 #include "sg_device.cuh"
@@ -29,11 +40,25 @@ namespace sg {
 
 constexpr int kWriteThreads = 256;
 
-template <int S> struct WriteShape {
+template <typename T, int S> struct WriteShape {
     static constexpr int RHO = 1 << S;
     static constexpr int SLOTS = RHO * RHO;
     static constexpr int MEMBERS = pow3i(S);
-    static constexpr int TEAM = (S >= 5) ? kWriteThreads : 32;
+    // staged path
+    static constexpr int ROW_BYTES = RHO * (int)sizeof(T);
+    static constexpr int TILE_BYTES = RHO * ROW_BYTES;
+    static constexpr bool STAGE_OK = ROW_BYTES >= 16;
+    static constexpr int CHUNK_ELEMS = 16 / (int)sizeof(T);
+    static constexpr int CPR = STAGE_OK ? ROW_BYTES / 16 : 1;       // chunks per row
+    static constexpr int CHUNKS = RHO * CPR;
+    static constexpr int GROUP_ELEMS = (ROW_BYTES >= 32 ? 32 : 16) / (int)sizeof(T);
+};
+
+// Team size: one warp while a tile is small, the CTA for big tiles.
+template <typename T, int S, bool STAGED> struct WriteTeam {
+    using WS = WriteShape<T, S>;
+    static constexpr int TEAM = STAGED ? (WS::TILE_BYTES <= 1024 ? 32 : kWriteThreads)
+                                       : (S >= 5 ? kWriteThreads : 32);
 };
 
 // Row-major rank of member slot (tx, ty) among the 3^S members of a level-S
@@ -73,30 +98,15 @@ __device__ __forceinline__ uint32_t unrolled_offset(int e)
     return (uint32_t)lx | ((uint32_t)((1 << S) - 1 - ly) << 8);
 }
 
-template <typename T, int VK, int S, int MAP>
-__global__ void __launch_bounds__(kWriteThreads)
-write_kernel(T *__restrict__ grid, int r, uint64_t vs, uint64_t ntiles, uint32_t W)
+// This thread's tile-independent offsets (tx | ty << 8, or ~0u): slots of the
+// sub-box, or member slots from the lookup table or the unrolled map.
+template <int S, int MAP, int TEAM, int ITERS>
+__device__ __forceinline__ void intra_tile_offsets(uint32_t (&off)[ITERS], int t_in_team,
+                                                   uint16_t *lut)
 {
-    using WS = WriteShape<S>;
-    constexpr int RHO = WS::RHO;
-    constexpr int TEAM = WS::TEAM;
-    constexpr bool SUBBOX = (MAP == kMapLambda || MAP == kMapBBox);
-    constexpr int NSLOT = SUBBOX ? WS::SLOTS : WS::MEMBERS;
-    constexpr int ITERS = (NSLOT + TEAM - 1) / TEAM;
-    constexpr int TEAMS_PER_CTA = kWriteThreads / TEAM;
-
-    const int lane = threadIdx.x & 31;
-    const int t_in_team = threadIdx.x % TEAM;
-    const uint64_t team = (uint64_t)blockIdx.x * TEAMS_PER_CTA + threadIdx.x / TEAM;
-    const uint64_t nteams = (uint64_t)gridDim.x * TEAMS_PER_CTA;
-    const int rb = r - S;
-    const uint64_t seedmix = vs * kGoldenGamma;
-
-    // Tile-independent offsets of this thread: tx | ty << 8, or ~0u if none.
-    uint32_t off[ITERS];
+    constexpr int RHO = 1 << S, SLOTS = RHO * RHO, MEMBERS = pow3i(S);
     if constexpr (MAP == kMapLut) {
-        __shared__ uint16_t lut[WS::MEMBERS];
-        for (int slot = threadIdx.x; slot < WS::SLOTS; slot += kWriteThreads) {
+        for (int slot = threadIdx.x; slot < SLOTS; slot += kWriteThreads) {
             const int tx = slot & (RHO - 1), ty = slot >> S;
             if ((tx & ty) == 0) lut[member_rank<S>(tx, ty)] = (uint16_t)(tx | (ty << 8));
         }
@@ -104,41 +114,80 @@ write_kernel(T *__restrict__ grid, int r, uint64_t vs, uint64_t ntiles, uint32_t
 #pragma unroll
         for (int j = 0; j < ITERS; ++j) {
             const int e = t_in_team + j * TEAM;
-            off[j] = (e < WS::MEMBERS) ? (uint32_t)lut[e] : ~0u;
+            off[j] = (e < MEMBERS) ? (uint32_t)lut[e] : ~0u;
         }
     } else if constexpr (MAP == kMapUnroll) {
 #pragma unroll
         for (int j = 0; j < ITERS; ++j) {
             const int e = t_in_team + j * TEAM;
-            off[j] = (e < WS::MEMBERS) ? unrolled_offset<S>(e) : ~0u;
+            off[j] = (e < MEMBERS) ? unrolled_offset<S>(e) : ~0u;
         }
     } else {
 #pragma unroll
         for (int j = 0; j < ITERS; ++j) {
             const int slot = t_in_team + j * TEAM;
-            off[j] = (slot < WS::SLOTS)
-                         ? (uint32_t)((slot & (RHO - 1)) | ((slot >> S) << 8)) : ~0u;
+            off[j] = (slot < SLOTS) ? (uint32_t)((slot & (RHO - 1)) | ((slot >> S) << 8)) : ~0u;
         }
     }
+}
 
+// Tile walker: the team's sequence of tiles under a map and traversal order.
+template <int MAP>
+struct TileWalker {
     LambdaLane ll;
     OmegaWalker ow;
-    if constexpr (MAP != kMapBBox) {
-        ll.init(lane, rb);
-        ow.init((uint32_t)team, (uint32_t)nteams, W);
-    }
-    for (uint64_t q = team; q < ntiles; q += nteams) {
-        uint32_t bx, by;
-        if constexpr (MAP == kMapBBox) {
-            bx = (uint32_t)(q & ((1ull << rb) - 1));
-            by = (uint32_t)(q >> rb);
-        } else {
-            const uint2 b = ll.decode(ow.wx, ow.wy);
-            bx = b.x;
-            by = b.y;
-            ow.advance();
+    int rb;
+    __device__ __forceinline__ void init(int lane, int rb_, int order, uint64_t team,
+                                         uint64_t nteams)
+    {
+        rb = rb_;
+        if constexpr (MAP != kMapBBox) {
+            ll.init(lane, rb, order);
+            ow.init((uint32_t)team, (uint32_t)nteams, pi_word(order, rb));
         }
-        const uint32_t x0 = bx << S, y0 = by << S;
+    }
+    // Block coordinate of tile q (q advances by nteams between calls).
+    __device__ __forceinline__ uint2 next(uint64_t q)
+    {
+        if constexpr (MAP == kMapBBox) {
+            return make_uint2((uint32_t)(q & ((1ull << rb) - 1)), (uint32_t)(q >> rb));
+        } else {
+            const uint2 b = ll.decode(ow.a, ow.b);
+            ow.advance();
+            return b;
+        }
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Scatter stores.
+// ---------------------------------------------------------------------------
+template <typename T, int VK, int S, int MAP>
+__global__ void __launch_bounds__(kWriteThreads)
+write_scatter_kernel(T *__restrict__ grid, int r, int order, uint64_t vs, uint64_t ntiles)
+{
+    using WS = WriteShape<T, S>;
+    constexpr int RHO = WS::RHO;
+    constexpr int TEAM = WriteTeam<T, S, false>::TEAM;
+    constexpr bool SUBBOX = (MAP == kMapLambda || MAP == kMapBBox);
+    constexpr int NSLOT = SUBBOX ? WS::SLOTS : WS::MEMBERS;
+    constexpr int ITERS = (NSLOT + TEAM - 1) / TEAM;
+    constexpr int TEAMS_PER_CTA = kWriteThreads / TEAM;
+    __shared__ uint16_t lut[MAP == kMapLut ? WS::MEMBERS : 1];
+
+    const int t_in_team = threadIdx.x % TEAM;
+    const uint64_t team = (uint64_t)blockIdx.x * TEAMS_PER_CTA + threadIdx.x / TEAM;
+    const uint64_t nteams = (uint64_t)gridDim.x * TEAMS_PER_CTA;
+    const uint64_t seedmix = vs * kGoldenGamma;
+
+    uint32_t off[ITERS];
+    intra_tile_offsets<S, MAP, TEAM, ITERS>(off, t_in_team, lut);
+    TileWalker<MAP> tw;
+    tw.init(threadIdx.x & 31, r - S, order, team, nteams);
+
+    for (uint64_t q = team; q < ntiles; q += nteams) {
+        const uint2 b = tw.next(q);
+        const uint32_t x0 = b.x << S, y0 = b.y << S;
 #pragma unroll
         for (int j = 0; j < ITERS; ++j) {
             if (off[j] == ~0u) continue;
@@ -150,20 +199,153 @@ write_kernel(T *__restrict__ grid, int r, uint64_t vs, uint64_t ntiles, uint32_t
     }
 }
 
-template <typename T, int VK, int S, int MAP>
-cudaError_t launch_write_t(int r, T *grid, uint64_t vs, cudaStream_t st,
-                           const LaunchCfg &cfg)
+// ---------------------------------------------------------------------------
+// Staged stores.
+// ---------------------------------------------------------------------------
+// Gasket mask of a 16-byte chunk starting at column xc (a multiple of the
+// chunk width) on row y, as byte lanes of 0xFF (u8) or element lanes (f32).
+__device__ __forceinline__ uint4 chunk_mask_u8(uint32_t xc, uint32_t y)
 {
-    using WS = WriteShape<S>;
+    if ((xc & y) != 0u) return make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t yl = y & 15u;
+    uint32_t w = 0xFFFFFFFFu;
+    if (yl & 1u) w &= 0x00FF00FFu;
+    if (yl & 2u) w &= 0x0000FFFFu;
+    uint4 m = make_uint4(w, w, w, w);
+    if (yl & 4u) { m.y = 0u; m.w = 0u; }
+    if (yl & 8u) { m.z = 0u; m.w = 0u; }
+    return m;
+}
+
+__device__ __forceinline__ uint4 chunk_mask_f32(uint32_t xc, uint32_t y)
+{
+    return make_uint4(in_gasket(xc, y) ? ~0u : 0u, in_gasket(xc + 1u, y) ? ~0u : 0u,
+                      in_gasket(xc + 2u, y) ? ~0u : 0u, in_gasket(xc + 3u, y) ? ~0u : 0u);
+}
+
+template <typename T>
+__device__ __forceinline__ uint4 chunk_mask(uint32_t xc, uint32_t y)
+{
+    if constexpr (sizeof(T) == 1) return chunk_mask_u8(xc, y);
+    else return chunk_mask_f32(xc, y);
+}
+
+__device__ __forceinline__ uint4 merge4(uint4 old, uint4 nw, uint4 m)
+{
+    return make_uint4((old.x & ~m.x) | (nw.x & m.x), (old.y & ~m.y) | (nw.y & m.y),
+                      (old.z & ~m.z) | (nw.z & m.z), (old.w & ~m.w) | (nw.w & m.w));
+}
+
+template <int TEAM>
+__device__ __forceinline__ void team_sync()
+{
+    if constexpr (TEAM == 32) __syncwarp();
+    else __syncthreads();
+}
+
+template <typename T, int VK, int S, int MAP>
+__global__ void __launch_bounds__(kWriteThreads)
+write_staged_kernel(T *__restrict__ grid, int r, int order, uint64_t vs, uint64_t ntiles)
+{
+    using WS = WriteShape<T, S>;
+    static_assert(WS::STAGE_OK, "staged stores need tile rows of at least 16 bytes");
+    constexpr int RHO = WS::RHO;
+    constexpr int TEAM = WriteTeam<T, S, true>::TEAM;
+    constexpr bool SUBBOX = (MAP == kMapLambda || MAP == kMapBBox);
+    constexpr int NSLOT = SUBBOX ? WS::SLOTS : WS::MEMBERS;
+    constexpr int ITERS = (NSLOT + TEAM - 1) / TEAM;
+    constexpr int CPT = (WS::CHUNKS + TEAM - 1) / TEAM;      // chunks per thread
+    constexpr int TEAMS_PER_CTA = kWriteThreads / TEAM;
+    __shared__ uint16_t lut[MAP == kMapLut ? WS::MEMBERS : 1];
+    __shared__ __align__(16) T tile[TEAMS_PER_CTA][WS::SLOTS];
+
+    const int t_in_team = threadIdx.x % TEAM;
+    const int team_in_cta = threadIdx.x / TEAM;
+    const uint64_t team = (uint64_t)blockIdx.x * TEAMS_PER_CTA + team_in_cta;
+    const uint64_t nteams = (uint64_t)gridDim.x * TEAMS_PER_CTA;
+    const uint64_t seedmix = vs * kGoldenGamma;
+    T *my = tile[team_in_cta];
+
+    uint32_t off[ITERS];
+    intra_tile_offsets<S, MAP, TEAM, ITERS>(off, t_in_team, lut);
+    TileWalker<MAP> tw;
+    tw.init(threadIdx.x & 31, r - S, order, team, nteams);
+
+    for (uint64_t q = team; q < ntiles; q += nteams) {
+        const uint2 b = tw.next(q);
+        const uint32_t x0 = b.x << S, y0 = b.y << S;
+
+        // 1. issue the loads of this thread's touched chunks
+        uint4 old[CPT];
+        bool act[CPT];
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+            const int c = t_in_team + k * TEAM;
+            const int row = c / WS::CPR, cx = c % WS::CPR;
+            const uint32_t xc = x0 + (uint32_t)(cx * WS::CHUNK_ELEMS), y = y0 + (uint32_t)row;
+            const uint32_t xg = xc & ~(uint32_t)(WS::GROUP_ELEMS - 1);   // its sector group
+            act[k] = (c < WS::CHUNKS) && in_gasket(xg, y);
+            old[k] = act[k] ? *reinterpret_cast<const uint4 *>(grid + ((uint64_t)y << r) + xc)
+                            : make_uint4(0u, 0u, 0u, 0u);
+        }
+        // 2. new values into the shared copy of the tile
+        team_sync<TEAM>();        // the previous tile's merge has read `my`
+#pragma unroll
+        for (int j = 0; j < ITERS; ++j) {
+            if (off[j] == ~0u) continue;
+            const uint32_t tx = off[j] & (RHO - 1), ty = (off[j] >> 8) & (RHO - 1);
+            const uint32_t x = x0 + tx, y = y0 + ty;
+            if (SUBBOX && !in_gasket(x, y)) continue;
+            my[ty * RHO + tx] = Value<T>::template at<VK>(x, y, r, vs, seedmix);
+        }
+        team_sync<TEAM>();
+        // 3. merge under the gasket mask and store whole chunks
+#pragma unroll
+        for (int k = 0; k < CPT; ++k) {
+            if (!act[k]) continue;
+            const int c = t_in_team + k * TEAM;
+            const int row = c / WS::CPR, cx = c % WS::CPR;
+            const uint32_t xc = x0 + (uint32_t)(cx * WS::CHUNK_ELEMS), y = y0 + (uint32_t)row;
+            const uint4 nw = *reinterpret_cast<const uint4 *>(my + row * RHO + cx * WS::CHUNK_ELEMS);
+            *reinterpret_cast<uint4 *>(grid + ((uint64_t)y << r) + xc) =
+                merge4(old[k], nw, chunk_mask<T>(xc, y));
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+template <typename T, int VK, int S, int MAP>
+cudaError_t launch_write_t(int r, T *grid, uint64_t vs, cudaStream_t st, const LaunchCfg &cfg)
+{
     const int rb = r - S;
     const uint64_t ntiles = (MAP == kMapBBox) ? (1ull << (2 * rb)) : (uint64_t)pow3i(rb);
-    const uint32_t W = (uint32_t)pow3i(rb / 2);
-    auto kern = write_kernel<T, VK, S, MAP>;
-    const uint64_t units = (ntiles * WS::TEAM + kWriteThreads - 1) / kWriteThreads;
+    using WS = WriteShape<T, S>;
+    bool staged = false;     // the caller resolved kStoreAuto already
+    if constexpr (WS::STAGE_OK) staged = (cfg.store == kStoreStaged);
     unsigned grid_ctas = 1;
-    cudaError_t e = persistent_grid(kern, kWriteThreads, 0, units, cfg, &grid_ctas);
+    cudaError_t e;
+    if constexpr (WS::STAGE_OK) {
+        if (staged) {
+            constexpr int TEAM = WriteTeam<T, S, true>::TEAM;
+            static std::atomic<int> occ{0};
+            auto kern = write_staged_kernel<T, VK, S, MAP>;
+            const uint64_t units = (ntiles * TEAM + kWriteThreads - 1) / kWriteThreads;
+            e = persistent_grid(kern, kWriteThreads, 0, units, cfg, &grid_ctas, &occ);
+            if (e != cudaSuccess) return e;
+            kern<<<grid_ctas, kWriteThreads, 0, st>>>(grid, r, cfg.order, vs, ntiles);
+            return cudaGetLastError();
+        }
+    }
+    if (cfg.store == kStoreStaged) return cudaErrorNotSupported;
+    constexpr int TEAM = WriteTeam<T, S, false>::TEAM;
+    static std::atomic<int> occ{0};
+    auto kern = write_scatter_kernel<T, VK, S, MAP>;
+    const uint64_t units = (ntiles * TEAM + kWriteThreads - 1) / kWriteThreads;
+    e = persistent_grid(kern, kWriteThreads, 0, units, cfg, &grid_ctas, &occ);
     if (e != cudaSuccess) return e;
-    kern<<<grid_ctas, kWriteThreads, 0, st>>>(grid, r, vs, ntiles, W);
+    kern<<<grid_ctas, kWriteThreads, 0, st>>>(grid, r, cfg.order, vs, ntiles);
     return cudaGetLastError();
 }
 

@@ -20,7 +20,8 @@ WRITE_SWEEP = dict(levels=tuple(range(8, 17)), rhos=(8, 16, 32, 64),
 # The headline: the write pass at n = 2^16 (a 4.3 GB uint8 grid), lambda map.
 # rho and the intra-tile variant are the measured best on GB300.
 WRITE_HEADLINE = dict(r=16, dtype="u8", value="hash", seed=1,
-                      map="lambda_lut", rho=16, bbox_rho=64)
+                      map="lambda_lut", rho=64, order="interleaved", store="staged",
+                      bbox_rho=64)
 
 # Stencils at levels 14 and 15: 256 CA steps from Bernoulli(0.3) seeded with
 # 0; 100 diffusion steps (alpha = 0.2) from U[0,1) seeded with 0.

@@ -81,9 +81,27 @@ def test_bad_pointers_and_enums_are_einval(L):
     assert sg.sg_ca_step(8, 16, 0, FAKE + 8, FAKE + 8192, 0) == sg.SG_EINVAL   # misaligned
     assert sg.sg_diffuse_step(8, 16, 0, FAKE, FAKE + 4, 0.2, 0) == sg.SG_EINVAL
     assert sg.sg_diffuse_step(8, 16, 0, FAKE, FAKE + 8192, float("nan"), 0) == sg.SG_EINVAL
-    assert sg.sg_block_map(17, FAKE, FAKE + 64, 0) == sg.SG_EINVAL
-    assert sg.sg_block_map(4, FAKE, FAKE, 0) == sg.SG_EINVAL
-    assert sg.sg_block_map(4, 0, FAKE, 0) == sg.SG_EINVAL
+    assert sg.sg_block_map(17, 1, FAKE, FAKE + 64, 0) == sg.SG_EINVAL
+    assert sg.sg_block_map(4, 1, FAKE, FAKE, 0) == sg.SG_EINVAL
+    assert sg.sg_block_map(4, 1, 0, FAKE, 0) == sg.SG_EINVAL
+    assert sg.sg_block_map(4, 2, FAKE, FAKE + 64, 0) == sg.SG_EINVAL      # bad order
+
+
+def test_bad_launch_options_are_rejected_before_launch(L):
+    bad = [sg.launch_opts(order=5), sg.launch_opts(store=7), sg.launch_opts(ctas_per_sm=-1),
+           sg.launch_opts(ctas_per_sm=65)]
+    o = sg.launch_opts(order=1)
+    o.reserved[2] = 1
+    bad.append(o)
+    for opts in bad:
+        assert sg.sg_map_write_ex(8, 16, 0, 0, FAKE, 2, 1, opts) == sg.SG_EINVAL
+        assert sg.sg_ca_step_ex(8, 16, 0, FAKE, FAKE + 8192, opts) == sg.SG_EINVAL
+        assert sg.sg_diffuse_step_ex(8, 16, 0, FAKE, FAKE + 8192, 0.2, opts) == sg.SG_EINVAL
+    # staged stores need 16-byte tile rows and a 16-byte aligned grid
+    staged = sg.launch_opts(store="staged")
+    assert sg.sg_map_write_ex(8, 8, 0, 0, FAKE, 2, 1, staged) == sg.SG_EUNSUPPORTED
+    assert sg.sg_map_write_ex(8, 2, 0, 1, FAKE, 2, 1, staged) == sg.SG_EUNSUPPORTED
+    assert sg.sg_map_write_ex(8, 16, 0, 0, FAKE + 1, 2, 1, staged) == sg.SG_EINVAL
 
 
 def test_stencils_reject_intra_block_maps(L):

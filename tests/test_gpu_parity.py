@@ -49,10 +49,11 @@ def max_rel_err(got, want):
 
 # --------------------------------------------------------------- block map
 
+@pytest.mark.parametrize("order", ["rowmajor", "interleaved"])
 @pytest.mark.parametrize("rb", list(range(0, 13)) + [16])
-def test_block_map_bit_exact(orc, rb):
-    bx, by = sg.block_map(rb)
-    ebx, eby = orc.block_map(rb)
+def test_block_map_bit_exact(orc, rb, order):
+    bx, by = sg.block_map(rb, order)
+    ebx, eby = orc.block_map(rb, sg.ORDERS[order])
     torch.cuda.synchronize()
     assert np.array_equal(bx.cpu().numpy().view(np.uint32), ebx)
     assert np.array_equal(by.cpu().numpy().view(np.uint32), eby)
@@ -86,6 +87,35 @@ def test_write_matches_oracle(orc, r, mapk, dtype):
             if dtype == "f32":
                 got, want = got.view(np.uint32), want.view(np.uint32)
             assert np.array_equal(got, want), (r, rho, mapk, vname)
+
+
+@pytest.mark.parametrize("dtype", ["u8", "f32"])
+@pytest.mark.parametrize("r", [4, 9, 11])
+def test_write_every_order_and_store(orc, r, dtype):
+    # both walking orders of Pi and both store paths, every map and rho
+    n = 1 << r
+    rng = np.random.default_rng(300 + r)
+    if dtype == "u8":
+        before = rng.integers(0, 256, (n, n), dtype=np.uint8)
+    else:
+        before = (rng.standard_normal((n, n)) - 5.0).astype(np.float32)
+    want = before.copy()
+    orc.map_write(r, want, orc.VAL_HASH, 3)
+    elem = 1 if dtype == "u8" else 4
+    for mapk in ALL_MAPS:
+        for rho in rhos_for(r):
+            for order in ("rowmajor", "interleaved"):
+                for store in ("scatter", "staged"):
+                    if store == "staged" and rho * elem < 16:
+                        continue
+                    g = to_dev(before)
+                    sg.map_write(g, r, rho, mapk, "hash", 3, order=order, store=store)
+                    got = to_host(g, n)
+                    if dtype == "f32":
+                        ok = np.array_equal(got.view(np.uint32), want.view(np.uint32))
+                    else:
+                        ok = np.array_equal(got, want)
+                    assert ok, (mapk, rho, order, store)
 
 
 @pytest.mark.parametrize("mapk", ALL_MAPS)
@@ -142,7 +172,8 @@ def test_write_level16_headline_u8_whole_grid(orc):
     r, n = w["r"], 1 << w["r"]
     g = _headline_grid("u8", 11)
     before = g.cpu().numpy().reshape(n, n)
-    sg.map_write(g, r, w["rho"], w["map"], w["value"], w["seed"])
+    sg.map_write(g, r, w["rho"], w["map"], w["value"], w["seed"], order=w["order"],
+                 store=w["store"])
     got = to_host(g, n)
     orc.map_write(r, before, orc.VAL_HASH, w["seed"])
     assert np.array_equal(got, before)
@@ -156,7 +187,8 @@ def test_write_level16_headline_f32_whole_grid_in_bands(orc):
     g2 = g.view(n, n)
     band = 4096
     before = [g2[y:y + band].cpu().numpy() for y in range(0, n, band)]
-    sg.map_write(g, r, w["rho"], w["map"], w["value"], w["seed"])
+    sg.map_write(g, r, w["rho"], w["map"], w["value"], w["seed"], order=w["order"],
+                 store=w["store"])
     torch.cuda.synchronize()
     for i, y in enumerate(range(0, n, band)):
         want = before[i]
@@ -208,11 +240,11 @@ def test_write_level16_sweep_sampled(orc, rho, mapk, dtype):
 
 # ---------------------------------------------------------------------- CA
 
-def _run_ca(state, r, rho, mapk, steps, check=None):
+def _run_ca(state, r, rho, mapk, steps, check=None, order=None):
     a = to_dev(state)
     b = torch.zeros_like(a)
     for t in range(steps):
-        sg.ca_step(a, b, r, rho, mapk)
+        sg.ca_step(a, b, r, rho, mapk, order=order)
         a, b = b, a
         if check is not None:
             check(t + 1, a)
@@ -238,10 +270,11 @@ def test_small_config_write_then_ca_bit_exact(orc, mapk):
     _run_ca(s, r, rho, mapk, w["ca_steps"], check)
 
 
+@pytest.mark.parametrize("order", ["rowmajor", "interleaved"])
 @pytest.mark.parametrize("mapk", STENCIL_MAPS)
 @pytest.mark.parametrize("r,p", [(0, 1.0), (1, 1.0), (2, 0.5), (4, 0.5), (6, 0.4),
                                  (9, 0.5), (12, 0.3)])
-def test_ca_matches_oracle_every_rho(orc, r, p, mapk):
+def test_ca_matches_oracle_every_rho(orc, r, p, mapk, order):
     n = 1 << r
     s0 = inputs.ca_seed_grid(r, p, 3)
     steps = 6
@@ -251,7 +284,7 @@ def test_ca_matches_oracle_every_rho(orc, r, p, mapk):
     for rho in rhos_for(r):
         def check(t, a, rho=rho):
             assert np.array_equal(to_host(a, n), ref[t]), (rho, t)
-        _run_ca(s0, r, rho, mapk, steps, check)
+        _run_ca(s0, r, rho, mapk, steps, check, order)
 
 
 def _offgasket_zero(t, r):
@@ -312,25 +345,26 @@ def test_ca_full_size_light_cones(orc, r):
 
 # --------------------------------------------------------------- diffusion
 
-def _run_diffusion(u0, r, rho, mapk, steps, alpha=0.2):
+def _run_diffusion(u0, r, rho, mapk, steps, alpha=0.2, order=None):
     a = to_dev(u0)
     b = torch.zeros_like(a)
     for _ in range(steps):
-        sg.diffuse_step(a, b, r, rho, alpha, mapk)
+        sg.diffuse_step(a, b, r, rho, alpha, mapk, order=order)
         a, b = b, a
     return a
 
 
+@pytest.mark.parametrize("order", ["rowmajor", "interleaved"])
 @pytest.mark.parametrize("mapk", STENCIL_MAPS)
 @pytest.mark.parametrize("r", [0, 1, 2, 5, 8, 11])
-def test_diffusion_matches_fp64_oracle_every_rho(orc, r, mapk):
+def test_diffusion_matches_fp64_oracle_every_rho(orc, r, mapk, order):
     n = 1 << r
     u0 = inputs.uniform_grid(r, 4)
     steps = 12
     want = orc.diffuse_steps(r, u0, steps, 0.2)
     mask = orc.member_grid(r).astype(bool)
     for rho in rhos_for(r):
-        got = to_host(_run_diffusion(u0, r, rho, mapk, steps), n)
+        got = to_host(_run_diffusion(u0, r, rho, mapk, steps, order=order), n)
         assert not got[~mask].any(), rho
         assert max_rel_err(got[mask], want[mask]) <= DIFF_TOL, rho
 

@@ -111,6 +111,37 @@ def test_lambda_is_a_bijection_onto_the_block_gasket(orc, rb):
     assert len(np.unique(keys)) == 3 ** rb
 
 
+@pytest.mark.parametrize("rb", [0, 1, 2, 5, 8, 11])
+def test_interleaved_order_is_a_bijection_of_pi(orc, rb):
+    # dealing q's base-3 digits alternately to omega_y and omega_x visits
+    # every omega of Pi once, so both walking orders launch the same tiles
+    wx_e, wy_e = orc.pi_extent(rb)
+    seen = set()
+    for q in range(3 ** rb):
+        wx, wy = orc.omega_of_index(rb, q, orc.ORDER_INTERLEAVED)
+        assert wx < wx_e and wy < wy_e
+        seen.add((wx, wy))
+    assert len(seen) == 3 ** rb
+    a = orc.block_map(rb, orc.ORDER_ROWMAJOR)
+    b = orc.block_map(rb, orc.ORDER_INTERLEAVED)
+    ka = set(zip(a[0].tolist(), a[1].tolist()))
+    kb = set(zip(b[0].tolist(), b[1].tolist()))
+    assert ka == kb and len(kb) == 3 ** rb
+
+
+def test_interleaved_order_hand_worked():
+    # rb = 2: q = 3*d1 + d0, omega_y = d0, omega_x = d1; with the rb = 2 table
+    # q = 5 (d0 = 2, d1 = 1): omega = (1, 2) -> lambda = (1, 3)
+    # rb = 4: q = 63 = 2*27 + 1*9 + 0*3 + 0 has digits d0..d3 = 0, 0, 1, 2, so
+    # omega_y = d0 + 3*d2 = 3 and omega_x = d1 + 3*d3 = 6
+    import oracle
+    assert oracle.omega_of_index(2, 5, oracle.ORDER_INTERLEAVED) == (1, 2)
+    assert oracle.omega_of_index(4, 63, oracle.ORDER_INTERLEAVED) == (6, 3)
+    lx, ly = oracle.lambda_paper(2, 1, 2)
+    assert (lx, ly) == (1, 3)
+    assert oracle.block_of_index(2, 5, oracle.ORDER_INTERLEAVED) == (1, 0)
+
+
 @pytest.mark.parametrize("r,s", [(4, 1), (6, 2), (8, 3), (9, 4), (10, 4),
                                  (10, 5), (10, 6), (12, 4)])
 def test_lambda_tiles_are_exactly_the_nonempty_tiles(orc, r, s):
