@@ -71,13 +71,16 @@ class Group:
         self.rank = int(os.environ.get("RANK", "0"))
         self.local = int(os.environ.get("LOCAL_RANK", "0"))
         self.dist = None
+        self.backend = None
         if self.world > 1:
             import torch.distributed as dist
-            backend = "nccl" if _cuda_ok() else "gloo"
-            if backend == "nccl":
+            # SG_BENCH_BACKEND=gloo keeps every rank on the CPU (used by tests)
+            self.backend = os.environ.get("SG_BENCH_BACKEND") or (
+                "nccl" if _cuda_ok() else "gloo")
+            if self.backend == "nccl":
                 import torch
                 torch.cuda.set_device(self.local)
-            dist.init_process_group(backend=backend)
+            dist.init_process_group(backend=self.backend)
             self.dist = dist
 
     def barrier(self):
@@ -88,7 +91,7 @@ class Group:
         if self.dist is None:
             return value
         import torch
-        dev = f"cuda:{self.local}" if _cuda_ok() else "cpu"
+        dev = f"cuda:{self.local}" if self.backend == "nccl" else "cpu"
         t = torch.tensor([value], dtype=torch.float64, device=dev)
         self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
         return float(t.item())
@@ -522,7 +525,8 @@ def main():
         if rank != 0:
             return 0
         grp = Group.__new__(Group)
-        grp.world, grp.rank, grp.local, grp.dist = int(os.environ.get("WORLD_SIZE", "1")), 0, 0, None
+        grp.world, grp.rank, grp.local, grp.dist, grp.backend = (
+            int(os.environ.get("WORLD_SIZE", "1")), 0, 0, None, None)
         print(json.dumps(run_reference(args, grp)))
         return 0
     grp = Group()

@@ -95,8 +95,11 @@ typedef enum { SG_ORDER_ROWMAJOR = 0, SG_ORDER_INTERLEAVED = 1 } sg_order;
 typedef enum {
     SG_STORE_AUTO = 0,      /* the library's choice for dtype and rho */
     SG_STORE_SCATTER = 1,   /* one store per gasket cell */
-    SG_STORE_STAGED = 2     /* whole 16-byte chunks merged in shared memory;
+    SG_STORE_STAGED = 2,    /* whole 16-byte chunks merged in shared memory;
                                needs rho * element size >= 16 bytes */
+    SG_STORE_TMA = 3        /* whole tiles moved by 2-D bulk tensor copies (TMA),
+                               several tiles in flight per team; same
+                               requirement as SG_STORE_STAGED */
 } sg_store;
 
 /* Launch options of the *_ex calls.  Zero-initialise, then set fields. */
@@ -130,10 +133,11 @@ typedef enum {
  *   stream         cudaStream_t
  * Launches one kernel.  Returns SG_OK, SG_EINVAL or SG_ECUDA.
  *
- * With SG_STORE_STAGED (the default where rho * element size >= 16 bytes)
- * off-gasket cells that share a 16-byte chunk with gasket cells are read and
- * written back unchanged, so no other kernel may write `grid` while the pass
- * runs; with SG_STORE_SCATTER only gasket cells are ever stored.
+ * With SG_STORE_STAGED or SG_STORE_TMA (the default is one of them wherever
+ * rho * element size >= 16 bytes and `grid` is 16-byte aligned) the off-gasket
+ * cells of a touched tile are read and written back unchanged, so no other
+ * kernel may write `grid` while the pass runs; with SG_STORE_SCATTER only
+ * gasket cells are ever stored.
  */
 SG_API sg_status sg_map_write(int r, int rho, sg_map map, sg_dtype dtype, void *grid,
                               sg_value_kind value_kind, uint64_t value_or_seed,
@@ -208,6 +212,15 @@ SG_API sg_status sg_block_map(int rb, sg_order order, uint32_t *bx, uint32_t *by
  */
 SG_API sg_status sg_launch_stats(int r, int rho, sg_map map, uint64_t *launched,
                                  uint64_t *useful);
+
+/*
+ * sg_device_status -- report and clear the device status word of the current
+ * device.  Kernels with bounded waits (SG_STORE_TMA) record a wait that gave
+ * up there instead of spinning; the call synchronises `stream` and returns
+ * SG_ETIMEOUT if any kernel recorded one since the last call, else SG_OK
+ * (or SG_ECUDA if the status could not be read).
+ */
+SG_API sg_status sg_device_status(void *stream);
 
 /* Human-readable name of a status code (static storage). */
 SG_API const char *sg_status_str(sg_status status);

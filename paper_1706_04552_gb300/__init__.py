@@ -24,7 +24,8 @@ __all__ = [
     "SGError", "lib", "lib_path",
     "sg_map_write", "sg_ca_step", "sg_diffuse_step", "sg_block_map",
     "sg_map_write_ex", "sg_ca_step_ex", "sg_diffuse_step_ex", "LaunchOpts", "launch_opts",
-    "sg_launch_stats", "sg_status_str", "sg_abi_version",
+    "sg_launch_stats", "sg_status_str", "sg_abi_version", "sg_device_status",
+    "device_status",
     "map_write", "map_write_host", "ca_step", "diffuse_step", "block_map", "launch_stats",
     "MAPS", "DTYPES", "VALUES", "ORDERS", "STORES",
 ]
@@ -37,7 +38,7 @@ MAPS = {"lambda": 0, "bbox": 1, "lambda_lut": 2, "lambda_unroll": 3}
 DTYPES = {"u8": 0, "f32": 1}
 VALUES = {"const": 0, "linear31": 1, "hash": 2}
 ORDERS = {"rowmajor": 0, "interleaved": 1}
-STORES = {"auto": 0, "scatter": 1, "staged": 2}
+STORES = {"auto": 0, "scatter": 1, "staged": 2, "tma": 3}
 
 
 class LaunchOpts(ctypes.Structure):
@@ -108,6 +109,8 @@ def lib() -> ctypes.CDLL:
         L.sg_status_str.restype = ctypes.c_char_p
         L.sg_last_error_string.argtypes = []
         L.sg_last_error_string.restype = ctypes.c_char_p
+        L.sg_device_status.argtypes = [vp]
+        L.sg_device_status.restype = i32
         L.sg_abi_version.argtypes = []
         L.sg_abi_version.restype = i32
         _lib = L
@@ -122,6 +125,19 @@ def sg_status_str(status: int) -> str:
 
 def sg_abi_version() -> int:
     return int(lib().sg_abi_version())
+
+
+def sg_device_status(stream=0) -> int:
+    return int(lib().sg_device_status(stream))
+
+
+def device_status(stream=None):
+    """Raise SGError if a kernel recorded a bounded wait that gave up since
+    the last check (synchronises the stream)."""
+    import torch
+    h = torch.cuda.current_stream().cuda_stream if stream is None else (
+        stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check("sg_device_status", sg_device_status(h))
 
 
 def _check(fn: str, status: int) -> None:

@@ -8,6 +8,7 @@
 #include "sg.h"
 #include "sg_device.cuh"
 #include "sg_internal.h"
+#include "sg_tma.cuh"
 
 namespace sg {
 
@@ -47,6 +48,7 @@ bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0;
 
 // Library defaults: the measured best on GB300.
 constexpr int kDefaultOrder = kOrderInterleaved;
+constexpr int kDefaultWholeTileStore = kStoreTma;
 
 // Translate sg_launch_opts (NULL = defaults) into a LaunchCfg.
 bool read_opts(const sg_launch_opts *o, LaunchCfg *cfg)
@@ -61,7 +63,7 @@ bool read_opts(const sg_launch_opts *o, LaunchCfg *cfg)
         if (o->order != SG_ORDER_ROWMAJOR && o->order != SG_ORDER_INTERLEAVED) return false;
         cfg->order = o->order;
     }
-    if (o->store < SG_STORE_AUTO || o->store > SG_STORE_STAGED) return false;
+    if (o->store < SG_STORE_AUTO || o->store > SG_STORE_TMA) return false;
     cfg->store = o->store;
     if (o->ctas_per_sm < 0 || o->ctas_per_sm > 64) return false;
     cfg->ctas_per_sm = o->ctas_per_sm;
@@ -167,11 +169,11 @@ sg_status sg_map_write_ex(int r, int rho, sg_map map, sg_dtype dtype, void *grid
     // staged stores move whole 16-byte chunks: tile rows of >= 16 bytes and a
     // 16-byte aligned grid; AUTO falls back to per-cell stores otherwise
     const bool can_stage = rho * elem >= 16;
-    if (cfg.store == SG_STORE_STAGED) {
+    if (cfg.store == SG_STORE_STAGED || cfg.store == SG_STORE_TMA) {
         if (!can_stage) return SG_EUNSUPPORTED;
         if (!aligned(grid, 16)) return SG_EINVAL;
     } else if (cfg.store == SG_STORE_AUTO) {
-        cfg.store = (can_stage && aligned(grid, 16)) ? kStoreStaged : kStoreScatter;
+        cfg.store = (can_stage && aligned(grid, 16)) ? kDefaultWholeTileStore : kStoreScatter;
     }
     if (dtype == SG_U8)
         return finish(launch_write_u8(r, s, (int)map, (int)value_kind, (uint8_t *)grid,
@@ -234,6 +236,14 @@ sg_status sg_block_map(int rb, sg_order order, uint32_t *bx, uint32_t *by, void 
     if (bx == nullptr || by == nullptr || bx == by) return SG_EINVAL;
     if (!aligned(bx, 4) || !aligned(by, 4)) return SG_EINVAL;
     return finish(launch_block_map(rb, (int)order, bx, by, (cudaStream_t)stream));
+}
+
+sg_status sg_device_status(void *stream)
+{
+    int status = 0;
+    cudaError_t e = read_device_status(&status, (cudaStream_t)stream);
+    if (e != cudaSuccess) return fail_cuda(e);
+    return status == kDevOk ? SG_OK : SG_ETIMEOUT;
 }
 
 sg_status sg_launch_stats(int r, int rho, sg_map map, uint64_t *launched, uint64_t *useful)

@@ -23,6 +23,13 @@
 //     change, so stores are per cell and the L2 merges them into partially
 //     written 32-byte sectors, which it must fill from DRAM before writing
 //     back (a read-modify-write per touched sector done by the memory system).
+//   tma: a persistent team keeps STAGES-1 whole tiles in flight with 2-D
+//     bulk tensor copies (cp.async.bulk.tensor, completing on mbarriers),
+//     overwrites only the gasket cells of the tile in shared memory and
+//     stores the tile back with a bulk tensor copy.  The read-modify-write is
+//     implicit (off-gasket bytes go back as they came), whole rows of the tile
+//     move, and the loads of later tiles overlap the hashing of this one.
+//     Same concurrency rule as staged stores.
 //   staged: the team loads the tile's touched 16-byte chunks (coalesced),
 //     computes the new values into a shared-memory copy of the tile, merges
 //     them into the loaded chunks under the gasket mask and stores whole
@@ -35,6 +42,7 @@
 
 #include "sg_device.cuh"
 #include "sg_internal.h"
+#include "sg_tma.cuh"
 
 namespace sg {
 
@@ -100,13 +108,13 @@ __device__ __forceinline__ uint32_t unrolled_offset(int e)
 
 // This thread's tile-independent offsets (tx | ty << 8, or ~0u): slots of the
 // sub-box, or member slots from the lookup table or the unrolled map.
-template <int S, int MAP, int TEAM, int ITERS>
+template <int S, int MAP, int TEAM, int ITERS, int CTA_THREADS = kWriteThreads>
 __device__ __forceinline__ void intra_tile_offsets(uint32_t (&off)[ITERS], int t_in_team,
                                                    uint16_t *lut)
 {
     constexpr int RHO = 1 << S, SLOTS = RHO * RHO, MEMBERS = pow3i(S);
     if constexpr (MAP == kMapLut) {
-        for (int slot = threadIdx.x; slot < SLOTS; slot += kWriteThreads) {
+        for (int slot = threadIdx.x; slot < SLOTS; slot += CTA_THREADS) {
             const int tx = slot & (RHO - 1), ty = slot >> S;
             if ((tx & ty) == 0) lut[member_rank<S>(tx, ty)] = (uint16_t)(tx | (ty << 8));
         }
@@ -313,14 +321,164 @@ write_staged_kernel(T *__restrict__ grid, int r, int order, uint64_t vs, uint64_
     }
 }
 
+
+// ---------------------------------------------------------------------------
+// TMA-pipelined stores.
+// ---------------------------------------------------------------------------
+constexpr int kTmaThreads = 128;
+
+template <typename T, int S, int MAP> struct TmaShape {
+    static constexpr int RHO = 1 << S;
+    static constexpr bool OK = RHO * (int)sizeof(T) >= 16;
+    static constexpr int TILE_BYTES = RHO * RHO * (int)sizeof(T);
+    static constexpr int BUF = (TILE_BYTES + 127) / 128 * 128;      // 128-byte aligned slots
+    static constexpr bool SUBBOX = (MAP == kMapLambda || MAP == kMapBBox);
+    static constexpr int NSLOT = SUBBOX ? RHO * RHO : pow3i(S);
+    static constexpr int TEAM = NSLOT > 96 ? kTmaThreads : 32;
+    static constexpr int TEAMS = kTmaThreads / TEAM;
+    static constexpr int ITERS = (NSLOT + TEAM - 1) / TEAM;
+    static constexpr int STAGES = TILE_BYTES <= 1024 ? 6 : (TILE_BYTES <= 4096 ? 4 : 3);
+    static constexpr size_t DSMEM = (size_t)TEAMS * STAGES * BUF + 128;
+};
+
+template <typename T, int VK, int S, int MAP>
+__global__ void __launch_bounds__(kTmaThreads)
+write_tma_kernel(const __grid_constant__ CUtensorMap tmap, int r, int order, uint64_t vs,
+                 uint64_t ntiles, int *status)
+{
+    using TS = TmaShape<T, S, MAP>;
+    constexpr int RHO = TS::RHO, TEAM = TS::TEAM, TEAMS = TS::TEAMS, ST = TS::STAGES;
+    constexpr int ITERS = TS::ITERS;
+    extern __shared__ uint8_t dsm_raw[];
+    __shared__ __align__(8) uint64_t full[TEAMS][ST];
+    __shared__ uint2 coord[TEAMS][ST];
+    __shared__ int abort_team[TEAMS];
+    __shared__ uint16_t lut[MAP == kMapLut ? pow3i(S) : 1];
+
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int tm = tid / TEAM, t = tid % TEAM;
+    const bool producer_warp = t < 32;             // the team's first warp issues copies
+    const uint64_t team = (uint64_t)blockIdx.x * TEAMS + tm;
+    const uint64_t nteams = (uint64_t)gridDim.x * TEAMS;
+    const uint64_t seedmix = vs * kGoldenGamma;
+    uint8_t *dsm = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(dsm_raw) + 127) & ~(uintptr_t)127);
+    uint8_t *buf = dsm + (size_t)tm * ST * TS::BUF;
+
+    uint32_t off[ITERS];
+    intra_tile_offsets<S, MAP, TEAM, ITERS, kTmaThreads>(off, t, lut);
+    if (t == 0) {
+        for (int i = 0; i < ST; ++i) mbar_init(&full[tm][i], 1);
+        abort_team[tm] = 0;
+    }
+    mbar_init_fence();
+    __syncthreads();
+
+    TileWalker<MAP> tw;
+    if (producer_warp) tw.init(lane, r - S, order, team, nteams);
+    const uint64_t cnt = team < ntiles ? (ntiles - team + nteams - 1) / nteams : 0;
+
+    // issue tile k of this team into slot k % ST (warp-collective decode).
+    // A bounding-box tile without gasket cells moves nothing: its slot is
+    // released with a plain arrive and the consumers skip it.
+    auto issue = [&](uint64_t k) {
+        const uint2 b = tw.next(team + k * nteams);
+        if (lane == 0) {
+            const int sn = (int)(k % ST);
+            coord[tm][sn] = b;
+            if (MAP == kMapBBox && (b.x & b.y) != 0u) {
+                mbar_arrive(&full[tm][sn]);
+            } else {
+                mbar_arrive_expect_tx(&full[tm][sn], (uint32_t)TS::TILE_BYTES);
+                tma_load_2d(buf + sn * TS::BUF, &tmap, (int)(b.x << S), (int)(b.y << S),
+                            &full[tm][sn]);
+            }
+        }
+    };
+    if (producer_warp)
+        for (uint64_t k = 0; k + 1 < (uint64_t)ST && k < cnt; ++k) issue(k);
+
+    for (uint64_t k = 0; k < cnt; ++k) {
+        const int sl = (int)(k % ST);
+        const bool got = mbar_wait_bounded(&full[tm][sl], (uint32_t)((k / ST) & 1));
+        if (!got) {
+            abort_team[tm] = 1;
+            record_device_error(status, kDevTimeout);
+        }
+        const uint2 b = coord[tm][sl];
+        const bool empty = MAP == kMapBBox && (b.x & b.y) != 0u;
+        const uint32_t x0 = b.x << S, y0 = b.y << S;
+        T *tile = reinterpret_cast<T *>(buf + sl * TS::BUF);
+        if (got && !empty) {
+#pragma unroll
+            for (int j = 0; j < ITERS; ++j) {
+                if (off[j] == ~0u) continue;
+                const uint32_t tx = off[j] & (RHO - 1), ty = (off[j] >> 8) & (RHO - 1);
+                const uint32_t x = x0 + tx, y = y0 + ty;
+                if (TS::SUBBOX && !in_gasket(x, y)) continue;
+                tile[ty * RHO + tx] = Value<T>::template at<VK>(x, y, r, vs, seedmix);
+            }
+        }
+        fence_proxy_async_shared();
+        team_sync<TEAM>();
+        if (abort_team[tm]) {
+            // a copy never completed: let the ones still in flight land (bounded)
+            // before this block's shared memory goes away
+            // (tiles k .. k+ST-2 were issued; tile k+ST-1 never was)
+            if (t == 0)
+                for (uint64_t kk = k; kk < cnt && kk + 1 < k + ST; ++kk)
+                    (void)mbar_wait_bounded(&full[tm][kk % ST], (uint32_t)((kk / ST) & 1));
+            break;
+        }
+        if (t == 0) {
+            if (!empty) tma_store_2d(&tmap, (int)x0, (int)y0, tile);
+            bulk_commit();              // (an empty group for an empty tile)
+            bulk_wait_read<1>();        // the previous tile's slot is free again
+        }
+        if (producer_warp && k + ST - 1 < cnt) issue(k + ST - 1);
+    }
+    if (t == 0) bulk_wait_all();
+}
+
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+template <typename T, int VK, int S, int MAP>
+cudaError_t launch_write_tma(int r, T *grid, uint64_t vs, uint64_t ntiles, cudaStream_t st,
+                             const LaunchCfg &cfg)
+{
+    using TS = TmaShape<T, S, MAP>;
+    if constexpr (!TS::OK) {
+        return cudaErrorNotSupported;
+    } else {
+        CUtensorMap map;
+        cudaError_t e = make_grid_tensor_map(&map, grid, r, (int)sizeof(T), 1 << S);
+        if (e != cudaSuccess) return e;
+        int *status = nullptr;
+        e = device_status_ptr(&status);
+        if (e != cudaSuccess) return e;
+        auto kern = write_tma_kernel<T, VK, S, MAP>;
+        if (TS::DSMEM > 48 * 1024) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)TS::DSMEM);
+            if (e != cudaSuccess) return e;
+        }
+        static std::atomic<int> occ{0};
+        unsigned grid_ctas = 1;
+        const uint64_t units = (ntiles + TS::TEAMS - 1) / TS::TEAMS;
+        e = persistent_grid(kern, kTmaThreads, TS::DSMEM, units, cfg, &grid_ctas, &occ);
+        if (e != cudaSuccess) return e;
+        kern<<<grid_ctas, kTmaThreads, TS::DSMEM, st>>>(map, r, cfg.order, vs, ntiles, status);
+        return cudaGetLastError();
+    }
+}
+
 template <typename T, int VK, int S, int MAP>
 cudaError_t launch_write_t(int r, T *grid, uint64_t vs, cudaStream_t st, const LaunchCfg &cfg)
 {
     const int rb = r - S;
     const uint64_t ntiles = (MAP == kMapBBox) ? (1ull << (2 * rb)) : (uint64_t)pow3i(rb);
+    if (cfg.store == kStoreTma) return launch_write_tma<T, VK, S, MAP>(r, grid, vs, ntiles, st, cfg);
     using WS = WriteShape<T, S>;
     bool staged = false;     // the caller resolved kStoreAuto already
     if constexpr (WS::STAGE_OK) staged = (cfg.store == kStoreStaged);

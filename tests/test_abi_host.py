@@ -27,7 +27,7 @@ def test_header_declares_the_boundary():
     names = _declared_symbols()
     for want in ("sg_map_write", "sg_ca_step", "sg_diffuse_step", "sg_block_map",
                  "sg_launch_stats", "sg_status_str", "sg_last_error_string",
-                 "sg_abi_version"):
+                 "sg_abi_version", "sg_device_status", "sg_map_write_ex"):
         assert want in names
 
 
@@ -102,6 +102,11 @@ def test_bad_launch_options_are_rejected_before_launch(L):
     assert sg.sg_map_write_ex(8, 8, 0, 0, FAKE, 2, 1, staged) == sg.SG_EUNSUPPORTED
     assert sg.sg_map_write_ex(8, 2, 0, 1, FAKE, 2, 1, staged) == sg.SG_EUNSUPPORTED
     assert sg.sg_map_write_ex(8, 16, 0, 0, FAKE + 1, 2, 1, staged) == sg.SG_EINVAL
+    tma = sg.launch_opts(store="tma")
+    assert sg.sg_map_write_ex(8, 8, 0, 0, FAKE, 2, 1, tma) == sg.SG_EUNSUPPORTED
+    assert sg.sg_map_write_ex(8, 2, 0, 1, FAKE, 2, 1, tma) == sg.SG_EUNSUPPORTED
+    assert sg.sg_map_write_ex(8, 16, 0, 0, FAKE + 8, 2, 1, tma) == sg.SG_EINVAL
+    assert sg.sg_map_write_ex(8, 16, 0, 0, FAKE, 2, 1, sg.launch_opts(store=4)) == sg.SG_EINVAL
 
 
 def test_stencils_reject_intra_block_maps(L):

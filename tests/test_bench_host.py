@@ -1,0 +1,45 @@
+"""Host-side pieces of bench.py: the algorithmic-bytes formula (checked by
+brute force over small grids), the clock-sample summary and the row-band cell
+count of the reference arm."""
+import numpy as np
+import pytest
+
+import bench
+
+
+@pytest.mark.parametrize("r", [5, 7, 9, 10])
+@pytest.mark.parametrize("elem,granule", [(1, 32), (1, 128), (4, 32), (4, 128)])
+def test_touched_bytes_brute_force(orc, r, elem, granule):
+    n = 1 << r
+    per = granule // elem
+    if per > n:
+        pytest.skip("granule wider than the grid")
+    mask = orc.member_grid(r).reshape(n, n // per, per)
+    touched = int(mask.any(axis=2).sum())
+    assert bench.touched_bytes(r, elem, granule) == touched * granule
+
+
+def test_touched_bytes_level16_figures():
+    # the per-launch algorithmic bytes quoted for the headline workload
+    assert bench.touched_bytes(16, 1, 128) == 322_486_272
+    assert bench.touched_bytes(16, 1, 32) == 181_398_528
+    assert bench.touched_bytes(16, 4, 128) == 725_594_112
+    assert bench.touched_bytes(16, 4, 32) == 408_146_688
+
+
+def test_band_cells_match_member_counts(orc):
+    r = 10
+    g = orc.member_grid(r)
+    for y0, y1 in ((0, 64), (100, 300), (512, 1024)):
+        assert bench.band_cells(r, y0, y1) == int(g[y0:y1].sum())
+    assert bench.band_cells(r, 0, 1 << r) == 3 ** r
+
+
+def test_clock_summary():
+    rows = [["0", "2070", "2070", "500.1", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"],
+            ["0", "1980", "2070", "610.0", "0x4", "Not Active", "Not Active", "Not Active", "Active"],
+            ["0", "2070", "2070", "620.0", "0x0", "Not Active", "Not Active", "Not Active", "Not Active"]]
+    s = bench.summarize_clocks(rows)
+    assert s["sm_mhz"] == 2070 and s["sm_max_mhz"] == 2070
+    assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 3
+    assert bench.summarize_clocks([])["samples"] == 0

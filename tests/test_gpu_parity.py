@@ -105,8 +105,8 @@ def test_write_every_order_and_store(orc, r, dtype):
     for mapk in ALL_MAPS:
         for rho in rhos_for(r):
             for order in ("rowmajor", "interleaved"):
-                for store in ("scatter", "staged"):
-                    if store == "staged" and rho * elem < 16:
+                for store in ("scatter", "staged", "tma"):
+                    if store != "scatter" and rho * elem < 16:
                         continue
                     g = to_dev(before)
                     sg.map_write(g, r, rho, mapk, "hash", 3, order=order, store=store)
@@ -116,6 +116,7 @@ def test_write_every_order_and_store(orc, r, dtype):
                     else:
                         ok = np.array_equal(got, want)
                     assert ok, (mapk, rho, order, store)
+    sg.device_status()
 
 
 @pytest.mark.parametrize("mapk", ALL_MAPS)
