@@ -52,7 +52,7 @@ def parse_args():
     p.add_argument("--rho", type=int, default=None)
     p.add_argument("--map", default=None)
     p.add_argument("--order", default=None, choices=("rowmajor", "interleaved"))
-    p.add_argument("--store", default=None, choices=("auto", "scatter", "staged"))
+    p.add_argument("--store", default=None, choices=("auto", "scatter", "staged", "tma", "fill"))
     p.add_argument("--no-extras", action="store_true",
                    help="skip the comparison workloads (bbox, f32, stencils)")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")

@@ -97,9 +97,16 @@ typedef enum {
     SG_STORE_SCATTER = 1,   /* one store per gasket cell */
     SG_STORE_STAGED = 2,    /* whole 16-byte chunks merged in shared memory;
                                needs rho * element size >= 16 bytes */
-    SG_STORE_TMA = 3        /* whole tiles moved by 2-D bulk tensor copies (TMA),
+    SG_STORE_TMA = 3,       /* whole tiles moved by 2-D bulk tensor copies (TMA),
                                several tiles in flight per team; same
                                requirement as SG_STORE_STAGED */
+    SG_STORE_FILL = 4       /* write-only: every tile that holds gasket cells is
+                               written whole, v(x, y) at gasket cells and 0 at
+                               the other cells of the tile; nothing is read.
+                               The result equals the other modes' whenever the
+                               grid is 0 off the gasket (the zero matrix of the
+                               paper's benchmark, the stencils' invariant).
+                               Same requirement as SG_STORE_STAGED. */
 } sg_store;
 
 /* Launch options of the *_ex calls.  Zero-initialise, then set fields. */
@@ -137,7 +144,8 @@ typedef enum {
  * rho * element size >= 16 bytes and `grid` is 16-byte aligned) the off-gasket
  * cells of a touched tile are read and written back unchanged, so no other
  * kernel may write `grid` while the pass runs; with SG_STORE_SCATTER only
- * gasket cells are ever stored.
+ * gasket cells are ever stored.  SG_STORE_FILL (on request only) writes 0 to
+ * the off-gasket cells of every tile that holds gasket cells.
  */
 SG_API sg_status sg_map_write(int r, int rho, sg_map map, sg_dtype dtype, void *grid,
                               sg_value_kind value_kind, uint64_t value_or_seed,

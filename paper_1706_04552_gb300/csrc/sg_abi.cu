@@ -63,7 +63,7 @@ bool read_opts(const sg_launch_opts *o, LaunchCfg *cfg)
         if (o->order != SG_ORDER_ROWMAJOR && o->order != SG_ORDER_INTERLEAVED) return false;
         cfg->order = o->order;
     }
-    if (o->store < SG_STORE_AUTO || o->store > SG_STORE_TMA) return false;
+    if (o->store < SG_STORE_AUTO || o->store > SG_STORE_FILL) return false;
     cfg->store = o->store;
     if (o->ctas_per_sm < 0 || o->ctas_per_sm > 64) return false;
     cfg->ctas_per_sm = o->ctas_per_sm;
@@ -169,7 +169,8 @@ sg_status sg_map_write_ex(int r, int rho, sg_map map, sg_dtype dtype, void *grid
     // staged stores move whole 16-byte chunks: tile rows of >= 16 bytes and a
     // 16-byte aligned grid; AUTO falls back to per-cell stores otherwise
     const bool can_stage = rho * elem >= 16;
-    if (cfg.store == SG_STORE_STAGED || cfg.store == SG_STORE_TMA) {
+    if (cfg.store == SG_STORE_STAGED || cfg.store == SG_STORE_TMA ||
+        cfg.store == SG_STORE_FILL) {
         if (!can_stage) return SG_EUNSUPPORTED;
         if (!aligned(grid, 16)) return SG_EINVAL;
     } else if (cfg.store == SG_STORE_AUTO) {

@@ -106,7 +106,10 @@ def test_bad_launch_options_are_rejected_before_launch(L):
     assert sg.sg_map_write_ex(8, 8, 0, 0, FAKE, 2, 1, tma) == sg.SG_EUNSUPPORTED
     assert sg.sg_map_write_ex(8, 2, 0, 1, FAKE, 2, 1, tma) == sg.SG_EUNSUPPORTED
     assert sg.sg_map_write_ex(8, 16, 0, 0, FAKE + 8, 2, 1, tma) == sg.SG_EINVAL
-    assert sg.sg_map_write_ex(8, 16, 0, 0, FAKE, 2, 1, sg.launch_opts(store=4)) == sg.SG_EINVAL
+    assert sg.sg_map_write_ex(8, 16, 0, 0, FAKE, 2, 1, sg.launch_opts(store=5)) == sg.SG_EINVAL
+    fill = sg.launch_opts(store="fill")
+    assert sg.sg_map_write_ex(8, 8, 0, 0, FAKE, 2, 1, fill) == sg.SG_EUNSUPPORTED
+    assert sg.sg_map_write_ex(8, 16, 0, 0, FAKE + 4, 2, 1, fill) == sg.SG_EINVAL
 
 
 def test_stencils_reject_intra_block_maps(L):

@@ -119,6 +119,46 @@ def test_write_every_order_and_store(orc, r, dtype):
     sg.device_status()
 
 
+@pytest.mark.parametrize("dtype", ["u8", "f32"])
+@pytest.mark.parametrize("r", [4, 9, 11])
+def test_write_fill_on_zero_grid(orc, r, dtype):
+    # write-only tiles: on a grid that is 0 off the gasket the result is the
+    # oracle's pass; on any grid, touched tiles hold v at gasket cells and 0
+    # elsewhere, and untouched tiles keep their content
+    n = 1 << r
+    np_dt = np.uint8 if dtype == "u8" else np.float32
+    zero = np.zeros((n, n), dtype=np_dt)
+    want = zero.copy()
+    orc.map_write(r, want, orc.VAL_HASH, 2)
+    rng = np.random.default_rng(500 + r)
+    noisy = (rng.integers(1, 256, (n, n)) if dtype == "u8"
+             else rng.standard_normal((n, n)) + 10.0).astype(np_dt)
+    elem = 1 if dtype == "u8" else 4
+    for mapk in ALL_MAPS:
+        for rho in rhos_for(r):
+            if rho * elem < 16:
+                continue
+            for order in ("rowmajor", "interleaved"):
+                g = to_dev(zero)
+                sg.map_write(g, r, rho, mapk, "hash", 2, order=order, store="fill")
+                got = to_host(g, n)
+                assert np.array_equal(got.view(np.uint8), want.view(np.uint8)), (mapk, rho, order)
+            g = to_dev(noisy)
+            sg.map_write(g, r, rho, mapk, "hash", 2, store="fill")
+            got = to_host(g, n)
+            nb = n // rho
+            t = got.reshape(nb, rho, nb, rho)
+            ref = noisy.reshape(nb, rho, nb, rho)
+            wt = want.reshape(nb, rho, nb, rho)
+            for by in range(nb):
+                for bx in range(nb):
+                    if bx & by:
+                        assert np.array_equal(t[by, :, bx, :], ref[by, :, bx, :])
+                    else:
+                        assert np.array_equal(t[by, :, bx, :].view(np.uint8),
+                                              wt[by, :, bx, :].view(np.uint8))
+
+
 @pytest.mark.parametrize("mapk", ALL_MAPS)
 def test_write_level12_every_rho(orc, mapk):
     r, n = 12, 4096
