@@ -196,16 +196,18 @@ def measured_peak():
 
 
 def recorded_traffic(kernel_key: str):
-    """DRAM bytes per launch from the committed ncu summary of this kernel,
-    if the library it was measured on is the library built now."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes (read + write) per launch of this kernel from the committed
+    ncu summary profiles/traffic.txt (lines: key, libsg source digest, bytes),
+    or None when the kernel sources changed since that capture."""
+    path = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
-        with open(path) as f:
-            d = json.load(f)
         from paper_1706_04552_gb300 import build as sg_build
-        entry = d.get(kernel_key)
-        if entry and entry.get("libsg_digest") == sg_build._digest():
-            return entry.get("dram_bytes_per_launch")
+        digest = sg_build._digest()
+        with open(path) as f:
+            for line in f:
+                parts = line.split()
+                if len(parts) == 3 and not line.startswith("#") and parts[0] == kernel_key:
+                    return int(parts[2]) if parts[1] == digest else None
     except Exception:
         pass
     return None
@@ -351,24 +353,38 @@ def compare_workloads(sg, torch, dev, stream, w, grid_u8, headline_launch_ms):
     r, n = w["r"], 1 << w["r"]
     cells = 3 ** r
     res = {}
-    # the bounding-box map on the same uint8 grid, at its own best rho
-    for name, mapk, rho, steps in (("bbox_u8", "bbox", w["bbox_rho"], 20),
-                                   ("lambda_subbox_u8", "lambda", w["rho"], 200)):
-        f = lambda: sg.map_write(grid_u8, r, rho, mapk, "hash", w["seed"], stream)
+    # the bounding-box map on the same grid at its own best rho and the same
+    # stores; the lambda pass with stores that keep arbitrary off-gasket
+    # content; the paper's own intra-tile variant (bounding sub-boxes)
+    from paper_1706_04552_gb300 import workloads as wl
+    pv = wl.WRITE_PRESERVE
+    for name, mapk, rho, order, store, steps in (
+            ("bbox_u8", "bbox", w["bbox_rho"], w["order"], w["store"], 20),
+            ("lambda_preserving_u8", pv["map"], pv["rho"], pv["order"], pv["store"], 200),
+            ("lambda_subbox_u8", "lambda", w["rho"], w["order"], w["store"], 200)):
+        f = lambda: sg.map_write(grid_u8, r, rho, mapk, "hash", w["seed"], stream,
+                                 order=order, store=store)
         for _ in range(3):
             f()
+        grid_u8.zero_()
         ms, per = time_launches(f, steps, stream)
-        res[name] = {"map": mapk, "rho": rho, "GCells_s": _rate(cells, ms / steps),
-                     "launch_ms": round(statistics.mean(per), 5)}
+        res[name] = {"map": mapk, "rho": rho, "order": order, "store": store,
+                     "GCells_s": _rate(cells, ms / steps),
+                     "launch_ms": round(statistics.mean(per), 5),
+                     "line_GBps": round(touched_bytes(r, 1, 128) /
+                                        (statistics.mean(per) / 1e3) / 1e9, 1)}
+    grid_u8.zero_()
     res["speedup_lambda_over_bbox"] = round(res["bbox_u8"]["launch_ms"] / headline_launch_ms, 3)
     # float32 grid (17.2 GB)
     g32 = torch.zeros(n * n, dtype=torch.float32, device=dev)
-    f = lambda: sg.map_write(g32, r, w["rho"], w["map"], "hash", w["seed"], stream)
+    f = lambda: sg.map_write(g32, r, w["f32_rho"], w["map"], "hash", w["seed"], stream,
+                             order=w["order"], store=w["store"])
     for _ in range(3):
         f()
     ms, per = time_launches(f, 100, stream)
     lb = touched_bytes(r, 4, 128)
-    res["lambda_f32"] = {"map": w["map"], "rho": w["rho"], "GCells_s": _rate(cells, ms / 100),
+    res["lambda_f32"] = {"map": w["map"], "rho": w["f32_rho"], "store": w["store"],
+                         "GCells_s": _rate(cells, ms / 100),
                          "launch_ms": round(statistics.mean(per), 5),
                          "line_GBps": round(lb / (statistics.mean(per) / 1e3) / 1e9, 1)}
     del g32

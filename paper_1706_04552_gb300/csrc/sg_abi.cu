@@ -48,7 +48,7 @@ bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0;
 
 // Library defaults: the measured best on GB300.
 constexpr int kDefaultOrder = kOrderInterleaved;
-constexpr int kDefaultWholeTileStore = kStoreTma;
+constexpr int kDefaultWholeTileStore = kStoreStaged;
 
 // Translate sg_launch_opts (NULL = defaults) into a LaunchCfg.
 bool read_opts(const sg_launch_opts *o, LaunchCfg *cfg)

@@ -458,7 +458,7 @@ write_fill_kernel(const __grid_constant__ CUtensorMap tmap, int r, int order, ui
     using TS = TmaShape<T, S, MAP>;
     constexpr int RHO = TS::RHO, TEAM = TS::TEAM, TEAMS = TS::TEAMS, ST = TS::STAGES;
     constexpr int ITERS = TS::ITERS;
-    constexpr int VEC16 = TS::TILE_BYTES / 16;                    // 16-byte pieces per tile
+    static_assert(ST >= 2, "the slot ring needs two slots");
     extern __shared__ uint8_t dsm_raw[];
     __shared__ uint16_t lut[MAP == kMapLut ? pow3i(S) : 1];
 
@@ -471,42 +471,46 @@ write_fill_kernel(const __grid_constant__ CUtensorMap tmap, int r, int order, ui
         (reinterpret_cast<uintptr_t>(dsm_raw) + 127) & ~(uintptr_t)127);
     uint8_t *buf = dsm + (size_t)tm * ST * TS::BUF;
 
+    // The gasket cells of a tile sit at the same tile-relative places in
+    // every tile, so each slot is zeroed once here and afterwards only its
+    // gasket cells are rewritten: its other cells stay 0 for the whole pass.
+    for (int i = tid; i < TEAMS * ST * TS::BUF / 16; i += kTmaThreads)
+        reinterpret_cast<uint4 *>(dsm)[i] = make_uint4(0u, 0u, 0u, 0u);
+    fence_proxy_async_shared();        // the zeros are read by other teams' bulk stores too
     uint32_t off[ITERS];
-    intra_tile_offsets<S, MAP, TEAM, ITERS, kTmaThreads>(off, t, lut);
+    intra_tile_offsets<S, MAP, TEAM, ITERS, kTmaThreads>(off, t, lut);   // syncs the CTA
+    if constexpr (MAP != kMapLut) __syncthreads();
     TileWalker<MAP> tw;
     tw.init(lane, r - S, order, team, nteams);
 
+    // Iteration k writes slot k % ST.  Before the barrier of iteration k the
+    // issuing thread has waited (end of iteration k-1) until every store but
+    // the newest ST-2 has read its slot, i.e. through the store of tile
+    // k+1-ST, which is the last tile that used slot (k+1) % ST -- the slot
+    // iteration k+1 writes after that barrier.
     uint64_t k = 0;
     for (uint64_t q = team; q < ntiles; q += nteams, ++k) {
         const uint2 b = tw.next(q);                  // every warp of the team decodes
-        if (MAP == kMapBBox && (b.x & b.y) != 0u) {
-            // nothing to write; an empty bulk group keeps one group per tile,
-            // which the slot-reuse wait below counts on
-            if (t == 0) bulk_commit();
-            continue;
-        }
-        const int sl = (int)(k % ST);
-        uint8_t *tile = buf + sl * TS::BUF;
-        if (t == 0) bulk_wait_read<ST - 1>();       // slot sl's previous store has read it
-        team_sync<TEAM>();
-        for (int i = t; i < VEC16; i += TEAM)
-            reinterpret_cast<uint4 *>(tile)[i] = make_uint4(0u, 0u, 0u, 0u);
-        team_sync<TEAM>();
+        const bool empty = MAP == kMapBBox && (b.x & b.y) != 0u;
         const uint32_t x0 = b.x << S, y0 = b.y << S;
+        uint8_t *tile = buf + (int)(k % ST) * TS::BUF;
+        if (!empty) {
 #pragma unroll
-        for (int j = 0; j < ITERS; ++j) {
-            if (off[j] == ~0u) continue;
-            const uint32_t tx = off[j] & (RHO - 1), ty = (off[j] >> 8) & (RHO - 1);
-            const uint32_t x = x0 + tx, y = y0 + ty;
-            if (TS::SUBBOX && !in_gasket(x, y)) continue;
-            reinterpret_cast<T *>(tile)[ty * RHO + tx] =
-                Value<T>::template at<VK>(x, y, r, vs, seedmix);
+            for (int j = 0; j < ITERS; ++j) {
+                if (off[j] == ~0u) continue;
+                const uint32_t tx = off[j] & (RHO - 1), ty = (off[j] >> 8) & (RHO - 1);
+                const uint32_t x = x0 + tx, y = y0 + ty;
+                if (TS::SUBBOX && !in_gasket(x, y)) continue;
+                reinterpret_cast<T *>(tile)[ty * RHO + tx] =
+                    Value<T>::template at<VK>(x, y, r, vs, seedmix);
+            }
+            fence_proxy_async_shared();
         }
-        fence_proxy_async_shared();
         team_sync<TEAM>();
         if (t == 0) {
-            tma_store_2d(&tmap, (int)x0, (int)y0, tile);
-            bulk_commit();
+            if (!empty) tma_store_2d(&tmap, (int)x0, (int)y0, tile);
+            bulk_commit();                 // one group per tile (empty for an empty tile)
+            bulk_wait_read<ST - 2>();
         }
     }
     if (t == 0) bulk_wait_all();

@@ -208,8 +208,24 @@ def _headline_grid(dtype, seed):
 
 @pytest.mark.slow
 def test_write_level16_headline_u8_whole_grid(orc):
-    # the launch configuration the benchmark times, checked at every cell
+    # the launch configuration and input the benchmark times (a zero grid),
+    # checked at every cell, twice in a row on the same grid
     w = workloads.WRITE_HEADLINE
+    r, n = w["r"], 1 << w["r"]
+    g = torch.zeros(n * n, dtype=torch.uint8, device=DEV)
+    for _ in range(2):
+        sg.map_write(g, r, w["rho"], w["map"], w["value"], w["seed"], order=w["order"],
+                     store=w["store"])
+    got = to_host(g, n)
+    want = np.zeros((n, n), dtype=np.uint8)
+    orc.map_write(r, want, orc.VAL_HASH, w["seed"])
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.slow
+def test_write_level16_preserving_u8_whole_grid(orc):
+    # the preserving stores keep arbitrary off-gasket content at full size
+    w = dict(workloads.WRITE_HEADLINE, **workloads.WRITE_PRESERVE)
     r, n = w["r"], 1 << w["r"]
     g = _headline_grid("u8", 11)
     before = g.cpu().numpy().reshape(n, n)
@@ -221,14 +237,14 @@ def test_write_level16_headline_u8_whole_grid(orc):
 
 
 @pytest.mark.slow
-def test_write_level16_headline_f32_whole_grid_in_bands(orc):
-    w = workloads.WRITE_HEADLINE
+def test_write_level16_preserving_f32_whole_grid_in_bands(orc):
+    w = dict(workloads.WRITE_HEADLINE, **workloads.WRITE_PRESERVE)
     r, n = w["r"], 1 << w["r"]
     g = _headline_grid("f32", 12)
     g2 = g.view(n, n)
     band = 4096
     before = [g2[y:y + band].cpu().numpy() for y in range(0, n, band)]
-    sg.map_write(g, r, w["rho"], w["map"], w["value"], w["seed"], order=w["order"],
+    sg.map_write(g, r, w["f32_rho"], w["map"], w["value"], w["seed"], order=w["order"],
                  store=w["store"])
     torch.cuda.synchronize()
     for i, y in enumerate(range(0, n, band)):
@@ -258,14 +274,17 @@ def _sample_cells(r, count, seed):
     return np.concatenate(xs), np.concatenate(ys)
 
 
+@pytest.mark.parametrize("store", ["auto", "fill"])
 @pytest.mark.parametrize("dtype", ["u8", "f32"])
 @pytest.mark.parametrize("mapk", ALL_MAPS)
 @pytest.mark.parametrize("rho", workloads.WRITE_SWEEP["rhos"])
-def test_write_level16_sweep_sampled(orc, rho, mapk, dtype):
+def test_write_level16_sweep_sampled(orc, rho, mapk, dtype, store):
     r = 16
     n = 1 << r
+    if store == "fill" and rho * (1 if dtype == "u8" else 4) < 16:
+        pytest.skip("fill stores need 16-byte tile rows")
     g = torch.zeros(n * n, dtype=torch.uint8 if dtype == "u8" else torch.float32, device=DEV)
-    sg.map_write(g, r, rho, mapk, "hash", 1)
+    sg.map_write(g, r, rho, mapk, "hash", 1, store=store)
     xs, ys = _sample_cells(r, 100_000, rho)
     idx = torch.from_numpy(ys * n + xs).to(DEV)
     got = g[idx].cpu().numpy()
