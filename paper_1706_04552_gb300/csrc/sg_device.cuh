@@ -119,30 +119,36 @@ __device__ __forceinline__ uint64_t splitmix64(uint64_t s)
     return z ^ (z >> 31);
 }
 
-template <typename T> struct Value;
+// Value of the cell whose linear index (row-major, pitch n = 2^r) is
+// base + koff, for r <= 16 (so the index, which is also the hash key y*n + x,
+// fits in 32 bits).  The write kernels split the index into a per-tile base
+// and a per-thread offset that is the same for every tile, so each cell
+// costs one add before the hash.  For the linear value the split is the
+// same with x*31 + y in place of the index.
+template <typename T, int VK> struct CellValue {
+    uint64_t seedmix;      // seed * gamma
+    uint32_t cval;         // the constant's bits
 
-template <> struct Value<uint8_t> {
-    template <int VK>
-    static __device__ __forceinline__ uint8_t at(uint32_t x, uint32_t y, int r,
-                                                 uint64_t vs, uint64_t seedmix)
+    __device__ __forceinline__ static uint32_t base_of(uint32_t x0, uint32_t y0, int r)
     {
-        if (VK == kValConst) return (uint8_t)vs;
-        if (VK == kValLinear31) return (uint8_t)((x * 31u + y) & 0xFFu);
-        const uint64_t key = ((uint64_t)y << r) | x;
-        return (uint8_t)(splitmix64(seedmix ^ key) >> 56);
+        return VK == kValLinear31 ? x0 * 31u + y0 : (y0 << r) | x0;
     }
-};
-
-template <> struct Value<float> {
-    template <int VK>
-    static __device__ __forceinline__ float at(uint32_t x, uint32_t y, int r,
-                                               uint64_t vs, uint64_t seedmix)
+    __device__ __forceinline__ static uint32_t offset_of(uint32_t tx, uint32_t ty, int r)
     {
-        if (VK == kValConst) return __uint_as_float((uint32_t)vs);
-        if (VK == kValLinear31) return (float)((x * 31u + y) & 0xFFu);
-        const uint64_t key = ((uint64_t)y << r) | x;
-        // a 24-bit integer scaled by 2^-24: exact in float
-        return (float)(uint32_t)(splitmix64(seedmix ^ key) >> 40) * (1.0f / 16777216.0f);
+        return VK == kValLinear31 ? tx * 31u + ty : (ty << r) | tx;
+    }
+    __device__ __forceinline__ T operator()(uint32_t base, uint32_t koff) const
+    {
+        if constexpr (VK == kValConst) {
+            if constexpr (sizeof(T) == 1) return (T)cval;
+            else return __uint_as_float(cval);
+        } else if constexpr (VK == kValLinear31) {
+            return (T)((base + koff) & 0xFFu);
+        } else {
+            const uint64_t h = splitmix64(seedmix ^ (uint64_t)(base + koff));
+            if constexpr (sizeof(T) == 1) return (T)(h >> 56);
+            else return (float)(uint32_t)(h >> 40) * (1.0f / 16777216.0f);
+        }
     }
 };
 

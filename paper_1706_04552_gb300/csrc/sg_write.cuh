@@ -190,20 +190,31 @@ write_scatter_kernel(T *__restrict__ grid, int r, int order, uint64_t vs, uint64
 
     uint32_t off[ITERS];
     intra_tile_offsets<S, MAP, TEAM, ITERS>(off, t_in_team, lut);
+    // tile-independent parts of each cell: grid offset (ty << r | tx, masked
+    // to the tile so every address stays inside it) and value-key offset;
+    // slots off the gasket are dropped (in a tile holding gasket cells,
+    // (x & y) == 0 iff (tx & ty) == 0; empty bounding-box tiles are skipped)
+    uint32_t goff[ITERS], koff[ITERS];
+#pragma unroll
+    for (int j = 0; j < ITERS; ++j) {
+        const uint32_t tx = off[j] & (RHO - 1), ty = (off[j] >> 8) & (RHO - 1);
+        const bool keep = off[j] != ~0u && (!SUBBOX || (tx & ty) == 0u);
+        goff[j] = keep ? (ty << r) | tx : ~0u;
+        koff[j] = CellValue<T, VK>::offset_of(tx, ty, r);
+    }
+    const CellValue<T, VK> cv{seedmix, (uint32_t)vs};
     TileWalker<MAP> tw;
     tw.init(threadIdx.x & 31, r - S, order, team, nteams);
 
     for (uint64_t q = team; q < ntiles; q += nteams) {
         const uint2 b = tw.next(q);
+        if (MAP == kMapBBox && (b.x & b.y) != 0u) continue;   // no gasket cell
         const uint32_t x0 = b.x << S, y0 = b.y << S;
+        T *tile = grid + (((uint64_t)y0 << r) | x0);
+        const uint32_t base = CellValue<T, VK>::base_of(x0, y0, r);
 #pragma unroll
-        for (int j = 0; j < ITERS; ++j) {
-            if (off[j] == ~0u) continue;
-            // offsets are masked to the tile, so every address stays inside it
-            const uint32_t x = x0 + (off[j] & (RHO - 1)), y = y0 + ((off[j] >> 8) & (RHO - 1));
-            if (SUBBOX && !in_gasket(x, y)) continue;
-            grid[((uint64_t)y << r) + x] = Value<T>::template at<VK>(x, y, r, vs, seedmix);
-        }
+        for (int j = 0; j < ITERS; ++j)
+            if (goff[j] != ~0u) tile[goff[j]] = cv(base, koff[j]);
     }
 }
 
@@ -276,11 +287,21 @@ write_staged_kernel(T *__restrict__ grid, int r, int order, uint64_t vs, uint64_
 
     uint32_t off[ITERS];
     intra_tile_offsets<S, MAP, TEAM, ITERS>(off, t_in_team, lut);
+    uint32_t koff[ITERS], soff[ITERS];
+#pragma unroll
+    for (int j = 0; j < ITERS; ++j) {
+        const uint32_t tx = off[j] & (RHO - 1), ty = (off[j] >> 8) & (RHO - 1);
+        const bool keep = off[j] != ~0u && (!SUBBOX || (tx & ty) == 0u);
+        koff[j] = CellValue<T, VK>::offset_of(tx, ty, r);
+        soff[j] = keep ? ty * RHO + tx : ~0u;
+    }
+    const CellValue<T, VK> cv{seedmix, (uint32_t)vs};
     TileWalker<MAP> tw;
     tw.init(threadIdx.x & 31, r - S, order, team, nteams);
 
     for (uint64_t q = team; q < ntiles; q += nteams) {
         const uint2 b = tw.next(q);
+        if (MAP == kMapBBox && (b.x & b.y) != 0u) continue;   // no gasket cell
         const uint32_t x0 = b.x << S, y0 = b.y << S;
 
         // 1. issue the loads of this thread's touched chunks
@@ -298,14 +319,10 @@ write_staged_kernel(T *__restrict__ grid, int r, int order, uint64_t vs, uint64_
         }
         // 2. new values into the shared copy of the tile
         team_sync<TEAM>();        // the previous tile's merge has read `my`
+        const uint32_t base = CellValue<T, VK>::base_of(x0, y0, r);
 #pragma unroll
-        for (int j = 0; j < ITERS; ++j) {
-            if (off[j] == ~0u) continue;
-            const uint32_t tx = off[j] & (RHO - 1), ty = (off[j] >> 8) & (RHO - 1);
-            const uint32_t x = x0 + tx, y = y0 + ty;
-            if (SUBBOX && !in_gasket(x, y)) continue;
-            my[ty * RHO + tx] = Value<T>::template at<VK>(x, y, r, vs, seedmix);
-        }
+        for (int j = 0; j < ITERS; ++j)
+            if (soff[j] != ~0u) my[soff[j]] = cv(base, koff[j]);
         team_sync<TEAM>();
         // 3. merge under the gasket mask and store whole chunks
 #pragma unroll
@@ -367,6 +384,15 @@ write_tma_kernel(const __grid_constant__ CUtensorMap tmap, int r, int order, uin
 
     uint32_t off[ITERS];
     intra_tile_offsets<S, MAP, TEAM, ITERS, kTmaThreads>(off, t, lut);
+    uint32_t koff[ITERS], soff[ITERS];
+#pragma unroll
+    for (int j = 0; j < ITERS; ++j) {
+        const uint32_t tx = off[j] & (RHO - 1), ty = (off[j] >> 8) & (RHO - 1);
+        const bool keep = off[j] != ~0u && (!TS::SUBBOX || (tx & ty) == 0u);
+        koff[j] = CellValue<T, VK>::offset_of(tx, ty, r);
+        soff[j] = keep ? ty * RHO + tx : ~0u;
+    }
+    const CellValue<T, VK> cv{seedmix, (uint32_t)vs};
     if (t == 0) {
         for (int i = 0; i < ST; ++i) mbar_init(&full[tm][i], 1);
         abort_team[tm] = 0;
@@ -410,14 +436,10 @@ write_tma_kernel(const __grid_constant__ CUtensorMap tmap, int r, int order, uin
         const uint32_t x0 = b.x << S, y0 = b.y << S;
         T *tile = reinterpret_cast<T *>(buf + sl * TS::BUF);
         if (got && !empty) {
+            const uint32_t base = CellValue<T, VK>::base_of(x0, y0, r);
 #pragma unroll
-            for (int j = 0; j < ITERS; ++j) {
-                if (off[j] == ~0u) continue;
-                const uint32_t tx = off[j] & (RHO - 1), ty = (off[j] >> 8) & (RHO - 1);
-                const uint32_t x = x0 + tx, y = y0 + ty;
-                if (TS::SUBBOX && !in_gasket(x, y)) continue;
-                tile[ty * RHO + tx] = Value<T>::template at<VK>(x, y, r, vs, seedmix);
-            }
+            for (int j = 0; j < ITERS; ++j)
+                if (soff[j] != ~0u) tile[soff[j]] = cv(base, koff[j]);
         }
         fence_proxy_async_shared();
         team_sync<TEAM>();
@@ -480,6 +502,18 @@ write_fill_kernel(const __grid_constant__ CUtensorMap tmap, int r, int order, ui
     uint32_t off[ITERS];
     intra_tile_offsets<S, MAP, TEAM, ITERS, kTmaThreads>(off, t, lut);   // syncs the CTA
     if constexpr (MAP != kMapLut) __syncthreads();
+    // per-thread, tile-independent parts of each cell: value-key offset and
+    // shared-memory offset (slots off the gasket are dropped: for a tile that
+    // holds gasket cells, (x & y) == 0 iff (tx & ty) == 0)
+    uint32_t koff[ITERS], soff[ITERS];
+#pragma unroll
+    for (int j = 0; j < ITERS; ++j) {
+        const uint32_t tx = off[j] & (RHO - 1), ty = (off[j] >> 8) & (RHO - 1);
+        const bool keep = off[j] != ~0u && (!TS::SUBBOX || (tx & ty) == 0u);
+        koff[j] = CellValue<T, VK>::offset_of(tx, ty, r);
+        soff[j] = keep ? ty * RHO + tx : ~0u;
+    }
+    const CellValue<T, VK> cv{seedmix, (uint32_t)vs};
     TileWalker<MAP> tw;
     tw.init(lane, r - S, order, team, nteams);
 
@@ -495,15 +529,10 @@ write_fill_kernel(const __grid_constant__ CUtensorMap tmap, int r, int order, ui
         const uint32_t x0 = b.x << S, y0 = b.y << S;
         uint8_t *tile = buf + (int)(k % ST) * TS::BUF;
         if (!empty) {
+            const uint32_t base = CellValue<T, VK>::base_of(x0, y0, r);
 #pragma unroll
-            for (int j = 0; j < ITERS; ++j) {
-                if (off[j] == ~0u) continue;
-                const uint32_t tx = off[j] & (RHO - 1), ty = (off[j] >> 8) & (RHO - 1);
-                const uint32_t x = x0 + tx, y = y0 + ty;
-                if (TS::SUBBOX && !in_gasket(x, y)) continue;
-                reinterpret_cast<T *>(tile)[ty * RHO + tx] =
-                    Value<T>::template at<VK>(x, y, r, vs, seedmix);
-            }
+            for (int j = 0; j < ITERS; ++j)
+                if (soff[j] != ~0u) reinterpret_cast<T *>(tile)[soff[j]] = cv(base, koff[j]);
             fence_proxy_async_shared();
         }
         team_sync<TEAM>();
