@@ -124,6 +124,12 @@ ca_vec_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int r,
     constexpr int RHO = 1 << S, CPR = RHO / 16, CHUNKS = RHO * CPR;
     constexpr int TPC = CHUNKS >= kStencilThreads ? 1 : kStencilThreads / CHUNKS;
     constexpr int P = RHO + 32;            // row pitch; interior at byte 16
+    // Chunks are loaded and stored by 32-byte sector when a tile row spans
+    // whole sectors (rho >= 32): a sector holding any gasket cell moves whole
+    // (its off-gasket bytes are 0 in both buffers), so the L2 never has to
+    // fill a half-written sector.  With rho = 16 a sector straddles two
+    // tiles and chunks move alone.
+    constexpr uint32_t kCaGroupMask = ~(uint32_t)((RHO >= 32 ? 32 : 16) - 1);
     constexpr int TILE = (RHO + 2) * P;
     constexpr int HALO = 4 * RHO + 4;
     __shared__ __align__(16) uint8_t sm[TPC * TILE];
@@ -145,7 +151,7 @@ ca_vec_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int r,
             uint4 v = make_uint4(0, 0, 0, 0);
             if (b.x != kNoTile) {
                 const uint32_t x = (b.x << S) + 16u * cx, y = (b.y << S) + ty;
-                if (in_gasket(x, y))
+                if (in_gasket(x & kCaGroupMask, y))   // chunk in a touched sector
                     v = *reinterpret_cast<const uint4 *>(in + ((uint64_t)y << r) + x);
             }
             *reinterpret_cast<uint4 *>(sm + t * TILE + (ty + 1) * P + 16 + 16 * cx) = v;
@@ -166,7 +172,7 @@ ca_vec_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int r,
             const uint2 b = coord[t];
             if (b.x == kNoTile) continue;
             const uint32_t x = (b.x << S) + 16u * cx, y = (b.y << S) + ty;
-            if (!in_gasket(x, y)) continue;       // no gasket cell in this chunk
+            if (!in_gasket(x & kCaGroupMask, y)) continue;   // sector holds no gasket cell
             const uint8_t *base = sm + t * TILE + 16 + 16 * cx;
             const uint8_t *up = base + ty * P, *mid = up + P, *dn = mid + P;
             const uint4 cu = *reinterpret_cast<const uint4 *>(up);
@@ -176,7 +182,9 @@ ca_vec_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int r,
             const uint4 hd = add4(add4(shift_in_left(cd, dn[-1]), cd), shift_in_right(cd, dn[16]));
             const uint4 hm = add4(shift_in_left(cm, mid[-1]), shift_in_right(cm, mid[16]));
             const uint4 cnt = add4(add4(hu, hd), hm);
-            const uint4 m = member_bytes16(y & 15u);
+            // x is 16-aligned: the chunk holds gasket cells iff (x & y) == 0,
+            // and then bytes i with (i & (y mod 16)) == 0 are the gasket ones
+            const uint4 m = in_gasket(x, y) ? member_bytes16(y & 15u) : make_uint4(0u, 0u, 0u, 0u);
             uint4 o;
             o.x = life_rule(cnt.x, cm.x, m.x);
             o.y = life_rule(cnt.y, cm.y, m.y);
@@ -271,6 +279,8 @@ diffuse_vec_kernel(const float *__restrict__ in, float *__restrict__ out, int r,
     constexpr int RHO = 1 << S, CPR = RHO / 4, CHUNKS = RHO * CPR;
     constexpr int TPC = CHUNKS >= kStencilThreads ? 1 : kStencilThreads / CHUNKS;
     constexpr int P = RHO + 8;             // row pitch (floats); interior at 4
+    // whole 32-byte sectors (8 floats) move together when inside the tile
+    constexpr uint32_t kDfGroupMask = ~(uint32_t)((RHO >= 8 ? 8 : 4) - 1);
     constexpr int TILE = (RHO + 2) * P;
     constexpr int HALO = 4 * RHO + 4;
     __shared__ __align__(16) float sm[TPC * TILE];
@@ -293,7 +303,7 @@ diffuse_vec_kernel(const float *__restrict__ in, float *__restrict__ out, int r,
             float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
             if (b.x != kNoTile) {
                 const uint32_t x = (b.x << S) + 4u * cx, y = (b.y << S) + ty;
-                if (in_gasket(x, y))
+                if (in_gasket(x & kDfGroupMask, y))   // chunk in a touched sector
                     v = *reinterpret_cast<const float4 *>(in + ((uint64_t)y << r) + x);
             }
             *reinterpret_cast<float4 *>(sm + t * TILE + (ty + 1) * P + 4 + 4 * cx) = v;
@@ -314,7 +324,7 @@ diffuse_vec_kernel(const float *__restrict__ in, float *__restrict__ out, int r,
             const uint2 b = coord[t];
             if (b.x == kNoTile) continue;
             const uint32_t x = (b.x << S) + 4u * cx, y = (b.y << S) + ty;
-            if (!in_gasket(x, y)) continue;
+            if (!in_gasket(x & kDfGroupMask, y)) continue;   // sector holds no gasket cell
             const float *mid = sm + t * TILE + (ty + 1) * P + 4 + 4 * cx;
             const float4 cu = *reinterpret_cast<const float4 *>(mid - P);
             const float4 cm = *reinterpret_cast<const float4 *>(mid);
