@@ -59,6 +59,9 @@ def parse_args():
     p.add_argument("--quick", action="store_true",
                    help="headline launches only (no clock soak, extras, e2e or CPU "
                         "baseline): the form used under ncu")
+    p.add_argument("--workload", choices=("write", "ca", "diffusion"), default="write",
+                   help="with --quick: time the level-15 CA or diffusion step instead "
+                        "of the write pass (the form used to profile those kernels)")
     return p.parse_args()
 
 
@@ -256,6 +259,8 @@ def run_ours(args, grp: Group):
     dev = torch.device("cuda", grp.local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
+    if args.quick and args.workload != "write":
+        return run_stencil_quick(args, sg, torch, dev, stream)
     w = dict(workloads.WRITE_HEADLINE)
     if args.rho:
         w["rho"] = args.rho
@@ -341,6 +346,36 @@ def run_ours(args, grp: Group):
     if grp.rank == 0 and grp.world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(w)
     return out
+
+
+def run_stencil_quick(args, sg, torch, dev, stream):
+    """K steps of the level-15 CA or diffusion step (lambda map), for ncu."""
+    from paper_1706_04552_gb300 import inputs, workloads
+    s = workloads.STENCILS
+    r = max(s["levels"])
+    n = 1 << r
+    if args.workload == "ca":
+        idx, vals = inputs.ca_seed_sparse(r, s["ca_p"], s["ca_seed"])
+        dt, rho = torch.uint8, s["ca_rho"]
+    else:
+        idx, vals = inputs.uniform_sparse(r, s["diff_seed"])
+        dt, rho = torch.float32, s["diff_rho"]
+    a = torch.zeros(n * n, dtype=dt, device=dev)
+    a[torch.from_numpy(idx).to(dev)] = torch.from_numpy(vals).to(dev)
+    bufs = [a, torch.zeros_like(a)]
+
+    def step():
+        if args.workload == "ca":
+            sg.ca_step(bufs[0], bufs[1], r, rho, "lambda", stream)
+        else:
+            sg.diffuse_step(bufs[0], bufs[1], r, rho, s["alpha"], "lambda", stream)
+        bufs.reverse()
+    for _ in range(max(3, args.warmup)):
+        step()
+    total_ms, per = time_launches(step, args.steps, stream)
+    return {"workload": f"{args.workload} step, level {r}, rho {rho}, lambda",
+            "unit": UNIT, "value": round(3 ** r / (total_ms / args.steps / 1e3) / 1e9, 3),
+            "launch_ms_mean": round(statistics.mean(per), 5), "steps": args.steps}
 
 
 def _rate(cells, ms):
