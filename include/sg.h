@@ -221,6 +221,71 @@ SG_API sg_status sg_block_map(int rb, sg_order order, uint32_t *bx, uint32_t *by
 SG_API sg_status sg_launch_stats(int r, int rho, sg_map map, uint64_t *launched,
                                  uint64_t *useful);
 
+/* ------------------------------------------------------------------------
+ * Batches: many gaskets of uneven levels stepped by one launch.
+ *
+ * A batch is `count` gaskets, gasket i of level levels[i] with its own pair
+ * of uint8 CA state buffers (buf_a[i], buf_b[i]; n_i*n_i bytes each, 16-byte
+ * aligned, same conditions as sg_ca_step).  A step runs one persistent grid
+ * over a single work list -- the concatenation of every gasket's lambda block
+ * space, 3^(r_i - s) tiles each, indexed through a prefix sum -- instead of
+ * one grid per gasket.  Parity 0 reads buf_a and writes buf_b; parity 1 the
+ * reverse.  Results are bit-identical to stepping each gasket alone with
+ * sg_ca_step.  The paper has no counterpart for batching; the per-gasket work
+ * is the same lambda map (Theorem 1) and stencil as sg_ca_step.
+ * ------------------------------------------------------------------------ */
+
+/* A planned batch (filled by sg_batch_ca_plan; plain data the caller owns). */
+typedef struct {
+    void *workspace;            /* device memory holding the work list */
+    uint64_t workspace_bytes;
+    int count;                  /* gaskets */
+    int rho;                    /* tile side: 16, 32 or 64 */
+    uint32_t total_tiles;       /* work items per step */
+    uint32_t max_level;
+    int reserved[4];
+} sg_batch_plan;
+
+/* Device bytes the work list of `count` gaskets needs (0 if count is out of
+ * range 1..65535).  Host-only. */
+SG_API uint64_t sg_batch_workspace_bytes(int count);
+
+/* Build the work list in `workspace` (caller-owned device memory of at least
+ * sg_batch_workspace_bytes(count) bytes, 16-byte aligned) and fill *plan.
+ * Every level must satisfy log2(rho) <= level <= 16.  levels, buf_a and buf_b
+ * are host arrays of `count` entries (buf_* hold device pointers); they are
+ * copied before the call returns.  One host-to-device copy on `stream`. */
+SG_API sg_status sg_batch_ca_plan(int count, const int *levels, uint8_t *const *buf_a,
+                                  uint8_t *const *buf_b, int rho, void *workspace,
+                                  uint64_t workspace_bytes, sg_batch_plan *plan, void *stream);
+
+/* One CA step of every gasket of the batch: one launch. */
+SG_API sg_status sg_batch_ca_step(const sg_batch_plan *plan, int parity,
+                                  const sg_launch_opts *opts, void *stream);
+
+/* Capture `steps` consecutive batch steps (parities start_parity,
+ * start_parity ^ 1, ...) into an instantiated CUDA graph (*graph, a
+ * cudaGraphExec_t).  Launch it with sg_graph_launch, release it with
+ * sg_graph_destroy.  The plan's workspace and buffers must outlive it. */
+SG_API sg_status sg_batch_ca_graph_create(const sg_batch_plan *plan, int steps,
+                                          int start_parity, const sg_launch_opts *opts,
+                                          void **graph);
+SG_API sg_status sg_graph_launch(void *graph, void *stream);
+SG_API sg_status sg_graph_destroy(void *graph);
+
+/* Autotune a batch: time `trial_steps` parity-0 steps for every rho in
+ * {16, 32, 64} allowed by the smallest level, both walking orders and
+ * CTAs per SM in {occupancy maximum, 2, 4, 8}; plan the batch with the
+ * fastest rho and return its launch options.  Parity-0 steps only read
+ * buf_a, so the batch's current state (in buf_a) is left as it was; buf_b is
+ * overwritten.  Results are cached per multiset of levels for the process.
+ * Synchronises `stream`. */
+SG_API sg_status sg_batch_ca_autotune(int count, const int *levels, uint8_t *const *buf_a,
+                                      uint8_t *const *buf_b, void *workspace,
+                                      uint64_t workspace_bytes, int trial_steps,
+                                      sg_batch_plan *plan, sg_launch_opts *opts_out,
+                                      void *stream);
+
 /*
  * sg_device_status -- report and clear the device status word of the current
  * device.  Kernels with bounded waits (SG_STORE_TMA) record a wait that gave

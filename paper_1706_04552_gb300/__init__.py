@@ -26,6 +26,7 @@ __all__ = [
     "sg_map_write_ex", "sg_ca_step_ex", "sg_diffuse_step_ex", "LaunchOpts", "launch_opts",
     "sg_launch_stats", "sg_status_str", "sg_abi_version", "sg_device_status",
     "device_status",
+    "CABatch", "Graph", "BatchPlan",
     "map_write", "map_write_host", "ca_step", "diffuse_step", "block_map", "launch_stats",
     "MAPS", "DTYPES", "VALUES", "ORDERS", "STORES",
 ]
@@ -45,6 +46,14 @@ class LaunchOpts(ctypes.Structure):
     """sg_launch_opts of include/sg.h."""
     _fields_ = [("order", ctypes.c_int), ("store", ctypes.c_int),
                 ("ctas_per_sm", ctypes.c_int), ("reserved", ctypes.c_int * 5)]
+
+
+class BatchPlan(ctypes.Structure):
+    """sg_batch_plan of include/sg.h."""
+    _fields_ = [("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_uint64),
+                ("count", ctypes.c_int), ("rho", ctypes.c_int),
+                ("total_tiles", ctypes.c_uint32), ("max_level", ctypes.c_uint32),
+                ("reserved", ctypes.c_int * 4)]
 
 
 def launch_opts(order=None, store=None, ctas_per_sm=None):
@@ -109,6 +118,21 @@ def lib() -> ctypes.CDLL:
         L.sg_status_str.restype = ctypes.c_char_p
         L.sg_last_error_string.argtypes = []
         L.sg_last_error_string.restype = ctypes.c_char_p
+        p_plan = ctypes.POINTER(BatchPlan)
+        L.sg_batch_workspace_bytes.argtypes = [i32]
+        L.sg_batch_workspace_bytes.restype = u64
+        L.sg_batch_ca_plan.argtypes = [i32, vp, vp, vp, i32, vp, u64, p_plan, vp]
+        L.sg_batch_ca_plan.restype = i32
+        L.sg_batch_ca_step.argtypes = [p_plan, i32, p_opts, vp]
+        L.sg_batch_ca_step.restype = i32
+        L.sg_batch_ca_graph_create.argtypes = [p_plan, i32, i32, p_opts, ctypes.POINTER(vp)]
+        L.sg_batch_ca_graph_create.restype = i32
+        L.sg_graph_launch.argtypes = [vp, vp]
+        L.sg_graph_launch.restype = i32
+        L.sg_graph_destroy.argtypes = [vp]
+        L.sg_graph_destroy.restype = i32
+        L.sg_batch_ca_autotune.argtypes = [i32, vp, vp, vp, vp, u64, i32, p_plan, p_opts, vp]
+        L.sg_batch_ca_autotune.restype = i32
         L.sg_device_status.argtypes = [vp]
         L.sg_device_status.restype = i32
         L.sg_abi_version.argtypes = []
@@ -301,6 +325,96 @@ def block_map(rb: int, order="interleaved", device="cuda", stream=None):
         _check("sg_block_map", sg_block_map(rb, oid, bx.data_ptr(), by.data_ptr(),
                                             _stream_handle(bx, stream)))
     return bx, by
+
+
+# ------------------------------------------------------------------ batches
+
+class CABatch:
+    """Many gaskets of uneven levels stepped together (sg_batch_* calls).
+
+    levels: gasket levels; bufs_a / bufs_b: uint8 CUDA tensors of n_i*n_i
+    cells (0 off the gasket; the state to step starts in bufs_a).  rho picks
+    the tile side; autotune=K times K steps per candidate and plans with the
+    fastest (rho, walking order, CTAs per SM).  The work list lives in a
+    workspace tensor this object owns."""
+
+    def __init__(self, levels, bufs_a, bufs_b, rho=64, autotune=None, stream=None):
+        import torch
+        self.levels = [int(r) for r in levels]
+        count = len(self.levels)
+        if not (len(bufs_a) == len(bufs_b) == count):
+            raise ValueError("one pair of buffers per gasket")
+        for r, a, b in zip(self.levels, bufs_a, bufs_b):
+            _grid_check(a, r, (torch.uint8,), "bufs_a")
+            _grid_check(b, r, (torch.uint8,), "bufs_b")
+        self.bufs_a, self.bufs_b = list(bufs_a), list(bufs_b)
+        dev = self.bufs_a[0].device
+        nbytes = int(lib().sg_batch_workspace_bytes(count))
+        if nbytes == 0:
+            raise ValueError(f"batch of {count} gaskets is out of range")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        lv = (ctypes.c_int * count)(*self.levels)
+        pa = (ctypes.c_void_p * count)(*[t.data_ptr() for t in self.bufs_a])
+        pb = (ctypes.c_void_p * count)(*[t.data_ptr() for t in self.bufs_b])
+        self.plan = BatchPlan()
+        self.opts = None
+        st = _stream_handle(self.workspace, stream)
+        with _on_device(self.workspace):
+            if autotune:
+                self.opts = LaunchOpts()
+                _check("sg_batch_ca_autotune", int(lib().sg_batch_ca_autotune(
+                    count, lv, pa, pb, self.workspace.data_ptr(), nbytes, int(autotune),
+                    ctypes.byref(self.plan), ctypes.byref(self.opts), st)))
+            else:
+                _check("sg_batch_ca_plan", int(lib().sg_batch_ca_plan(
+                    count, lv, pa, pb, int(rho), self.workspace.data_ptr(), nbytes,
+                    ctypes.byref(self.plan), st)))
+
+    @property
+    def rho(self):
+        return self.plan.rho
+
+    def step(self, parity=0, stream=None, order=None, ctas_per_sm=None):
+        opts = self.opts if (order is None and ctas_per_sm is None) else launch_opts(
+            order, None, ctas_per_sm)
+        with _on_device(self.workspace):
+            _check("sg_batch_ca_step", int(lib().sg_batch_ca_step(
+                ctypes.byref(self.plan), int(parity), _opts_ref(opts),
+                _stream_handle(self.workspace, stream))))
+
+    def graph(self, steps, start_parity=0):
+        """A CUDA graph of `steps` consecutive steps (see Graph)."""
+        h = ctypes.c_void_p()
+        with _on_device(self.workspace):
+            _check("sg_batch_ca_graph_create", int(lib().sg_batch_ca_graph_create(
+                ctypes.byref(self.plan), int(steps), int(start_parity), _opts_ref(self.opts),
+                ctypes.byref(h))))
+        return Graph(h, self)
+
+
+class Graph:
+    """An instantiated CUDA graph made by libsg; launch() replays it."""
+
+    def __init__(self, handle, owner=None):
+        self.handle = handle
+        self._owner = owner            # keeps the workspace and buffers alive
+
+    def launch(self, stream=None):
+        import torch
+        st = torch.cuda.current_stream().cuda_stream if stream is None else (
+            stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        _check("sg_graph_launch", int(lib().sg_graph_launch(self.handle, st)))
+
+    def close(self):
+        if self.handle:
+            lib().sg_graph_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def launch_stats(r: int, rho: int, map="lambda"):

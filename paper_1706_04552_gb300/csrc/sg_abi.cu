@@ -50,8 +50,10 @@ bool aligned(const void *p, uintptr_t a) { return ((uintptr_t)p & (a - 1)) == 0;
 constexpr int kDefaultOrder = kOrderInterleaved;
 constexpr int kDefaultWholeTileStore = kStoreStaged;
 
+}  // namespace
+
 // Translate sg_launch_opts (NULL = defaults) into a LaunchCfg.
-bool read_opts(const sg_launch_opts *o, LaunchCfg *cfg)
+bool read_launch_opts(const sg_launch_opts *o, LaunchCfg *cfg)
 {
     cfg->order = kDefaultOrder;
     cfg->store = kStoreAuto;
@@ -69,6 +71,15 @@ bool read_opts(const sg_launch_opts *o, LaunchCfg *cfg)
     cfg->ctas_per_sm = o->ctas_per_sm;
     return true;
 }
+
+sg_status set_last_cuda_error(cudaError_t e)
+{
+    std::snprintf(g_last_error, sizeof g_last_error, "%s: %s", cudaGetErrorName(e),
+                  cudaGetErrorString(e));
+    return e == cudaErrorNotSupported ? SG_EUNSUPPORTED : SG_ECUDA;
+}
+
+namespace {
 
 sg_status finish(cudaError_t e)
 {
@@ -162,7 +173,7 @@ sg_status sg_map_write_ex(int r, int rho, sg_map map, sg_dtype dtype, void *grid
     if (value_kind < SG_VAL_CONST || value_kind > SG_VAL_HASH) return SG_EINVAL;
     if (grid == nullptr) return SG_EINVAL;
     LaunchCfg cfg;
-    if (!read_opts(opts, &cfg)) return SG_EINVAL;
+    if (!read_launch_opts(opts, &cfg)) return SG_EINVAL;
     if (dtype != SG_U8 && dtype != SG_F32) return SG_EINVAL;
     const int elem = dtype == SG_U8 ? 1 : 4;
     if (!aligned(grid, (uintptr_t)elem)) return SG_EINVAL;
@@ -199,7 +210,7 @@ sg_status sg_ca_step_ex(int r, int rho, sg_map map, const uint8_t *in, uint8_t *
     if (in == nullptr || out == nullptr || in == out) return SG_EINVAL;
     if (!aligned(in, 16) || !aligned(out, 16)) return SG_EINVAL;
     LaunchCfg cfg;
-    if (!read_opts(opts, &cfg)) return SG_EINVAL;
+    if (!read_launch_opts(opts, &cfg)) return SG_EINVAL;
     return finish(launch_ca(r, s, (int)map, in, out, (cudaStream_t)stream, cfg));
 }
 
@@ -220,7 +231,7 @@ sg_status sg_diffuse_step_ex(int r, int rho, sg_map map, const float *in, float 
     if (!aligned(in, 16) || !aligned(out, 16)) return SG_EINVAL;
     if (!(alpha == alpha) || alpha > 3.0e38f || alpha < -3.0e38f) return SG_EINVAL;
     LaunchCfg cfg;
-    if (!read_opts(opts, &cfg)) return SG_EINVAL;
+    if (!read_launch_opts(opts, &cfg)) return SG_EINVAL;
     return finish(launch_diffuse(r, s, (int)map, in, out, alpha, (cudaStream_t)stream, cfg));
 }
 

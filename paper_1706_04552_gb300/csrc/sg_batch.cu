@@ -1,0 +1,360 @@
+// sg_batch.cu -- many gaskets of uneven levels stepped by one launch.
+//
+// A batch is a list of gaskets, each with its own level r_i and its own pair
+// of uint8 state buffers.  Instead of one grid per gasket, a step launches
+// one persistent grid over a single work list: the concatenation of every
+// gasket's lambda block space (3^(r_i - s) tiles each), indexed through a
+// prefix sum.  A CTA takes a group of consecutive work items, finds each
+// item's gasket by binary search in the prefix sum, decodes the item's tile
+// with lambda at that gasket's level, and runs the CA tile step shared with
+// the single-gasket kernel.  The step sequence can be captured once in a
+// CUDA graph; an autotuner picks rho, the walking order and CTAs per SM.
+//
+// Workspace (caller-owned device memory, sg_batch_workspace_bytes(count)):
+//   uint32 prefix[count + 1]   first work item of gasket i (prefix[count] = total)
+//   int32  level[count]
+//   uint64 buf_a[count], buf_b[count]   state buffers (parity 0 reads a, writes b)
+#include <algorithm>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "sg.h"
+#include "sg_stencil.cuh"
+
+namespace sg {
+
+namespace {
+
+constexpr int kMaxBatch = 65535;
+
+uint64_t align16(uint64_t v) { return (v + 15) & ~(uint64_t)15; }
+
+struct WsLayout {
+    uint64_t prefix, level, a, b, total;
+};
+
+WsLayout ws_layout(int count)
+{
+    WsLayout L;
+    L.prefix = 0;
+    L.level = align16(L.prefix + 4ull * (count + 1));
+    L.a = align16(L.level + 4ull * count);
+    L.b = L.a + 8ull * count;
+    L.total = align16(L.b + 8ull * count);
+    return L;
+}
+
+struct BatchView {
+    const uint32_t *prefix;
+    const int32_t *level;
+    const uint64_t *buf_a;
+    const uint64_t *buf_b;
+    uint32_t count;
+};
+
+BatchView view_of(const sg_batch_plan *p)
+{
+    const WsLayout L = ws_layout(p->count);
+    const char *ws = static_cast<const char *>(p->workspace);
+    return BatchView{reinterpret_cast<const uint32_t *>(ws + L.prefix),
+                     reinterpret_cast<const int32_t *>(ws + L.level),
+                     reinterpret_cast<const uint64_t *>(ws + L.a),
+                     reinterpret_cast<const uint64_t *>(ws + L.b), (uint32_t)p->count};
+}
+
+// Gasket that work item q belongs to: the largest i with prefix[i] <= q.
+__device__ __forceinline__ uint32_t batch_instance(const uint32_t *prefix, uint32_t count,
+                                                   uint32_t q)
+{
+    uint32_t lo = 0, hi = count;           // prefix[lo] <= q < prefix[hi]
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (__ldg(prefix + mid) <= q) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+template <int S>
+__global__ void __launch_bounds__(kStencilThreads)
+ca_batch_kernel(BatchView bv, uint32_t total, int parity, int order)
+{
+    using G = CaGroup<S>;
+    __shared__ __align__(16) uint8_t sm[G::TPC * G::TILE];
+    __shared__ CaTile tiles[G::TPC];
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    LambdaLane ll;
+    ll.init(lane, 0, order);
+    const uint32_t groups = (total + G::TPC - 1) / G::TPC;
+
+    for (uint32_t g = blockIdx.x; g < groups; g += gridDim.x) {
+        __syncthreads();
+        for (int t = warp; t < G::TPC; t += kStencilThreads / 32) {
+            const uint32_t q = g * G::TPC + (uint32_t)t;
+            CaTile tl{kNoTile, kNoTile, 0, nullptr, nullptr};
+            if (q < total) {                                  // warp-uniform
+                const uint32_t i = batch_instance(bv.prefix, bv.count, q);
+                const int r = __ldg(bv.level + i);
+                const int rb = r - S;
+                const uint32_t local = q - __ldg(bv.prefix + i);
+                ll.set_level(lane, rb);
+                const uint32_t W = pi_word(order, rb);
+                const uint32_t b = local / W, a = local - b * W;
+                const uint2 c = ll.decode(a, b);
+                const uint64_t pa = __ldg(bv.buf_a + i), pb = __ldg(bv.buf_b + i);
+                tl = CaTile{c.x, c.y, r, reinterpret_cast<const uint8_t *>(parity ? pb : pa),
+                            reinterpret_cast<uint8_t *>(parity ? pa : pb)};
+            }
+            if (lane == 0) tiles[t] = tl;
+        }
+        __syncthreads();
+        ca_group_step<S>(sm, tiles);
+    }
+}
+
+template <int S>
+cudaError_t launch_batch_t(const sg_batch_plan *p, int parity, cudaStream_t st,
+                           const LaunchCfg &cfg)
+{
+    static std::atomic<int> occ{0};
+    constexpr int TPC = CaGroup<S>::TPC;
+    unsigned grid = 1;
+    const uint64_t groups = (p->total_tiles + TPC - 1) / TPC;
+    auto k = ca_batch_kernel<S>;
+    cudaError_t e = persistent_grid(k, kStencilThreads, 0, groups, cfg, &grid, &occ);
+    if (e != cudaSuccess) return e;
+    k<<<grid, kStencilThreads, 0, st>>>(view_of(p), p->total_tiles, parity, cfg.order);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_batch(const sg_batch_plan *p, int parity, cudaStream_t st,
+                         const LaunchCfg &cfg)
+{
+    switch (p->rho) {
+    case 16: return launch_batch_t<4>(p, parity, st, cfg);
+    case 32: return launch_batch_t<5>(p, parity, st, cfg);
+    case 64: return launch_batch_t<6>(p, parity, st, cfg);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+bool plan_ok(const sg_batch_plan *p)
+{
+    return p != nullptr && p->workspace != nullptr && p->count >= 1 && p->count <= kMaxBatch &&
+           (p->rho == 16 || p->rho == 32 || p->rho == 64) && p->total_tiles > 0;
+}
+
+sg_status cuda_fail(cudaError_t e) { return set_last_cuda_error(e); }
+
+// Autotuner results, keyed by the multiset of levels (host memory only).
+std::mutex g_tune_mu;
+std::map<std::string, std::vector<int>> g_tune_cache;
+
+}  // namespace
+
+}  // namespace sg
+
+using namespace sg;
+
+extern "C" {
+
+uint64_t sg_batch_workspace_bytes(int count)
+{
+    if (count < 1 || count > kMaxBatch) return 0;
+    return ws_layout(count).total;
+}
+
+sg_status sg_batch_ca_plan(int count, const int *levels, uint8_t *const *buf_a,
+                           uint8_t *const *buf_b, int rho, void *workspace,
+                           uint64_t workspace_bytes, sg_batch_plan *plan, void *stream)
+{
+    if (plan == nullptr || levels == nullptr || buf_a == nullptr || buf_b == nullptr)
+        return SG_EINVAL;
+    if (count < 1 || count > kMaxBatch) return SG_EINVAL;
+    if (rho != 16 && rho != 32 && rho != 64) return SG_EUNSUPPORTED;
+    if (workspace == nullptr || ((uintptr_t)workspace & 15) != 0) return SG_EINVAL;
+    const WsLayout L = ws_layout(count);
+    if (workspace_bytes < L.total) return SG_EINVAL;
+    int s = 0;
+    while ((1 << s) < rho) ++s;
+    std::vector<uint32_t> prefix(count + 1);
+    uint64_t total = 0;
+    int max_level = 0;
+    for (int i = 0; i < count; ++i) {
+        const int r = levels[i];
+        if (r < s || r > 16) return SG_EINVAL;        // every gasket holds whole tiles
+        if (buf_a[i] == nullptr || buf_b[i] == nullptr || buf_a[i] == buf_b[i]) return SG_EINVAL;
+        if (((uintptr_t)buf_a[i] & 15) || ((uintptr_t)buf_b[i] & 15)) return SG_EINVAL;
+        prefix[i] = (uint32_t)total;
+        total += (uint64_t)pow3i(r - s);
+        max_level = std::max(max_level, r);
+        if (total >= (1ull << 32)) return SG_EINVAL;
+    }
+    prefix[count] = (uint32_t)total;
+    // host image of the workspace, copied in one transfer (pageable memory:
+    // the call returns once the bytes are staged, so the vector may go)
+    std::vector<unsigned char> img(L.total, 0);
+    std::memcpy(img.data() + L.prefix, prefix.data(), 4ull * (count + 1));
+    std::memcpy(img.data() + L.level, levels, 4ull * count);
+    for (int i = 0; i < count; ++i) {
+        const uint64_t pa = (uint64_t)(uintptr_t)buf_a[i], pb = (uint64_t)(uintptr_t)buf_b[i];
+        std::memcpy(img.data() + L.a + 8ull * i, &pa, 8);
+        std::memcpy(img.data() + L.b + 8ull * i, &pb, 8);
+    }
+    cudaError_t e = cudaMemcpyAsync(workspace, img.data(), L.total, cudaMemcpyHostToDevice,
+                                    (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *plan = sg_batch_plan{};
+    plan->workspace = workspace;
+    plan->workspace_bytes = workspace_bytes;
+    plan->count = count;
+    plan->rho = rho;
+    plan->total_tiles = (uint32_t)total;
+    plan->max_level = (uint32_t)max_level;
+    return SG_OK;
+}
+
+sg_status sg_batch_ca_step(const sg_batch_plan *plan, int parity, const sg_launch_opts *opts,
+                           void *stream)
+{
+    if (!plan_ok(plan) || (parity != 0 && parity != 1)) return SG_EINVAL;
+    LaunchCfg cfg;
+    if (!read_launch_opts(opts, &cfg)) return SG_EINVAL;
+    const cudaError_t e = launch_batch(plan, parity, (cudaStream_t)stream, cfg);
+    return e == cudaSuccess ? SG_OK : cuda_fail(e);
+}
+
+sg_status sg_batch_ca_graph_create(const sg_batch_plan *plan, int steps, int start_parity,
+                                   const sg_launch_opts *opts, void **graph)
+{
+    if (!plan_ok(plan) || graph == nullptr || steps < 1 || steps > 1000000 ||
+        (start_parity != 0 && start_parity != 1))
+        return SG_EINVAL;
+    LaunchCfg cfg;
+    if (!read_launch_opts(opts, &cfg)) return SG_EINVAL;
+    *graph = nullptr;
+    cudaStream_t cs;
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return cuda_fail(e);
+    e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t le = cudaSuccess;
+        for (int k = 0; k < steps && le == cudaSuccess; ++k)
+            le = launch_batch(plan, (start_parity + k) & 1, cs, cfg);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(cs, &g);
+        if (le != cudaSuccess) e = le;
+        if (e == cudaSuccess) {
+            cudaGraphExec_t x = nullptr;
+            e = cudaGraphInstantiate(&x, g, 0);
+            if (e == cudaSuccess) *graph = x;
+        }
+        if (g) cudaGraphDestroy(g);
+    }
+    cudaStreamDestroy(cs);
+    return e == cudaSuccess ? SG_OK : cuda_fail(e);
+}
+
+sg_status sg_graph_launch(void *graph, void *stream)
+{
+    if (graph == nullptr) return SG_EINVAL;
+    const cudaError_t e = cudaGraphLaunch((cudaGraphExec_t)graph, (cudaStream_t)stream);
+    return e == cudaSuccess ? SG_OK : cuda_fail(e);
+}
+
+sg_status sg_graph_destroy(void *graph)
+{
+    if (graph == nullptr) return SG_EINVAL;
+    const cudaError_t e = cudaGraphExecDestroy((cudaGraphExec_t)graph);
+    return e == cudaSuccess ? SG_OK : cuda_fail(e);
+}
+
+sg_status sg_batch_ca_autotune(int count, const int *levels, uint8_t *const *buf_a,
+                               uint8_t *const *buf_b, void *workspace, uint64_t workspace_bytes,
+                               int trial_steps, sg_batch_plan *plan, sg_launch_opts *opts_out,
+                               void *stream)
+{
+    if (count < 1 || count > kMaxBatch || levels == nullptr || plan == nullptr ||
+        opts_out == nullptr || trial_steps < 1 || trial_steps > 1000)
+        return SG_EINVAL;
+    int min_level = 16;
+    std::vector<int> sorted(levels, levels + count);
+    std::sort(sorted.begin(), sorted.end());
+    min_level = sorted.front();
+    std::string key = std::to_string(trial_steps) + ":";
+    for (int r : sorted) key += std::to_string(r) + ",";
+    int best_rho = 0, best_order = 1, best_cps = 0;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            best_rho = it->second[0];
+            best_order = it->second[1];
+            best_cps = it->second[2];
+        }
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    if (best_rho == 0) {
+        cudaEvent_t e0, e1;
+        cudaError_t e = cudaEventCreate(&e0);
+        if (e != cudaSuccess) return cuda_fail(e);
+        e = cudaEventCreate(&e1);
+        if (e != cudaSuccess) { cudaEventDestroy(e0); return cuda_fail(e); }
+        float best_ms = 1e30f;
+        sg_status status = SG_OK;
+        for (int rho : {16, 32, 64}) {
+            if ((1 << min_level) < rho) continue;
+            sg_batch_plan p;
+            status = sg_batch_ca_plan(count, levels, buf_a, buf_b, rho, workspace,
+                                      workspace_bytes, &p, stream);
+            if (status != SG_OK) break;
+            for (int order : {SG_ORDER_ROWMAJOR, SG_ORDER_INTERLEAVED}) {
+                for (int cps : {0, 2, 4, 8}) {
+                    LaunchCfg cfg;
+                    cfg.order = order;
+                    cfg.ctas_per_sm = cps;
+                    // repeated parity-0 steps read buffer a and rewrite buffer b:
+                    // the caller's current state (a) is left as it was
+                    e = launch_batch(&p, 0, st, cfg);                    // warm-up
+                    if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+                    for (int k = 0; k < trial_steps && e == cudaSuccess; ++k)
+                        e = launch_batch(&p, 0, st, cfg);
+                    if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+                    if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                    float ms = 0.f;
+                    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                    if (e != cudaSuccess) { status = cuda_fail(e); break; }
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        best_rho = rho;
+                        best_order = order;
+                        best_cps = cps;
+                    }
+                }
+                if (status != SG_OK) break;
+            }
+            if (status != SG_OK) break;
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (status != SG_OK) return status;
+        if (best_rho == 0) return SG_EUNSUPPORTED;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tune_cache[key] = {best_rho, best_order, best_cps};
+    }
+    sg_status status = sg_batch_ca_plan(count, levels, buf_a, buf_b, best_rho, workspace,
+                                        workspace_bytes, plan, stream);
+    if (status != SG_OK) return status;
+    *opts_out = sg_launch_opts{};
+    opts_out->order = best_order;
+    opts_out->store = SG_STORE_AUTO;
+    opts_out->ctas_per_sm = best_cps;
+    return SG_OK;
+}
+
+}  // extern "C"

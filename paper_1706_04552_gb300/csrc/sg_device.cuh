@@ -70,6 +70,15 @@ struct LambdaLane {
         nb_m1 = (1u << rb) - 1u;
     }
 
+    // Re-aim the lane at another block-space level (the digit constants
+    // depend only on the walking order): used by batches of gaskets.
+    __device__ __forceinline__ void set_level(int lane, int rb)
+    {
+        const int l = lane & 15;
+        active = (lane < 16) && (l < rb);
+        nb_m1 = (1u << rb) - 1u;
+    }
+
     // Every lane of the warp must call this with the same (a, b).
     __device__ __forceinline__ uint2 decode(uint32_t a, uint32_t b) const
     {

@@ -24,6 +24,17 @@ struct LaunchCfg {
 // Number of SMs of the current device (cached per device).
 int sm_count(int *err);
 
+}  // namespace sg
+#include "sg.h"
+namespace sg {
+
+// sg_launch_opts (NULL = defaults) -> LaunchCfg; false on a bad value.
+bool read_launch_opts(const sg_launch_opts *o, LaunchCfg *cfg);
+
+// Record a CUDA error for sg_last_error_string(); returns SG_ECUDA
+// (SG_EUNSUPPORTED for cudaErrorNotSupported).
+sg_status set_last_cuda_error(cudaError_t e);
+
 cudaError_t launch_write_u8(int r, int s, int map, int vk, uint8_t *grid,
                             uint64_t vs, cudaStream_t st, const LaunchCfg &cfg);
 cudaError_t launch_write_f32(int r, int s, int map, int vk, float *grid,

@@ -115,3 +115,16 @@ def uniform_sparse(r: int, seed: int):
     values (float32)."""
     xs, ys = gasket_cells(r)
     return (ys << r) | xs, uniform_at(r, xs, ys, seed)
+
+
+def batch_levels(count: int, lo: int, hi: int, seed: int) -> list[int]:
+    """Levels of a batch of gaskets drawn uniformly from lo..hi (numpy PCG64
+    stream seeded with `seed`)."""
+    rng = np.random.default_rng(seed)
+    return [int(v) for v in rng.integers(lo, hi + 1, count)]
+
+
+def instance_seed(seed: int, i: int) -> int:
+    """Seed of gasket i of a batch: seed + i * 2^32 (distinct streams)."""
+    return int(seed) + (int(i) << 32)
+

@@ -34,3 +34,11 @@ WRITE_PRESERVE = dict(map="lambda_unroll", rho=32, order="rowmajor", store="stag
 STENCILS = dict(levels=(14, 15), ca_p=0.3, ca_seed=0, ca_steps=256,
                 diff_seed=0, diff_steps=100, alpha=0.2,
                 ca_rho=64, diff_rho=64, bbox_ca_rho=64, bbox_diff_rho=64)
+
+# Batched: 64 gaskets with levels drawn uniformly from 8..14 (seed 2), each
+# with its own uint8 CA state (Bernoulli(0.3), seed 2 + i * 2^32), 64 CA
+# steps each: one launch per step over the prefix-summed work list (captured
+# in a CUDA graph, autotuned) against 64 separate per-gasket launches.
+BATCH = dict(count=64, level_lo=8, level_hi=14, level_seed=2, ca_p=0.3, ca_seed=2,
+             steps=64, autotune_steps=4)
+

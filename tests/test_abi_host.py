@@ -131,3 +131,36 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(sg, "_lib", None)
     with pytest.raises(ImportError):
         sg.lib()
+
+
+def test_batch_workspace_bytes(L):
+    assert sg.lib().sg_batch_workspace_bytes(0) == 0
+    assert sg.lib().sg_batch_workspace_bytes(65536) == 0
+    for count in (1, 2, 3, 64, 1000):
+        b = sg.lib().sg_batch_workspace_bytes(count)
+        assert b % 16 == 0 and b >= 4 * (count + 1) + 4 * count + 16 * count
+
+
+def test_batch_plan_validation_is_host_side(L):
+    import ctypes
+    n = 3
+    lv = (ctypes.c_int * n)(8, 9, 10)
+    pa = (ctypes.c_void_p * n)(FAKE, FAKE + 0x100000, FAKE + 0x200000)
+    pb = (ctypes.c_void_p * n)(FAKE + 0x300000, FAKE + 0x400000, FAKE + 0x500000)
+    ws = sg.lib().sg_batch_workspace_bytes(n)
+    plan = sg.BatchPlan()
+    call = lambda **k: sg.lib().sg_batch_ca_plan(
+        k.get("count", n), k.get("lv", lv), pa, k.get("pb", pb), k.get("rho", 16),
+        k.get("ws", FAKE + 0x900000), k.get("wsb", ws), ctypes.byref(plan), None)
+    assert call(rho=8) == sg.SG_EUNSUPPORTED
+    assert call(count=0) == sg.SG_EINVAL
+    assert call(wsb=ws - 16) == sg.SG_EINVAL
+    assert call(ws=FAKE + 0x900004) == sg.SG_EINVAL
+    assert call(lv=(ctypes.c_int * n)(8, 3, 10)) == sg.SG_EINVAL          # level < log2(rho)
+    assert call(lv=(ctypes.c_int * n)(8, 17, 10)) == sg.SG_EINVAL
+    assert call(pb=(ctypes.c_void_p * n)(FAKE, FAKE + 0x400000, FAKE + 0x500000)) == sg.SG_EINVAL
+    bad = sg.BatchPlan()
+    assert sg.lib().sg_batch_ca_step(ctypes.byref(bad), 0, None, None) == sg.SG_EINVAL
+    h = ctypes.c_void_p()
+    assert sg.lib().sg_batch_ca_graph_create(ctypes.byref(bad), 4, 0, None, ctypes.byref(h)) == sg.SG_EINVAL
+    assert sg.lib().sg_graph_launch(None, None) == sg.SG_EINVAL
