@@ -340,6 +340,7 @@ def run_ours(args, grp: Group):
         return out
     if grp.rank == 0 and not args.no_extras:
         out["compare"] = compare_workloads(sg, torch, dev, stream, w, grid, launch_ms)
+        out["compare"]["batched_ca"] = batched_workload(sg, torch, dev, stream)
     del grid
     torch.cuda.empty_cache()
     out["e2e"] = measure_e2e(sg, torch, dev, stream, w, grp, min(args.steps, 4))
@@ -376,6 +377,78 @@ def run_stencil_quick(args, sg, torch, dev, stream):
     return {"workload": f"{args.workload} step, level {r}, rho {rho}, lambda",
             "unit": UNIT, "value": round(3 ** r / (total_ms / args.steps / 1e3) / 1e9, 3),
             "launch_ms_mean": round(statistics.mean(per), 5), "steps": args.steps}
+
+
+def batched_workload(sg, torch, dev, stream):
+    """64 gaskets of levels 8..14: 64 CA steps as (a) one launch per gasket
+    per step, eager and captured in a CUDA graph, and (b) one batched launch
+    per step over the prefix-summed work list, eager and as a CUDA graph
+    (autotuned rho / order / CTAs per SM)."""
+    from paper_1706_04552_gb300 import inputs, workloads
+    w = workloads.BATCH
+    levels = inputs.batch_levels(w["count"], w["level_lo"], w["level_hi"], w["level_seed"])
+    a, b = [], []
+    for i, r in enumerate(levels):
+        idx, vals = inputs.ca_seed_sparse(r, w["ca_p"], inputs.instance_seed(w["ca_seed"], i))
+        t = torch.zeros(1 << (2 * r), dtype=torch.uint8, device=dev)
+        t[torch.from_numpy(idx).to(dev)] = torch.from_numpy(vals).to(dev)
+        a.append(t)
+        b.append(torch.zeros_like(t))
+    steps = w["steps"]
+    cells = sum(3 ** r for r in levels) * steps
+    batch = sg.CABatch(levels, a, b, autotune=w["autotune_steps"], stream=stream)
+    opts = batch.opts
+    order = "interleaved" if opts.order == 1 else "rowmajor"
+    res = {"gaskets": len(levels), "levels": levels, "steps": steps,
+           "cells_per_step": sum(3 ** r for r in levels),
+           "tuned": {"rho": batch.rho, "order": order, "ctas_per_sm": opts.ctas_per_sm}}
+
+    def per_instance():
+        for k in range(steps):
+            for i, r in enumerate(levels):
+                src, dst = (a[i], b[i]) if k % 2 == 0 else (b[i], a[i])
+                sg.ca_step(src, dst, r, batch.rho, "lambda", stream, order=order)
+
+    def batched():
+        for k in range(steps):
+            batch.step(k & 1, stream)
+
+    g = batch.graph(steps, 0)
+    torch_graph = torch.cuda.CUDAGraph()
+    per_instance()                                 # warm-up (and occupancy caches)
+    torch.cuda.synchronize(dev)
+    with torch.cuda.graph(torch_graph, stream=torch.cuda.Stream(dev)):
+        s2 = torch.cuda.current_stream(dev)
+        for k in range(steps):
+            for i, r in enumerate(levels):
+                src, dst = (a[i], b[i]) if k % 2 == 0 else (b[i], a[i])
+                sg.ca_step(src, dst, r, batch.rho, "lambda", s2, order=order)
+    torch.cuda.synchronize(dev)
+
+    def timed(fn, reps=3):
+        fn()
+        torch.cuda.synchronize(dev)
+        ms, _ = time_launches(fn, reps, stream)
+        return ms / reps
+
+    t_pi = timed(per_instance)
+    t_pig = timed(lambda: torch_graph.replay())
+    t_b = timed(batched)
+    t_bg = timed(lambda: g.launch(stream))
+    g.close()
+    res.update({
+        "per_gasket_eager": {"ms": round(t_pi, 3), "GCells_s": _rate(cells, t_pi),
+                             "launches": steps * len(levels)},
+        "per_gasket_graph": {"ms": round(t_pig, 3), "GCells_s": _rate(cells, t_pig),
+                             "launches": steps * len(levels)},
+        "batched_eager": {"ms": round(t_b, 3), "GCells_s": _rate(cells, t_b), "launches": steps},
+        "batched_graph": {"ms": round(t_bg, 3), "GCells_s": _rate(cells, t_bg), "launches": steps},
+        "speedup_batched_graph_over_per_gasket_eager": round(t_pi / t_bg, 3),
+        "speedup_batched_graph_over_per_gasket_graph": round(t_pig / t_bg, 3),
+    })
+    del a, b, batch
+    torch.cuda.empty_cache()
+    return res
 
 
 def _rate(cells, ms):
