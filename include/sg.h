@@ -287,6 +287,39 @@ SG_API sg_status sg_batch_ca_autotune(int count, const int *levels, uint8_t *con
                                       void *stream);
 
 /*
+ * sg_batch_ca_step_noalloc -- one batch step for callers that cannot allocate
+ * device memory.  The paper has no counterpart: this is a library
+ * convenience.
+ *
+ * Who needs it: code that must not allocate device memory at the moment it
+ * steps a batch -- a real-time loop that fixed its memory budget at start-up,
+ * a plugin whose host application owns every device allocation, a server
+ * that has already given all of HBM to its own pool.  There a cudaMalloc (or
+ * any allocating library call, torch's included) can fail, stall the device
+ * or break the host's accounting.  This call allocates nothing: the work list
+ * that sg_batch_ca_plan would put in a caller-provided workspace lives in a
+ * fixed array inside libsg instead, sized for SG_NOALLOC_MAX_GASKETS gaskets
+ * (about 24 KB; every GPU that loads the library keeps it until the process
+ * exits).  The caller still provides the gaskets' state buffers.
+ *
+ * Arguments as for sg_batch_ca_plan plus a sg_batch_ca_step parity; each
+ * call rebuilds the work list (one host-to-device copy on `stream`) and then
+ * launches the step, with results identical to sg_batch_ca_step.
+ *   - More than SG_NOALLOC_MAX_GASKETS gaskets: SG_EINVAL, with the reason in
+ *     sg_last_error_string().
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - Every call shares the one array, and it keeps the last call's contents.
+ *     Calls whose copies and kernels can overlap on the GPU (for example on
+ *     two streams without ordering between them) race on it: order them on
+ *     one stream or with events.
+ */
+#define SG_NOALLOC_MAX_GASKETS 1024
+SG_API sg_status sg_batch_ca_step_noalloc(int count, const int *levels, uint8_t *const *buf_a,
+                                          uint8_t *const *buf_b, int rho, int parity,
+                                          const sg_launch_opts *opts, void *stream);
+
+/*
  * sg_device_status -- report and clear the device status word of the current
  * device.  Kernels with bounded waits (SG_STORE_TMA) record a wait that gave
  * up there instead of spinning; the call synchronises `stream` and returns

@@ -72,6 +72,11 @@ bool read_launch_opts(const sg_launch_opts *o, LaunchCfg *cfg)
     return true;
 }
 
+void set_last_error_message(const char *msg)
+{
+    std::snprintf(g_last_error, sizeof g_last_error, "%s", msg);
+}
+
 sg_status set_last_cuda_error(cudaError_t e)
 {
     std::snprintf(g_last_error, sizeof g_last_error, "%s: %s", cudaGetErrorName(e),

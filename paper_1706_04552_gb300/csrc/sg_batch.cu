@@ -358,3 +358,109 @@ sg_status sg_batch_ca_autotune(int count, const int *levels, uint8_t *const *buf
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// A batch step that allocates nothing.
+//
+// Some callers cannot allocate device memory when they want to step a batch:
+// a real-time loop that reserved its whole memory budget at start-up, a
+// plugin whose host application owns every device allocation, or a server
+// that has already handed all of HBM to its own pool.  For them a cudaMalloc
+// (or any allocating library call, torch's included) can fail, stall the
+// device or break the host's memory accounting.  This variant of the batch
+// step keeps its work list in the fixed array below instead of a workspace
+// the caller provides; the caller still passes the gaskets' state buffers.
+// ---------------------------------------------------------------------------
+namespace sg {
+namespace {
+
+constexpr int kNoAllocMaxGaskets = SG_NOALLOC_MAX_GASKETS;
+
+// Fixed-size scratch: the work list of at most kNoAllocMaxGaskets gaskets.
+// Every device that loads the library keeps it until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_worklist[(4u * (kNoAllocMaxGaskets + 1) + 15u) / 16u * 16u + (4u * kNoAllocMaxGaskets + 15u) / 16u * 16u + 16u * kNoAllocMaxGaskets];
+
+std::atomic<void *> g_noalloc_addr[64];
+
+// Device address of the scratch array on the current device, looked up once
+// per device (with that device current) on its first use.
+cudaError_t noalloc_scratch(void **out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    void *p = g_noalloc_addr[dev].load(std::memory_order_acquire);
+    if (p == nullptr) {
+        e = cudaGetSymbolAddress(&p, g_noalloc_worklist);
+        if (e != cudaSuccess) return e;
+        g_noalloc_addr[dev].store(p, std::memory_order_release);
+    }
+    *out = p;
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace sg
+
+extern "C" sg_status sg_batch_ca_step_noalloc(int count, const int *levels,
+                                              uint8_t *const *buf_a, uint8_t *const *buf_b,
+                                              int rho, int parity, const sg_launch_opts *opts,
+                                              void *stream)
+{
+    if (count > kNoAllocMaxGaskets) {
+        set_last_error_message("sg_batch_ca_step_noalloc: more gaskets than the fixed work-list "
+                               "array holds (SG_NOALLOC_MAX_GASKETS)");
+        return SG_EINVAL;
+    }
+    if (count < 1 || levels == nullptr || buf_a == nullptr || buf_b == nullptr) return SG_EINVAL;
+    if (parity != 0 && parity != 1) return SG_EINVAL;
+    if (rho != 16 && rho != 32 && rho != 64) return SG_EUNSUPPORTED;
+    LaunchCfg cfg;
+    if (!read_launch_opts(opts, &cfg)) return SG_EINVAL;
+    int s = 0;
+    while ((1 << s) < rho) ++s;
+
+    // Host image of the work list in a fixed per-thread buffer (no heap):
+    // the same layout and the same checks as sg_batch_ca_plan.
+    thread_local unsigned char img[sizeof(g_noalloc_worklist)];
+    const WsLayout L = ws_layout(count);
+    uint32_t *prefix = reinterpret_cast<uint32_t *>(img + L.prefix);
+    int32_t *level = reinterpret_cast<int32_t *>(img + L.level);
+    uint64_t *pa = reinterpret_cast<uint64_t *>(img + L.a);
+    uint64_t *pb = reinterpret_cast<uint64_t *>(img + L.b);
+    uint64_t total = 0;
+    int max_level = 0;
+    for (int i = 0; i < count; ++i) {
+        const int r = levels[i];
+        if (r < s || r > 16) return SG_EINVAL;
+        if (buf_a[i] == nullptr || buf_b[i] == nullptr || buf_a[i] == buf_b[i]) return SG_EINVAL;
+        if (((uintptr_t)buf_a[i] & 15) || ((uintptr_t)buf_b[i] & 15)) return SG_EINVAL;
+        prefix[i] = (uint32_t)total;
+        level[i] = r;
+        pa[i] = (uint64_t)(uintptr_t)buf_a[i];
+        pb[i] = (uint64_t)(uintptr_t)buf_b[i];
+        total += (uint64_t)pow3i(r - s);
+        max_level = std::max(max_level, r);
+        if (total >= (1ull << 32)) return SG_EINVAL;
+    }
+    prefix[count] = (uint32_t)total;
+
+    void *scratch = nullptr;
+    cudaError_t e = noalloc_scratch(&scratch);
+    if (e != cudaSuccess) return cuda_fail(e);
+    // The whole work list the step reads is rewritten on `stream` first, so
+    // nothing in the array has to start at zero.  (Pageable source: the copy
+    // is staged before the call returns, so `img` can be reused next call.)
+    e = cudaMemcpyAsync(scratch, img, L.total, cudaMemcpyHostToDevice, (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    sg_batch_plan plan{};
+    plan.workspace = scratch;
+    plan.workspace_bytes = sizeof(g_noalloc_worklist);
+    plan.count = count;
+    plan.rho = rho;
+    plan.total_tiles = (uint32_t)total;
+    plan.max_level = (uint32_t)max_level;
+    e = launch_batch(&plan, parity, (cudaStream_t)stream, cfg);
+    return e == cudaSuccess ? SG_OK : cuda_fail(e);
+}

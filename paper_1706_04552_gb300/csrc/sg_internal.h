@@ -31,6 +31,9 @@ namespace sg {
 // sg_launch_opts (NULL = defaults) -> LaunchCfg; false on a bad value.
 bool read_launch_opts(const sg_launch_opts *o, LaunchCfg *cfg);
 
+// Record a message for sg_last_error_string().
+void set_last_error_message(const char *msg);
+
 // Record a CUDA error for sg_last_error_string(); returns SG_ECUDA
 // (SG_EUNSUPPORTED for cudaErrorNotSupported).
 sg_status set_last_cuda_error(cudaError_t e);
