@@ -341,6 +341,7 @@ def run_ours(args, grp: Group):
     if grp.rank == 0 and not args.no_extras:
         out["compare"] = compare_workloads(sg, torch, dev, stream, w, grid, launch_ms)
         out["compare"]["batched_ca"] = batched_workload(sg, torch, dev, stream)
+        out["serving"] = serving_workload()
     del grid
     torch.cuda.empty_cache()
     out["e2e"] = measure_e2e(sg, torch, dev, stream, w, grp, min(args.steps, 4))
@@ -449,6 +450,23 @@ def batched_workload(sg, torch, dev, stream):
     del a, b, batch
     torch.cuda.empty_cache()
     return res
+
+
+def serving_workload():
+    """Continuous batching of CA-step requests (Poisson arrivals, 500 resident
+    gaskets of levels 6..15) with batched launches and, on the same trace,
+    with one launch per active gasket; plus the same comparison at ten times
+    the arrival rate."""
+    from paper_1706_04552_gb300.serve import ServeConfig, Server, make_trace, summarize
+    out = {}
+    for tag, rate in (("offered_2000rps", 2000.0), ("offered_20000rps", 20000.0)):
+        for mode in ("batched", "per_gasket"):
+            cfg = ServeConfig(rate=rate, duration=2.0 if rate <= 2000 else 0.5, mode=mode)
+            server = Server(cfg)
+            res = server.run(make_trace(cfg))
+            out.setdefault(tag, {})[mode] = summarize(res, cfg)
+            del server
+    return out
 
 
 def _rate(cells, ms):

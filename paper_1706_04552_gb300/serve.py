@@ -1,0 +1,268 @@
+"""Continuous-batching server for CA-step requests on resident gaskets.
+
+Requests ask for k steps of the gasket-restricted B3/S23 automaton on one
+of many resident gaskets of different levels.  The serving loop:
+
+  * admits requests as they arrive (their arrival times are real time on
+    the host clock) into per-gasket FIFOs;
+  * keeps every gasket's state on the device while it fits a device-memory
+    budget; a gasket that does not fit is brought in from pinned host memory
+    after evicting the least recently used idle gaskets (their current state
+    goes back to pinned host memory);
+  * runs iterations: every gasket whose head request still has steps left
+    advances one step, all of them in ONE batched launch (a prefix-summed
+    work list over the active gaskets' lambda block spaces, sg_batch_ca_*),
+    so requests that arrive while others are on the GPU join at the next
+    iteration; a request completes when its last step has run;
+  * reports per-request latency (arrival to completion) and throughput.
+
+mode="per_gasket" runs the same scheduler with one single-gasket launch per
+active gasket per iteration instead of the batched launch, for comparison.
+
+Every gasket's state follows the plain per-gasket sequence of CA steps in
+arrival order of its requests, so each result equals stepping the gasket
+alone; tests check that against single-gasket runs and the CPU oracle.
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import time
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class ServeConfig:
+    gaskets: int = 500
+    level_min: int = 6
+    level_max: int = 15
+    level_decay: float = 0.5          # P(level = min + k) proportional to decay^k
+    rate: float = 2000.0              # mean arrivals per second (Poisson)
+    steps_min: int = 1
+    steps_max: int = 32
+    duration: float = 2.0             # seconds of arrivals
+    budget_bytes: int = 40 << 30      # device bytes for resident gasket states
+    seed: int = 3
+    ca_p: float = 0.3
+    rho: int = 32
+    mode: str = "batched"             # or "per_gasket"
+
+
+def gasket_levels(cfg: ServeConfig) -> np.ndarray:
+    """Levels drawn geometrically toward small levels (seeded)."""
+    ks = np.arange(cfg.level_max - cfg.level_min + 1)
+    p = cfg.level_decay ** ks
+    p /= p.sum()
+    rng = np.random.default_rng(cfg.seed)
+    return cfg.level_min + rng.choice(len(ks), size=cfg.gaskets, p=p)
+
+
+def make_trace(cfg: ServeConfig):
+    """Poisson arrivals over cfg.duration: (arrival s, gasket id, steps)."""
+    rng = np.random.default_rng(cfg.seed + 1)
+    n = int(rng.poisson(cfg.rate * cfg.duration))
+    t = np.sort(rng.uniform(0.0, cfg.duration, n))
+    g = rng.integers(0, cfg.gaskets, n)
+    k = rng.integers(cfg.steps_min, cfg.steps_max + 1, n)
+    return t, g, k
+
+
+class _Gasket:
+    __slots__ = ("gid", "level", "n2", "host", "cur", "nxt", "resident", "queue",
+                 "last_use", "steps_done")
+
+    def __init__(self, gid, level, host):
+        self.gid = gid
+        self.level = int(level)
+        self.n2 = 1 << (2 * self.level)
+        self.host = host                  # pinned host copy (current state when evicted)
+        self.cur = self.nxt = None        # device buffers while resident
+        self.resident = False
+        self.queue = []                   # [request index, steps left] in arrival order
+        self.last_use = 0
+        self.steps_done = 0
+
+    @property
+    def device_bytes(self):
+        return 2 * self.n2
+
+
+class Server:
+    """The serving loop over one CUDA stream (see the module docstring)."""
+
+    def __init__(self, cfg: ServeConfig, initial_states=None, device="cuda"):
+        import torch
+        import paper_1706_04552_gb300 as sg
+        from paper_1706_04552_gb300 import inputs
+        self.torch, self.sg, self.cfg = torch, sg, cfg
+        self.dev = torch.device(device)
+        self.stream = torch.cuda.current_stream(self.dev)
+        levels = gasket_levels(cfg)
+        self.gaskets = []
+        for i, r in enumerate(levels):
+            host = torch.empty(1 << (2 * int(r)), dtype=torch.uint8, pin_memory=True)
+            if initial_states is not None:
+                host.copy_(torch.from_numpy(initial_states[i].ravel()))
+            else:
+                idx, vals = inputs.ca_seed_sparse(int(r), cfg.ca_p, inputs.instance_seed(cfg.seed, i))
+                host.zero_()
+                host[torch.from_numpy(idx)] = torch.from_numpy(vals)
+            self.gaskets.append(_Gasket(i, r, host))
+        self.used = 0
+        self.evictions = 0
+        self.loads = 0
+        cnt = len(self.gaskets)
+        self.ws = torch.empty(int(sg.lib().sg_batch_workspace_bytes(cnt)), dtype=torch.uint8,
+                              device=self.dev)
+        self._lv = np.zeros(cnt, dtype=np.int32)
+        self._pa = np.zeros(cnt, dtype=np.uint64)
+        self._pb = np.zeros(cnt, dtype=np.uint64)
+        self._plan = sg.BatchPlan()
+        self.tick = 0
+
+    # ------------------------------------------------------------ residency
+    def _evict_one(self, protect):
+        idle = [g for g in self.gaskets if g.resident and not g.queue and g.gid not in protect]
+        if not idle:
+            return False
+        v = min(idle, key=lambda g: g.last_use)
+        v.host.copy_(v.cur, non_blocking=True)           # current state back to host
+        self.stream.synchronize()
+        v.cur = v.nxt = None
+        v.resident = False
+        self.used -= v.device_bytes
+        self.evictions += 1
+        return True
+
+    def _make_resident(self, g, protect):
+        if g.resident:
+            return True
+        while self.used + g.device_bytes > self.cfg.budget_bytes:
+            if not self._evict_one(protect):
+                return False
+        torch = self.torch
+        g.cur = torch.empty(g.n2, dtype=torch.uint8, device=self.dev)
+        g.nxt = torch.zeros(g.n2, dtype=torch.uint8, device=self.dev)
+        g.cur.copy_(g.host, non_blocking=True)
+        g.resident = True
+        self.used += g.device_bytes
+        self.loads += 1
+        return True
+
+    # ------------------------------------------------------------- stepping
+    def _step(self, active):
+        sg = self.sg
+        if self.cfg.mode == "per_gasket":
+            for g in active:
+                sg.ca_step(g.cur, g.nxt, g.level, min(self.cfg.rho, 1 << g.level), "lambda",
+                           self.stream)
+            return
+        m = len(active)
+        for j, g in enumerate(active):
+            self._lv[j] = g.level
+            self._pa[j] = g.cur.data_ptr()
+            self._pb[j] = g.nxt.data_ptr()
+        L = sg.lib()
+        st = L.sg_batch_ca_plan(m, self._lv.ctypes.data, self._pa.ctypes.data,
+                                self._pb.ctypes.data, self.cfg.rho, self.ws.data_ptr(),
+                                self.ws.numel(), ctypes.byref(self._plan),
+                                self.stream.cuda_stream)
+        sg._check("sg_batch_ca_plan", int(st))
+        sg._check("sg_batch_ca_step", int(L.sg_batch_ca_step(
+            ctypes.byref(self._plan), 0, None, self.stream.cuda_stream)))
+
+    # ----------------------------------------------------------------- loop
+    def run(self, trace, on_complete=None):
+        """Serve a trace (arrival s, gasket, steps).  on_complete(req, gasket)
+        is called right after a request's last step (state in gasket.cur).
+        Returns per-request arrival/completion times and counters."""
+        t_arr, g_id, k_steps = trace
+        nreq = len(t_arr)
+        done_at = np.full(nreq, np.nan)
+        start_at = np.full(nreq, np.nan)
+        busy = 0.0
+        iters = 0
+        launches = 0
+        cells = 0
+        nxt = 0
+        remaining = nreq
+        pending = {}                      # gasket id -> gasket, for gaskets with requests
+        t0 = time.perf_counter()
+        while remaining:
+            now = time.perf_counter() - t0
+            while nxt < nreq and t_arr[nxt] <= now:
+                g = self.gaskets[int(g_id[nxt])]
+                g.queue.append([nxt, int(k_steps[nxt])])
+                pending[g.gid] = g
+                nxt += 1
+            if not pending:
+                if nxt < nreq:
+                    dt = t_arr[nxt] - (time.perf_counter() - t0)
+                    if dt > 0:
+                        time.sleep(min(dt, 0.0001))
+                continue
+            waiting = list(pending.values())
+            protect = set(pending)
+            active = [g for g in waiting if self._make_resident(g, protect)]
+            if not active:
+                raise RuntimeError("a requested gasket does not fit the device budget")
+            self.tick += 1
+            tb = time.perf_counter()
+            self._step(active)
+            self.stream.synchronize()
+            te = time.perf_counter()
+            busy += te - tb
+            iters += 1
+            launches += 1 if self.cfg.mode == "batched" else len(active)
+            tdone = te - t0
+            for g in active:
+                g.cur, g.nxt = g.nxt, g.cur
+                g.last_use = self.tick
+                g.steps_done += 1
+                cells += 3 ** g.level
+                head = g.queue[0]
+                if np.isnan(start_at[head[0]]):
+                    start_at[head[0]] = tb - t0
+                head[1] -= 1
+                if head[1] == 0:
+                    g.queue.pop(0)
+                    done_at[head[0]] = tdone
+                    remaining -= 1
+                    if not g.queue:
+                        del pending[g.gid]
+                    if on_complete is not None:
+                        on_complete(head[0], g)
+        wall = time.perf_counter() - t0
+        lat = done_at - t_arr
+        return {"requests": nreq, "wall_s": wall, "iterations": iters, "launches": launches,
+                "busy_s": busy, "cell_steps": cells, "latency_s": lat, "arrival_s": t_arr,
+                "evictions": self.evictions, "loads": self.loads}
+
+    def state_of(self, gid):
+        """Current state of gasket gid (host numpy copy)."""
+        g = self.gaskets[gid]
+        n = 1 << g.level
+        src = g.cur if g.resident else g.host
+        self.stream.synchronize()
+        return src.cpu().numpy().reshape(n, n)
+
+
+def summarize(res, cfg: ServeConfig):
+    lat_ms = res["latency_s"] * 1e3
+    return {
+        "mode": cfg.mode,
+        "requests": int(res["requests"]),
+        "offered_rate_rps": cfg.rate,
+        "throughput_rps": round(res["requests"] / res["wall_s"], 1),
+        "cell_steps_per_s_G": round(res["cell_steps"] / res["wall_s"] / 1e9, 4),
+        "gpu_busy_fraction": round(res["busy_s"] / res["wall_s"], 4),
+        "latency_ms_p50": round(float(np.percentile(lat_ms, 50)), 3),
+        "latency_ms_p99": round(float(np.percentile(lat_ms, 99)), 3),
+        "latency_ms_max": round(float(np.max(lat_ms)), 3),
+        "iterations": int(res["iterations"]),
+        "launches": int(res["launches"]),
+        "evictions": int(res["evictions"]),
+        "loads": int(res["loads"]),
+        "wall_s": round(res["wall_s"], 3),
+    }

@@ -1,0 +1,29 @@
+"""Host-side pieces of the server: the seeded level mix and request trace."""
+import numpy as np
+
+from paper_1706_04552_gb300.serve import ServeConfig, gasket_levels, make_trace
+
+
+def test_levels_are_geometric_toward_small_levels():
+    cfg = ServeConfig(gaskets=20000)
+    lv = gasket_levels(cfg)
+    assert lv.min() >= 6 and lv.max() <= 15
+    counts = np.bincount(lv - 6, minlength=10)
+    # P(6 + k) proportional to 0.5^k: each level about half as common as the one below
+    for k in range(4):
+        assert 0.4 < counts[k + 1] / counts[k] < 0.6
+    assert np.array_equal(gasket_levels(cfg), lv)           # seeded
+
+
+def test_trace_is_poisson_and_seeded():
+    cfg = ServeConfig(rate=2000.0, duration=5.0)
+    t, g, k = make_trace(cfg)
+    assert abs(len(t) - 10000) < 4 * 100                     # mean 10000, sd 100
+    assert np.all(np.diff(t) >= 0) and t[0] >= 0 and t[-1] <= 5.0
+    gaps = np.diff(t)
+    assert abs(gaps.mean() - 1 / 2000) < 0.05 / 2000         # exponential gaps
+    assert abs(np.std(gaps) / gaps.mean() - 1.0) < 0.05
+    assert g.min() >= 0 and g.max() < cfg.gaskets
+    assert k.min() >= 1 and k.max() <= 32
+    t2, g2, k2 = make_trace(cfg)
+    assert np.array_equal(t, t2) and np.array_equal(g, g2) and np.array_equal(k, k2)
