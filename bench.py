@@ -340,6 +340,7 @@ def run_ours(args, grp: Group):
         return out
     if grp.rank == 0 and not args.no_extras:
         out["compare"] = compare_workloads(sg, torch, dev, stream, w, grid, launch_ms)
+        out["compare"]["level_sweep"] = level_sweep(sg, torch, dev, w)
         out["compare"]["batched_ca"] = batched_workload(sg, torch, dev, stream)
         out["serving"] = serving_workload()
     del grid
@@ -450,6 +451,46 @@ def batched_workload(sg, torch, dev, stream):
     del a, b, batch
     torch.cuda.empty_cache()
     return res
+
+
+def level_sweep(sg, torch, dev, w):
+    """lambda vs bounding box at every level 8..16 (uint8, hash values, the
+    headline's intra-tile map, walking order and stores, rho = min(64, n)):
+    GPU time per launch from CUDA-graph replays of 20 back-to-back launches,
+    so host launch overhead does not mask the small levels."""
+    out = {}
+    for r in range(8, 17):
+        n = 1 << r
+        rho = min(64, n)
+        g = torch.zeros(n * n, dtype=torch.uint8, device=dev)
+        row = {}
+        for name, mapk in (("lambda", w["map"]), ("bbox", "bbox")):
+            cap = torch.cuda.Stream(dev)
+            sg.map_write(g, r, rho, mapk, "hash", w["seed"], order=w["order"], store=w["store"])
+            torch.cuda.synchronize(dev)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=cap):
+                for _ in range(20):
+                    sg.map_write(g, r, rho, mapk, "hash", w["seed"], torch.cuda.current_stream(dev),
+                                 order=w["order"], store=w["store"])
+            graph.replay()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s = torch.cuda.current_stream(dev)
+            e0.record(s)
+            for _ in range(5):
+                graph.replay()
+            e1.record(s)
+            e1.synchronize()
+            us = e0.elapsed_time(e1) * 1e3 / 100
+            row[name + "_us"] = round(us, 2)
+            del graph
+        row["speedup"] = round(row["bbox_us"] / row["lambda_us"], 3)
+        row["GCells_s_lambda"] = round(3 ** r / row["lambda_us"] / 1e3, 2)
+        out[f"r{r}"] = row
+        del g
+        torch.cuda.empty_cache()
+    return out
 
 
 def serving_workload():
