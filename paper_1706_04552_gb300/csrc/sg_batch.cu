@@ -83,20 +83,18 @@ template <int S>
 __global__ void __launch_bounds__(kStencilThreads)
 ca_batch_kernel(BatchView bv, uint32_t total, int parity, int order)
 {
-    using G = CaGroup<S>;
-    __shared__ __align__(16) uint8_t sm[G::TPC * G::TILE];
-    __shared__ CaTile tiles[G::TPC];
+    using G = StencilGroup<uint8_t, S>;
+    __shared__ __align__(16) uint8_t sm[2 * G::TPC * G::TILE];
+    __shared__ StencilTile<uint8_t> tiles[2 * G::TPC];
 
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     LambdaLane ll;
-    ll.init(lane, 0, order);
+    ll.init(threadIdx.x & 31, 0, order);
     const uint32_t groups = (total + G::TPC - 1) / G::TPC;
-
-    for (uint32_t g = blockIdx.x; g < groups; g += gridDim.x) {
-        __syncthreads();
+    auto decode = [&](uint64_t g, StencilTile<uint8_t> *dst) {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         for (int t = warp; t < G::TPC; t += kStencilThreads / 32) {
-            const uint32_t q = g * G::TPC + (uint32_t)t;
-            CaTile tl{kNoTile, kNoTile, 0, nullptr, nullptr};
+            const uint32_t q = (uint32_t)g * G::TPC + (uint32_t)t;
+            StencilTile<uint8_t> tl{kNoTile, kNoTile, 0, nullptr, nullptr};
             if (q < total) {                                  // warp-uniform
                 const uint32_t i = batch_instance(bv.prefix, bv.count, q);
                 const int r = __ldg(bv.level + i);
@@ -107,14 +105,17 @@ ca_batch_kernel(BatchView bv, uint32_t total, int parity, int order)
                 const uint32_t b = local / W, a = local - b * W;
                 const uint2 c = ll.decode(a, b);
                 const uint64_t pa = __ldg(bv.buf_a + i), pb = __ldg(bv.buf_b + i);
-                tl = CaTile{c.x, c.y, r, reinterpret_cast<const uint8_t *>(parity ? pb : pa),
-                            reinterpret_cast<uint8_t *>(parity ? pa : pb)};
+                tl = StencilTile<uint8_t>{c.x, c.y, r,
+                                          reinterpret_cast<const uint8_t *>(parity ? pb : pa),
+                                          reinterpret_cast<uint8_t *>(parity ? pa : pb)};
             }
-            if (lane == 0) tiles[t] = tl;
+            if (lane == 0) dst[t] = tl;
         }
-        __syncthreads();
-        ca_group_step<S>(sm, tiles);
-    }
+    };
+    auto compute = [](const uint8_t *buf, const StencilTile<uint8_t> *slot) {
+        ca_compute_group<S>(buf, slot);
+    };
+    stencil_pipeline<uint8_t, S>(sm, tiles, groups, decode, compute);
 }
 
 template <int S>
@@ -122,7 +123,7 @@ cudaError_t launch_batch_t(const sg_batch_plan *p, int parity, cudaStream_t st,
                            const LaunchCfg &cfg)
 {
     static std::atomic<int> occ{0};
-    constexpr int TPC = CaGroup<S>::TPC;
+    constexpr int TPC = StencilGroup<uint8_t, S>::TPC;
     unsigned grid = 1;
     const uint64_t groups = (p->total_tiles + TPC - 1) / TPC;
     auto k = ca_batch_kernel<S>;

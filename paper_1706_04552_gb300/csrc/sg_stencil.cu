@@ -31,26 +31,26 @@ __global__ void __launch_bounds__(kStencilThreads)
 ca_vec_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int r,
               int order, uint64_t ntiles)
 {
-    using G = CaGroup<S>;
-    __shared__ __align__(16) uint8_t sm[G::TPC * G::TILE];
-    __shared__ CaTile tiles[G::TPC];
+    using G = StencilGroup<uint8_t, S>;
+    __shared__ __align__(16) uint8_t sm[2 * G::TPC * G::TILE];
+    __shared__ StencilTile<uint8_t> tiles[2 * G::TPC];
 
     const int rb = r - S;
     LambdaLane ll;
     ll.init(threadIdx.x & 31, rb, order);
     const uint32_t W = pi_word(order, rb);
     const uint64_t groups = (ntiles + G::TPC - 1) / G::TPC;
-
-    for (uint64_t g = blockIdx.x; g < groups; g += gridDim.x) {
-        __syncthreads();
+    auto decode = [&](uint64_t g, StencilTile<uint8_t> *dst) {
         const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
         for (int t = warp; t < G::TPC; t += kStencilThreads / 32) {
             const uint2 c = decode_tile<MAP>(g * G::TPC + t, ntiles, rb, W, ll);
-            if (lane == 0) tiles[t] = CaTile{c.x, c.y, r, in, out};
+            if (lane == 0) dst[t] = StencilTile<uint8_t>{c.x, c.y, r, in, out};
         }
-        __syncthreads();
-        ca_group_step<S>(sm, tiles);
-    }
+    };
+    auto compute = [](const uint8_t *buf, const StencilTile<uint8_t> *slot) {
+        ca_compute_group<S>(buf, slot);
+    };
+    stencil_pipeline<uint8_t, S>(sm, tiles, groups, decode, compute);
 }
 
 // ---------------------------------------------------------------------------
@@ -115,87 +115,34 @@ ca_cell_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int r,
 }
 
 // ---------------------------------------------------------------------------
-// Diffusion.  deg(x, y) counts the in-grid gasket 4-neighbours.
+// Diffusion (diffuse_cell, in sg_stencil.cuh, gives one cell's update).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ float diffuse_cell(uint32_t x, uint32_t y, uint32_t n,
-                                              float u, float l, float rr, float up,
-                                              float dn, float alpha)
-{
-    if (!in_gasket(x, y)) return 0.0f;
-    const int deg = (x > 0u && in_gasket(x - 1u, y)) + (x + 1u < n && in_gasket(x + 1u, y)) +
-                    (y > 0u && in_gasket(x, y - 1u)) + (y + 1u < n && in_gasket(x, y + 1u));
-    const float sum = (l + rr) + (up + dn);
-    return u + alpha * (sum - (float)deg * u);
-}
-
 // rho >= 4: 4-cell chunks (float4).
 template <int S, int MAP>
 __global__ void __launch_bounds__(kStencilThreads)
 diffuse_vec_kernel(const float *__restrict__ in, float *__restrict__ out, int r,
                    int order, uint64_t ntiles, float alpha)
 {
-    constexpr int RHO = 1 << S, CPR = RHO / 4, CHUNKS = RHO * CPR;
-    constexpr int TPC = CHUNKS >= kStencilThreads ? 1 : kStencilThreads / CHUNKS;
-    constexpr int P = RHO + 8;             // row pitch (floats); interior at 4
-    // whole 32-byte sectors (8 floats) move together when inside the tile
-    constexpr uint32_t kDfGroupMask = ~(uint32_t)((RHO >= 8 ? 8 : 4) - 1);
-    constexpr int TILE = (RHO + 2) * P;
-    constexpr int HALO = 4 * RHO + 4;
-    __shared__ __align__(16) float sm[TPC * TILE];
-    __shared__ uint2 coord[TPC];
+    using G = StencilGroup<float, S>;
+    __shared__ __align__(16) float sm[2 * G::TPC * G::TILE];
+    __shared__ StencilTile<float> tiles[2 * G::TPC];
 
     const int rb = r - S;
-    const uint32_t n = 1u << r;
     LambdaLane ll;
     ll.init(threadIdx.x & 31, rb, order);
     const uint32_t W = pi_word(order, rb);
-    const uint64_t groups = (ntiles + TPC - 1) / TPC;
-
-    for (uint64_t g = blockIdx.x; g < groups; g += gridDim.x) {
-        __syncthreads();
-        decode_tiles<MAP>(coord, TPC, g, ntiles, rb, W, ll);
-        __syncthreads();
-        for (int c = threadIdx.x; c < TPC * CHUNKS; c += kStencilThreads) {
-            const int t = c / CHUNKS, k = c % CHUNKS, ty = k / CPR, cx = k % CPR;
-            const uint2 b = coord[t];
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (b.x != kNoTile) {
-                const uint32_t x = (b.x << S) + 4u * cx, y = (b.y << S) + ty;
-                if (in_gasket(x & kDfGroupMask, y))   // chunk in a touched sector
-                    v = *reinterpret_cast<const float4 *>(in + ((uint64_t)y << r) + x);
-            }
-            *reinterpret_cast<float4 *>(sm + t * TILE + (ty + 1) * P + 4 + 4 * cx) = v;
+    const uint64_t groups = (ntiles + G::TPC - 1) / G::TPC;
+    auto decode = [&](uint64_t g, StencilTile<float> *dst) {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        for (int t = warp; t < G::TPC; t += kStencilThreads / 32) {
+            const uint2 c = decode_tile<MAP>(g * G::TPC + t, ntiles, rb, W, ll);
+            if (lane == 0) dst[t] = StencilTile<float>{c.x, c.y, r, in, out};
         }
-        for (int c = threadIdx.x; c < TPC * HALO; c += kStencilThreads) {
-            const int t = c / HALO, h = c % HALO;
-            int row, col;
-            halo_slot<RHO>(h, row, col);
-            const uint2 b = coord[t];
-            float v = 0.f;
-            if (b.x != kNoTile)
-                v = load_cell(in, r, (int64_t)(b.x << S) + col, (int64_t)(b.y << S) + row);
-            sm[t * TILE + (row + 1) * P + 4 + col] = v;
-        }
-        __syncthreads();
-        for (int c = threadIdx.x; c < TPC * CHUNKS; c += kStencilThreads) {
-            const int t = c / CHUNKS, k = c % CHUNKS, ty = k / CPR, cx = k % CPR;
-            const uint2 b = coord[t];
-            if (b.x == kNoTile) continue;
-            const uint32_t x = (b.x << S) + 4u * cx, y = (b.y << S) + ty;
-            if (!in_gasket(x & kDfGroupMask, y)) continue;   // sector holds no gasket cell
-            const float *mid = sm + t * TILE + (ty + 1) * P + 4 + 4 * cx;
-            const float4 cu = *reinterpret_cast<const float4 *>(mid - P);
-            const float4 cm = *reinterpret_cast<const float4 *>(mid);
-            const float4 cd = *reinterpret_cast<const float4 *>(mid + P);
-            const float l = mid[-1], rr = mid[4];
-            float4 o;
-            o.x = diffuse_cell(x + 0u, y, n, cm.x, l, cm.y, cu.x, cd.x, alpha);
-            o.y = diffuse_cell(x + 1u, y, n, cm.y, cm.x, cm.z, cu.y, cd.y, alpha);
-            o.z = diffuse_cell(x + 2u, y, n, cm.z, cm.y, cm.w, cu.z, cd.z, alpha);
-            o.w = diffuse_cell(x + 3u, y, n, cm.w, cm.z, rr, cu.w, cd.w, alpha);
-            *reinterpret_cast<float4 *>(out + ((uint64_t)y << r) + x) = o;
-        }
-    }
+    };
+    auto compute = [alpha](const float *buf, const StencilTile<float> *slot) {
+        diffuse_compute_group<S>(buf, slot, alpha);
+    };
+    stencil_pipeline<float, S>(sm, tiles, groups, decode, compute);
 }
 
 // rho <= 2: one cell per thread.
@@ -260,24 +207,14 @@ diffuse_cell_kernel(const float *__restrict__ in, float *__restrict__ out, int r
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-template <int S> struct StencilShape {
-    static constexpr int CA_TPC =
-        S >= 4 ? ((1 << S) * ((1 << S) / 16) >= kStencilThreads
-                      ? 1 : kStencilThreads / ((1 << S) * ((1 << S) / 16)))
-               : kStencilThreads / ((1 << S) * (1 << S));
-    static constexpr int DF_TPC =
-        S >= 2 ? ((1 << S) * ((1 << S) / 4) >= kStencilThreads
-                      ? 1 : kStencilThreads / ((1 << S) * ((1 << S) / 4)))
-               : kStencilThreads / ((1 << S) * (1 << S));
-};
-
 template <int S, int MAP>
 cudaError_t launch_ca_t(int r, const uint8_t *in, uint8_t *out, cudaStream_t st,
                         const LaunchCfg &cfg)
 {
     const int rb = r - S;
     const uint64_t ntiles = (MAP == kMapBBox) ? (1ull << (2 * rb)) : (uint64_t)pow3i(rb);
-    constexpr int TPC = StencilShape<S>::CA_TPC;
+    constexpr int TPC = S >= 4 ? StencilGroup<uint8_t, (S >= 4 ? S : 4)>::TPC
+                               : kStencilThreads / ((1 << S) * (1 << S));
     const uint64_t groups = (ntiles + TPC - 1) / TPC;
     unsigned grid = 1;
     cudaError_t e;
@@ -303,7 +240,8 @@ cudaError_t launch_diffuse_t(int r, const float *in, float *out, float alpha,
 {
     const int rb = r - S;
     const uint64_t ntiles = (MAP == kMapBBox) ? (1ull << (2 * rb)) : (uint64_t)pow3i(rb);
-    constexpr int TPC = StencilShape<S>::DF_TPC;
+    constexpr int TPC = S >= 2 ? StencilGroup<float, (S >= 2 ? S : 2)>::TPC
+                               : kStencilThreads / ((1 << S) * (1 << S));
     const uint64_t groups = (ntiles + TPC - 1) / TPC;
     unsigned grid = 1;
     cudaError_t e;

@@ -108,71 +108,95 @@ __device__ __forceinline__ uint32_t life_rule(uint32_t count, uint32_t self, uin
 
 
 // ---------------------------------------------------------------------------
-// One group of CA tiles (rho >= 16), shared by the single-gasket kernel and
-// the batched kernel: every tile carries its own level and buffers.
+// Tile groups staged asynchronously, shared by the single-gasket and the
+// batched stencil kernels.
+//
+// A CTA works on groups of TPC tiles (TPC * tile chunks ~ 256 threads).  Each
+// tile is staged in shared memory with a one-cell halo as whole 16-byte
+// chunks: ROWS = rho + 2 rows of PC = rho/CE + 2 chunks (one halo chunk on
+// each side), every chunk an asynchronous copy (cp.async) when it holds an
+// in-grid gasket cell and zeros otherwise -- off-gasket cells are 0 in every
+// state, so nothing else needs reading.  Two buffers alternate: the copies of
+// the next group are in flight while the current group is computed.
 // ---------------------------------------------------------------------------
-struct CaTile {
+template <typename T> struct StencilTile {
     uint32_t bx, by;          // block coordinate (kNoTile: no tile in this slot)
     int r;                    // level of the gasket the tile belongs to
-    const uint8_t *in;
-    uint8_t *out;
+    const T *in;
+    T *out;
 };
 
-template <int S> struct CaGroup {
-    static constexpr int RHO = 1 << S, CPR = RHO / 16, CHUNKS = RHO * CPR;
+template <typename T, int S> struct StencilGroup {
+    static constexpr int RHO = 1 << S;
+    static constexpr int CE = 16 / (int)sizeof(T);           // elements per 16-byte chunk
+    static constexpr int CPR = RHO / CE;                      // interior chunks per row
+    static constexpr int CHUNKS = RHO * CPR;                  // interior chunks per tile
     static constexpr int TPC = CHUNKS >= kStencilThreads ? 1 : kStencilThreads / CHUNKS;
-    static constexpr int P = RHO + 32;             // row pitch; interior at byte 16
-    static constexpr int TILE = (RHO + 2) * P;
-    static constexpr int HALO = 4 * RHO + 4;
-    // Chunks are loaded and stored by 32-byte sector when a tile row spans
-    // whole sectors (rho >= 32): a sector holding any gasket cell moves whole
-    // (its off-gasket bytes are 0 in both buffers), so the L2 never has to
-    // fill a half-written sector.  With rho = 16 a sector straddles two
-    // tiles and chunks move alone.
-    static constexpr uint32_t GROUP_MASK = ~(uint32_t)((RHO >= 32 ? 32 : 16) - 1);
+    static constexpr int PC = CPR + 2;                        // staged chunks per row
+    static constexpr int ROWS = RHO + 2;
+    static constexpr int P = PC * CE;                         // row pitch (elements); interior at CE
+    static constexpr int TILE = ROWS * P;                     // elements per staged tile
+    static constexpr int STAGED = ROWS * PC;                  // 16-byte copies per tile
+    // Output chunks are stored by 32-byte sector when a tile row spans whole
+    // sectors: a sector holding any gasket cell is written whole (its
+    // off-gasket cells are 0 in both buffers), so the L2 never has to fill a
+    // half-written sector.  Narrower rows store chunk by chunk.
+    static constexpr uint32_t GROUP_MASK =
+        ~(uint32_t)((RHO * (int)sizeof(T) >= 32 ? 32 / (int)sizeof(T) : CE) - 1);
 };
 
-// Stage every tile of the group (interior chunks of touched sectors, and the
-// halo cell by cell at gasket cells only) into shared memory, then compute
-// and store the next state chunk by chunk.  Called by all threads; begins
-// and ends without a barrier of its own at the edges (the caller syncs
-// before reusing `tiles` or `sm`).
-template <int S>
-__device__ __forceinline__ void ca_group_step(uint8_t *sm, const CaTile *tiles)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
-    using G = CaGroup<S>;
-    constexpr int RHO = G::RHO, CPR = G::CPR, CHUNKS = G::CHUNKS, TPC = G::TPC;
-    constexpr int P = G::P, TILE = G::TILE, HALO = G::HALO;
-    for (int c = threadIdx.x; c < TPC * CHUNKS; c += kStencilThreads) {
-        const int t = c / CHUNKS, k = c % CHUNKS, ty = k / CPR, cx = k % CPR;
-        const CaTile tl = tiles[t];
-        uint4 v = make_uint4(0, 0, 0, 0);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Issue the staging copies of a group (every thread; completes at the next
+// cp_async_wait + barrier).  A chunk starting at column x (a multiple of CE)
+// on row y holds a gasket cell iff (x & y) == 0.
+template <typename T, int S>
+__device__ __forceinline__ void stage_group_async(T *sm, const StencilTile<T> *tiles)
+{
+    using G = StencilGroup<T, S>;
+    for (int c = threadIdx.x; c < G::TPC * G::STAGED; c += kStencilThreads) {
+        const int t = c / G::STAGED, k = c % G::STAGED, row = k / G::PC, cc = k % G::PC;
+        const StencilTile<T> tl = tiles[t];
+        T *dst = sm + t * G::TILE + row * G::P + cc * G::CE;
+        bool fill = false;
+        int64_t x = 0, y = 0;
         if (tl.bx != kNoTile) {
-            const uint32_t x = (tl.bx << S) + 16u * cx, y = (tl.by << S) + ty;
-            if (in_gasket(x & G::GROUP_MASK, y))   // chunk in a touched sector
-                v = *reinterpret_cast<const uint4 *>(tl.in + ((uint64_t)y << tl.r) + x);
+            const int64_t n = (int64_t)1 << tl.r;
+            x = (int64_t)(tl.bx << S) + (int64_t)(cc - 1) * G::CE;
+            y = (int64_t)(tl.by << S) + row - 1;
+            fill = x >= 0 && y >= 0 && x < n && y < n && (((uint64_t)x & (uint64_t)y) == 0);
         }
-        *reinterpret_cast<uint4 *>(sm + t * TILE + (ty + 1) * P + 16 + 16 * cx) = v;
+        if (fill) cp_async16(dst, tl.in + (((uint64_t)y << tl.r) + (uint64_t)x));
+        else *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
     }
-    for (int c = threadIdx.x; c < TPC * HALO; c += kStencilThreads) {
-        const int t = c / HALO, h = c % HALO;
-        int row, col;
-        halo_slot<RHO>(h, row, col);
-        const CaTile tl = tiles[t];
-        uint8_t v = 0;
-        if (tl.bx != kNoTile)
-            v = load_cell(tl.in, tl.r, (int64_t)(tl.bx << S) + col, (int64_t)(tl.by << S) + row);
-        sm[t * TILE + (row + 1) * P + 16 + col] = v;
-    }
-    __syncthreads();
-    for (int c = threadIdx.x; c < TPC * CHUNKS; c += kStencilThreads) {
-        const int t = c / CHUNKS, k = c % CHUNKS, ty = k / CPR, cx = k % CPR;
-        const CaTile tl = tiles[t];
+}
+
+// The CA's next state for every interior chunk of the group's tiles.
+template <int S>
+__device__ __forceinline__ void ca_compute_group(const uint8_t *sm,
+                                                 const StencilTile<uint8_t> *tiles)
+{
+    using G = StencilGroup<uint8_t, S>;
+    for (int c = threadIdx.x; c < G::TPC * G::CHUNKS; c += kStencilThreads) {
+        const int t = c / G::CHUNKS, k = c % G::CHUNKS, ty = k / G::CPR, cx = k % G::CPR;
+        const StencilTile<uint8_t> tl = tiles[t];
         if (tl.bx == kNoTile) continue;
         const uint32_t x = (tl.bx << S) + 16u * cx, y = (tl.by << S) + ty;
         if (!in_gasket(x & G::GROUP_MASK, y)) continue;   // sector holds no gasket cell
-        const uint8_t *base = sm + t * TILE + 16 + 16 * cx;
-        const uint8_t *up = base + ty * P, *mid = up + P, *dn = mid + P;
+        const uint8_t *up = sm + t * G::TILE + ty * G::P + 16 + 16 * cx;
+        const uint8_t *mid = up + G::P, *dn = mid + G::P;
         const uint4 cu = *reinterpret_cast<const uint4 *>(up);
         const uint4 cm = *reinterpret_cast<const uint4 *>(mid);
         const uint4 cd = *reinterpret_cast<const uint4 *>(dn);
@@ -190,6 +214,78 @@ __device__ __forceinline__ void ca_group_step(uint8_t *sm, const CaTile *tiles)
         o.w = life_rule(cnt.w, cm.w, m.w);
         *reinterpret_cast<uint4 *>(tl.out + ((uint64_t)y << tl.r) + x) = o;
     }
+}
+
+// Diffusion: u' = u + alpha * (sum of gasket 4-neighbours - deg * u).
+__device__ __forceinline__ float diffuse_cell(uint32_t x, uint32_t y, uint32_t n,
+                                              float u, float l, float rr, float up,
+                                              float dn, float alpha)
+{
+    if (!in_gasket(x, y)) return 0.0f;
+    const int deg = (x > 0u && in_gasket(x - 1u, y)) + (x + 1u < n && in_gasket(x + 1u, y)) +
+                    (y > 0u && in_gasket(x, y - 1u)) + (y + 1u < n && in_gasket(x, y + 1u));
+    const float sum = (l + rr) + (up + dn);
+    return u + alpha * (sum - (float)deg * u);
+}
+
+template <int S>
+__device__ __forceinline__ void diffuse_compute_group(const float *sm,
+                                                      const StencilTile<float> *tiles,
+                                                      float alpha)
+{
+    using G = StencilGroup<float, S>;
+    for (int c = threadIdx.x; c < G::TPC * G::CHUNKS; c += kStencilThreads) {
+        const int t = c / G::CHUNKS, k = c % G::CHUNKS, ty = k / G::CPR, cx = k % G::CPR;
+        const StencilTile<float> tl = tiles[t];
+        if (tl.bx == kNoTile) continue;
+        const uint32_t x = (tl.bx << S) + 4u * cx, y = (tl.by << S) + ty;
+        if (!in_gasket(x & G::GROUP_MASK, y)) continue;   // sector holds no gasket cell
+        const uint32_t n = 1u << tl.r;
+        const float *mid = sm + t * G::TILE + (ty + 1) * G::P + 4 + 4 * cx;
+        const float4 cu = *reinterpret_cast<const float4 *>(mid - G::P);
+        const float4 cm = *reinterpret_cast<const float4 *>(mid);
+        const float4 cd = *reinterpret_cast<const float4 *>(mid + G::P);
+        const float l = mid[-1], rr = mid[4];
+        float4 o;
+        o.x = diffuse_cell(x + 0u, y, n, cm.x, l, cm.y, cu.x, cd.x, alpha);
+        o.y = diffuse_cell(x + 1u, y, n, cm.y, cm.x, cm.z, cu.y, cd.y, alpha);
+        o.z = diffuse_cell(x + 2u, y, n, cm.z, cm.y, cm.w, cu.z, cd.z, alpha);
+        o.w = diffuse_cell(x + 3u, y, n, cm.w, cm.z, rr, cu.w, cd.w, alpha);
+        *reinterpret_cast<float4 *>(tl.out + ((uint64_t)y << tl.r) + x) = o;
+    }
+}
+
+// Double-buffered loop over the CTA's tile groups g = blockIdx.x, + gridDim.x,
+// ...: decode(g, slot) fills TPC tile descriptors (warp-collective inside),
+// compute(buf, slot) produces the group's output from the staged buffer.
+template <typename T, int S, class Decode, class Compute>
+__device__ __forceinline__ void stencil_pipeline(T *sm, StencilTile<T> *tiles, uint64_t groups,
+                                                 Decode decode, Compute compute)
+{
+    using G = StencilGroup<T, S>;
+    uint64_t g = blockIdx.x;
+    if (g >= groups) return;                      // uniform across the CTA
+    int cb = 0;
+    decode(g, tiles);
+    __syncthreads();
+    stage_group_async<T, S>(sm, tiles);
+    cp_async_commit();
+    for (; g < groups; g += gridDim.x) {
+        const uint64_t gn = g + gridDim.x;
+        const int nb = cb ^ 1;
+        // slot nb was last read by the compute of the previous iteration,
+        // which every thread finished before that iteration's last barrier
+        if (gn < groups) decode(gn, tiles + nb * G::TPC);
+        __syncthreads();
+        if (gn < groups) stage_group_async<T, S>(sm + nb * G::TPC * G::TILE, tiles + nb * G::TPC);
+        cp_async_commit();
+        cp_async_wait<1>();                       // this thread's copies of group g landed
+        __syncthreads();                          // ... and everyone else's
+        compute(sm + cb * G::TPC * G::TILE, tiles + cb * G::TPC);
+        __syncthreads();
+        cb = nb;
+    }
+    cp_async_wait<0>();
 }
 
 }  // namespace sg
