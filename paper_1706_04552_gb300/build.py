@@ -9,6 +9,7 @@ from __future__ import annotations
 import glob
 import hashlib
 import os
+import re
 import shutil
 import subprocess
 import sys
@@ -43,6 +44,42 @@ def _digest() -> str:
                                 glob.glob(os.path.join(CSRC, "*.h")) +
                                 glob.glob(os.path.join(INCLUDE, "*.h")))
     for f in files:
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+_INCLUDE_RE = re.compile(r'^\s*#\s*include\s+"([^"]+)"', re.M)
+
+
+def unit_files(unit: str) -> list[str]:
+    """One translation unit under csrc/ and every header it includes, directly
+    or through other headers, from csrc/ or include/."""
+    seen, todo = [], [os.path.join(CSRC, unit)]
+    while todo:
+        f = todo.pop()
+        if f in seen:
+            continue
+        seen.append(f)
+        with open(f) as fh:
+            names = _INCLUDE_RE.findall(fh.read())
+        for name in names:
+            for d in (os.path.dirname(f), CSRC, INCLUDE):
+                cand = os.path.join(d, name)
+                if os.path.exists(cand):
+                    todo.append(cand)
+                    break
+    return sorted(seen)
+
+
+def unit_digest(unit: str) -> str:
+    """Hash of the compile flags and the sources one translation unit is built
+    from: it changes exactly when that unit's kernels may have changed."""
+    h = hashlib.sha256()
+    # flags without the include directories, whose paths differ by machine
+    h.update(" ".join(f for f in NVCC_FLAGS if not os.path.isabs(f)).encode())
+    for f in unit_files(unit):
         h.update(os.path.basename(f).encode())
         with open(f, "rb") as fh:
             h.update(fh.read())

@@ -38,7 +38,8 @@ __host__ __device__ constexpr int pow3i(int k) { return k == 0 ? 1 : 3 * pow3i(k
 //
 // The per-lane divisor 3^k (k <= 7) is replaced by a fixed-point reciprocal
 // m = ceil(2^32 / 3^k): for w < 3^8, floor(w * m / 2^32) is exactly
-// floor(w / 3^k) because w * (m * 3^k - 2^32) < 2^32.
+// floor(w / 3^k) because w * (m * 3^k - 2^32) < 2^32.  For k = 0, m = 2^32
+// does not fit a word; that lane keeps m = 0 and adds w itself.
 // ---------------------------------------------------------------------------
 enum : int { kOrderRowMajor = 0, kOrderInterleaved = 1 };
 
@@ -50,8 +51,17 @@ __host__ __device__ inline uint32_t pi_word(int order, int rb)
     return order == kOrderInterleaved ? kPow3_8 : (uint32_t)pow3i(rb / 2);
 }
 
+// ceil(2^32 / 3^k) for k = 1..7 (k = 0 handled apart, see above)
+__host__ __device__ constexpr uint32_t recip3(int k)
+{
+    return k == 1 ? 1431655766u : k == 2 ? 477218589u : k == 3 ? 159072863u
+         : k == 4 ? 53024288u : k == 5 ? 17674763u : k == 6 ? 5891588u
+         : k == 7 ? 1963863u : 0u;
+}
+
 struct LambdaLane {
-    uint64_t recip;    // ceil(2^32 / 3^digit)
+    uint32_t recip;    // ceil(2^32 / 3^digit), 0 for digit 0
+    uint32_t keep_w;   // all ones for digit 0 (quotient = w), else 0
     uint32_t shift;    // mu - 1
     uint32_t reads_b;  // this lane's digit comes from word b
     uint32_t active;   // mu <= rb
@@ -61,9 +71,12 @@ struct LambdaLane {
     {
         const int l = lane & 15;
         const int digit = order == kOrderInterleaved ? (l & 7) : (l >> 1);
-        uint64_t p = 1;
-        for (int i = 0; i < digit; ++i) p *= 3;
-        recip = ((1ull << 32) + p - 1) / p;
+        // select from the table with compile-time indices (no local memory)
+        recip = 0u;
+#pragma unroll
+        for (int i = 1; i < 8; ++i)
+            if (digit == i) recip = recip3(i);
+        keep_w = digit == 0 ? 0xFFFFFFFFu : 0u;
         shift = (uint32_t)l;
         reads_b = order == kOrderInterleaved ? (l >= 8) : ((l & 1) == 0);
         active = (lane < 16) && (l < rb);
@@ -83,7 +96,7 @@ struct LambdaLane {
     __device__ __forceinline__ uint2 decode(uint32_t a, uint32_t b) const
     {
         const uint32_t w = reads_b ? b : a;
-        const uint32_t d = (uint32_t)(((uint64_t)w * recip) >> 32);
+        const uint32_t d = __umulhi(w, recip) + (w & keep_w);
         const uint32_t beta = d - 3u * ((d * 0xAAABu) >> 17);   // d mod 3, d < 2^16
         const uint32_t dx = beta >> 1, dy = beta - dx;
         const uint32_t tau = active ? ((dx << shift) | (dy << (shift + 16))) : 0u;

@@ -7,12 +7,42 @@ slots with thread-level lambda.  These tests restate that integer
 arithmetic in numpy exactly as the kernels do it and check it against the
 oracle for every block index up to level 14, and every rho, so that the
 index arithmetic is shown in range before the kernels run."""
+import os
+import re
+
 import numpy as np
 import pytest
 
 import oracle
 
 ORDERS = {0: "rowmajor", 1: "interleaved"}
+HEADER = os.path.join(os.path.dirname(__file__), os.pardir, "paper_1706_04552_gb300", "csrc",
+                      "sg_device.cuh")
+
+
+def _recip_table():
+    """The reciprocals recip3(k) as the device header writes them."""
+    with open(HEADER) as f:
+        body = re.search(r"constexpr uint32_t recip3\(int k\)\s*\{(.*?)\}", f.read(),
+                         re.S).group(1)
+    tab = [0] * 8
+    for k, v in re.findall(r"k == (\d) \? (\d+)u", body):
+        tab[int(k)] = int(v)
+    return tab
+
+
+def test_reciprocal_table_is_exact_for_every_word():
+    # entry k = ceil(2^32 / 3^k) (0 for k = 0, whose lane adds w instead), and
+    # the high word of w * entry (+ w for k = 0) is floor(w / 3^k) for every
+    # base-3 word w < 3^8
+    tab = _recip_table()
+    assert len(tab) == 8 and tab[0] == 0
+    w = np.arange(3 ** 8, dtype=np.uint64)
+    for k in range(8):
+        if k:
+            assert tab[k] == -(-(1 << 32) // 3 ** k) and tab[k] < (1 << 32)
+        d = ((w * np.uint64(tab[k])) >> np.uint64(32)) + (w if k == 0 else 0)
+        assert np.array_equal(d, w // np.uint64(3 ** k)), k
 
 
 def _pi_word(order, rb):
@@ -25,16 +55,18 @@ def _decode(q, rb, order):
     b = q // W
     a = q - b * W
     acc = np.zeros(len(q), dtype=np.uint64)
+    tab = _recip_table()
     for lane in range(32):
         l = lane & 15
         digit = (l & 7) if order == 1 else (l >> 1)
         p = 3 ** digit
-        recip = np.uint64(((1 << 32) + p - 1) // p)
+        recip = np.uint64(tab[digit])
+        keep_w = np.uint64(0xFFFFFFFF if digit == 0 else 0)
         reads_b = (l >= 8) if order == 1 else (l & 1) == 0
         active = lane < 16 and l < rb
         w = b if reads_b else a
         assert np.all(w < 6561)                          # the reciprocal's range
-        d = (w * recip) >> np.uint64(32)
+        d = ((w * recip) >> np.uint64(32)) + (w & keep_w)
         assert np.all(d < 65536)                         # the mod-3 trick's range
         beta = d - np.uint64(3) * ((d * np.uint64(0xAAAB)) >> np.uint64(17))
         assert np.all(beta == (w // np.uint64(p)) % np.uint64(3))
