@@ -64,9 +64,13 @@ def parse_args():
                         "into the gasket of a zero uint8 matrix for r = 0..16, rho = 1..32, "
                         "lambda (bounding sub-boxes, per-cell stores) vs bounding box, timed "
                         "as 100 sub-averages of 10 consecutive calls; prints one JSON line")
-    p.add_argument("--workload", choices=("write", "ca", "diffusion"), default="write",
-                   help="with --quick: time the level-15 CA or diffusion step instead "
-                        "of the write pass (the form used to profile those kernels)")
+    p.add_argument("--workload", choices=("write", "ca", "diffusion", "ca_fused",
+                                          "diffusion_fused"), default="write",
+                   help="with --quick: time the level-15 CA or diffusion step (or its "
+                        "fused form, k steps per launch) instead of the write pass (the "
+                        "form used to profile those kernels)")
+    p.add_argument("--level", type=int, default=None,
+                   help="with --quick and a stencil workload: the gasket level (default 15)")
     return p.parse_args()
 
 
@@ -358,32 +362,37 @@ def run_ours(args, grp: Group):
 
 
 def run_stencil_quick(args, sg, torch, dev, stream):
-    """K steps of the level-15 CA or diffusion step (lambda map), for ncu."""
+    """K launches of the level-15 (or --level) CA or diffusion step, or of
+    its fused form (k steps per launch), lambda map; for ncu."""
     from paper_1706_04552_gb300 import inputs, workloads
     s = workloads.STENCILS
-    r = max(s["levels"])
+    r = args.level if args.level else max(s["levels"])
     n = 1 << r
-    if args.workload == "ca":
+    kind, fused = args.workload.split("_")[0], args.workload.endswith("_fused")
+    if kind == "ca":
         idx, vals = inputs.ca_seed_sparse(r, s["ca_p"], s["ca_seed"])
-        dt, rho = torch.uint8, s["ca_rho"]
+        dt = torch.uint8
+        rho, k = (s["ca_fuse_rho"], s["ca_fuse"]) if fused else (s["ca_rho"], 1)
     else:
         idx, vals = inputs.uniform_sparse(r, s["diff_seed"])
-        dt, rho = torch.float32, s["diff_rho"]
+        dt = torch.float32
+        rho, k = (s["diff_fuse_rho"], s["diff_fuse"]) if fused else (s["diff_rho"], 1)
     a = torch.zeros(n * n, dtype=dt, device=dev)
     a[torch.from_numpy(idx).to(dev)] = torch.from_numpy(vals).to(dev)
     bufs = [a, torch.zeros_like(a)]
 
     def step():
-        if args.workload == "ca":
-            sg.ca_step(bufs[0], bufs[1], r, rho, "lambda", stream)
+        if kind == "ca":
+            sg.ca_steps(bufs[0], bufs[1], r, rho, k, "lambda", stream)
         else:
-            sg.diffuse_step(bufs[0], bufs[1], r, rho, s["alpha"], "lambda", stream)
+            sg.diffuse_steps(bufs[0], bufs[1], r, rho, k, s["alpha"], "lambda", stream)
         bufs.reverse()
     for _ in range(max(3, args.warmup)):
         step()
     total_ms, per = time_launches(step, args.steps, stream)
-    return {"workload": f"{args.workload} step, level {r}, rho {rho}, lambda",
-            "unit": UNIT, "value": round(3 ** r / (total_ms / args.steps / 1e3) / 1e9, 3),
+    return {"workload": f"{args.workload}, level {r}, rho {rho}, {k} step(s) per launch, "
+                        f"lambda",
+            "unit": UNIT, "value": round(3 ** r * k / (total_ms / args.steps / 1e3) / 1e9, 3),
             "launch_ms_mean": round(statistics.mean(per), 5), "steps": args.steps}
 
 

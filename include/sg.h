@@ -54,7 +54,7 @@
 extern "C" {
 #endif
 
-#define SG_ABI_VERSION 1
+#define SG_ABI_VERSION 2
 
 /* Exported from libsg.so (the library is built with hidden visibility). */
 #if defined(__GNUC__)
@@ -200,6 +200,30 @@ SG_API sg_status sg_ca_step_ex(int r, int rho, sg_map map, const uint8_t *in, ui
                                const sg_launch_opts *opts, void *stream);
 SG_API sg_status sg_diffuse_step_ex(int r, int rho, sg_map map, const float *in, float *out,
                                     float alpha, const sg_launch_opts *opts, void *stream);
+
+/*
+ * sg_ca_steps / sg_diffuse_steps -- k consecutive steps of sg_ca_step /
+ * sg_diffuse_step in one launch: out = step^k(in); `in` is not modified.
+ * Every tile is staged in shared memory with a halo at least k cells deep
+ * (rounded up to 4, 8 or 16 rows and to whole 16-byte chunks across), the k
+ * steps run there, and only the tile is written back, so HBM sees the tile
+ * bytes about once in and once out per launch rather than per step.  Each
+ * cell's arithmetic is that of the single step, so the result equals k
+ * calls of the single step.  (The paper fuses nothing; the per-tile lambda
+ * map is that of Theorem 1.)
+ *
+ *   k        1 .. SG_FUSE_MAX; k = 1 runs the single-step kernel
+ *   rho      16, 32 or 64 (other tile sides: SG_EUNSUPPORTED)
+ *   in, out, map, alpha, preconditions and postconditions: as for the
+ *            single step.
+ * Launches one kernel.
+ */
+#define SG_FUSE_MAX 16
+SG_API sg_status sg_ca_steps(int r, int rho, sg_map map, const uint8_t *in, uint8_t *out,
+                             int k, const sg_launch_opts *opts, void *stream);
+SG_API sg_status sg_diffuse_steps(int r, int rho, sg_map map, const float *in, float *out,
+                                  float alpha, int k, const sg_launch_opts *opts,
+                                  void *stream);
 
 /*
  * sg_block_map -- the lambda block decode on its own (Theorem 1: Eq. beta,

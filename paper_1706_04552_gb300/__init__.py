@@ -24,10 +24,12 @@ __all__ = [
     "SGError", "lib", "lib_path",
     "sg_map_write", "sg_ca_step", "sg_diffuse_step", "sg_block_map",
     "sg_map_write_ex", "sg_ca_step_ex", "sg_diffuse_step_ex", "LaunchOpts", "launch_opts",
+    "sg_ca_steps", "sg_diffuse_steps", "FUSE_MAX",
     "sg_launch_stats", "sg_status_str", "sg_abi_version", "sg_device_status",
     "device_status",
     "CABatch", "Graph", "BatchPlan",
-    "map_write", "map_write_host", "ca_step", "diffuse_step", "block_map", "launch_stats",
+    "map_write", "map_write_host", "ca_step", "diffuse_step", "ca_steps", "diffuse_steps",
+    "block_map", "launch_stats",
     "MAPS", "DTYPES", "VALUES", "ORDERS", "STORES",
 ]
 
@@ -112,6 +114,10 @@ def lib() -> ctypes.CDLL:
         L.sg_ca_step_ex.restype = i32
         L.sg_diffuse_step_ex.argtypes = [i32, i32, i32, vp, vp, ctypes.c_float, p_opts, vp]
         L.sg_diffuse_step_ex.restype = i32
+        L.sg_ca_steps.argtypes = [i32, i32, i32, vp, vp, i32, p_opts, vp]
+        L.sg_ca_steps.restype = i32
+        L.sg_diffuse_steps.argtypes = [i32, i32, i32, vp, vp, ctypes.c_float, i32, p_opts, vp]
+        L.sg_diffuse_steps.restype = i32
         L.sg_launch_stats.argtypes = [i32, i32, i32, p_u64, p_u64]
         L.sg_launch_stats.restype = i32
         L.sg_status_str.argtypes = [i32]
@@ -197,6 +203,15 @@ def sg_ca_step_ex(r, rho, map_kind, in_ptr, out_ptr, opts=None, stream=0) -> int
 def sg_diffuse_step_ex(r, rho, map_kind, in_ptr, out_ptr, alpha, opts=None, stream=0) -> int:
     return int(lib().sg_diffuse_step_ex(r, rho, map_kind, in_ptr, out_ptr, alpha,
                                         _opts_ref(opts), stream))
+
+
+def sg_ca_steps(r, rho, map_kind, in_ptr, out_ptr, k, opts=None, stream=0) -> int:
+    return int(lib().sg_ca_steps(r, rho, map_kind, in_ptr, out_ptr, k, _opts_ref(opts), stream))
+
+
+def sg_diffuse_steps(r, rho, map_kind, in_ptr, out_ptr, alpha, k, opts=None, stream=0) -> int:
+    return int(lib().sg_diffuse_steps(r, rho, map_kind, in_ptr, out_ptr, alpha, k,
+                                      _opts_ref(opts), stream))
 
 
 def sg_block_map(rb, order, bx_ptr, by_ptr, stream=0) -> int:
@@ -310,6 +325,36 @@ def diffuse_step(inp, out, r: int, rho: int, alpha: float = 0.2, map="lambda",
         _check("sg_diffuse_step", sg_diffuse_step_ex(r, rho, _map_id(map), inp.data_ptr(),
                                                      out.data_ptr(), float(alpha), opts,
                                                      _stream_handle(inp, stream)))
+    return out
+
+
+FUSE_MAX = 16     # SG_FUSE_MAX: most steps one sg_ca_steps / sg_diffuse_steps launch fuses
+
+
+def ca_steps(inp, out, r: int, rho: int, k: int, map="lambda", stream=None, order=None,
+             ctas_per_sm=None):
+    """k CA steps in one launch: out = step^k(inp); inp is left unchanged."""
+    import torch
+    _grid_check(inp, r, (torch.uint8,), "in")
+    _grid_check(out, r, (torch.uint8,), "out")
+    opts = launch_opts(order, None, ctas_per_sm)
+    with _on_device(inp):
+        _check("sg_ca_steps", sg_ca_steps(r, rho, _map_id(map), inp.data_ptr(), out.data_ptr(),
+                                          int(k), opts, _stream_handle(inp, stream)))
+    return out
+
+
+def diffuse_steps(inp, out, r: int, rho: int, k: int, alpha: float = 0.2, map="lambda",
+                  stream=None, order=None, ctas_per_sm=None):
+    """k diffusion steps in one launch: out = step^k(inp); inp is left unchanged."""
+    import torch
+    _grid_check(inp, r, (torch.float32,), "in")
+    _grid_check(out, r, (torch.float32,), "out")
+    opts = launch_opts(order, None, ctas_per_sm)
+    with _on_device(inp):
+        _check("sg_diffuse_steps", sg_diffuse_steps(r, rho, _map_id(map), inp.data_ptr(),
+                                                    out.data_ptr(), float(alpha), int(k), opts,
+                                                    _stream_handle(inp, stream)))
     return out
 
 

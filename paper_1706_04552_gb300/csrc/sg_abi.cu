@@ -246,6 +246,42 @@ sg_status sg_diffuse_step(int r, int rho, sg_map map, const float *in, float *ou
     return sg_diffuse_step_ex(r, rho, map, in, out, alpha, nullptr, stream);
 }
 
+sg_status sg_ca_steps(int r, int rho, sg_map map, const uint8_t *in, uint8_t *out, int k,
+                      const sg_launch_opts *opts, void *stream)
+{
+    if (k < 1 || k > SG_FUSE_MAX) return SG_EINVAL;
+    if (k == 1) return sg_ca_step_ex(r, rho, map, in, out, opts, stream);
+    int s = 0;
+    if (!valid_level_tile(r, rho, &s)) return SG_EINVAL;
+    if (map < SG_MAP_LAMBDA || map > SG_MAP_LAMBDA_UNROLL) return SG_EINVAL;
+    if (map != SG_MAP_LAMBDA && map != SG_MAP_BBOX) return SG_EUNSUPPORTED;
+    if (in == nullptr || out == nullptr || in == out) return SG_EINVAL;
+    if (!aligned(in, 16) || !aligned(out, 16)) return SG_EINVAL;
+    LaunchCfg cfg;
+    if (!read_launch_opts(opts, &cfg)) return SG_EINVAL;
+    if (rho < 16) return SG_EUNSUPPORTED;
+    return finish(launch_ca_fused(r, s, (int)map, in, out, k, (cudaStream_t)stream, cfg));
+}
+
+sg_status sg_diffuse_steps(int r, int rho, sg_map map, const float *in, float *out,
+                           float alpha, int k, const sg_launch_opts *opts, void *stream)
+{
+    if (k < 1 || k > SG_FUSE_MAX) return SG_EINVAL;
+    if (k == 1) return sg_diffuse_step_ex(r, rho, map, in, out, alpha, opts, stream);
+    int s = 0;
+    if (!valid_level_tile(r, rho, &s)) return SG_EINVAL;
+    if (map < SG_MAP_LAMBDA || map > SG_MAP_LAMBDA_UNROLL) return SG_EINVAL;
+    if (map != SG_MAP_LAMBDA && map != SG_MAP_BBOX) return SG_EUNSUPPORTED;
+    if (in == nullptr || out == nullptr || in == out) return SG_EINVAL;
+    if (!aligned(in, 16) || !aligned(out, 16)) return SG_EINVAL;
+    if (!(alpha == alpha) || alpha > 3.0e38f || alpha < -3.0e38f) return SG_EINVAL;
+    LaunchCfg cfg;
+    if (!read_launch_opts(opts, &cfg)) return SG_EINVAL;
+    if (rho < 16) return SG_EUNSUPPORTED;
+    return finish(launch_diffuse_fused(r, s, (int)map, in, out, alpha, k,
+                                       (cudaStream_t)stream, cfg));
+}
+
 sg_status sg_block_map(int rb, sg_order order, uint32_t *bx, uint32_t *by, void *stream)
 {
     if (rb < 0 || rb > 16) return SG_EINVAL;

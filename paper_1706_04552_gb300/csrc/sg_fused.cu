@@ -1,0 +1,514 @@
+// sg_fused.cu -- k stencil steps in one launch (temporal blocking).
+//
+// One step of either stencil reads every tile once and writes it once, with a
+// few operations per byte, so a sequence of steps is bound by HBM.  Here a
+// CTA stages one rho-tile together with a halo of KH >= k rows above and
+// below and HX >= k columns on either side (whole 16-byte chunks), runs the
+// k steps in shared memory, and writes back only the tile itself:
+//
+//   * after step s a cell is exact if every cell within distance s of it was
+//     staged.  Cells nearer the staged region's edge than that may be wrong
+//     (their missing neighbours read as 0), but they are never written back,
+//     and the tile lies KH >= k rows and HX >= k columns inside the edge;
+//   * at step s only rows [s, ROWS - s) are updated: the rows outside that
+//     window cannot be exact any more and nothing that is written reads them;
+//   * chunks outside the grid or holding no gasket cell are staged as zeros
+//     and produce zeros at every step, exactly as the single-step kernels
+//     treat them (off-gasket cells are 0 in every state).
+//
+// The CA runs bit-sliced (one warp per tile, 32 cells per word operation);
+// diffusion runs on float4 chunks with the single-step kernels' diffuse_cell
+// (one CTA per tile).  Either way each cell's result is the single step's, so
+// k fused steps equal k single steps.  HBM moves about the tile bytes once in
+// and once out per launch instead of per step.
+//
+// The tile coordinate comes from the lambda(omega) decode of Theorem 1 (one
+// warp, redux.sync) or from the bounding-box identity map, as elsewhere.
+#include "sg_stencil.cuh"
+
+namespace sg {
+
+template <typename T, int S, int KH> struct FusedShape {
+    static constexpr int RHO = 1 << S;
+    static constexpr int CE = 16 / (int)sizeof(T);            // elements per chunk
+    static constexpr int HX = ((KH + CE - 1) / CE) * CE;       // halo columns per side
+    static constexpr int HC = HX / CE;                         // halo chunks per side
+    static constexpr int CPR = RHO / CE;                       // tile chunks per row
+    static constexpr int PC = CPR + 2 * HC;                    // staged chunks per row
+    static constexpr int ROWS = RHO + 2 * KH;
+    static constexpr int P = PC * CE;                          // row pitch (elements)
+    static constexpr int BUF = ROWS * P * (int)sizeof(T);      // bytes per state buffer
+    static constexpr uint32_t GROUP_MASK = StencilGroup<T, S>::GROUP_MASK;
+};
+
+// Stage the tile at (x0, y0) with its halo into buf (every thread; complete
+// after cp_async_wait<0> + barrier).
+template <typename T, int S, int KH>
+__device__ __forceinline__ void fused_stage(T *buf, const T *__restrict__ in, int r,
+                                            int x0, int y0)
+{
+    using F = FusedShape<T, S, KH>;
+    const int n = 1 << r;
+    for (int i = threadIdx.x; i < F::ROWS * F::PC; i += kStencilThreads) {
+        const int row = i / F::PC, cc = i - row * F::PC;
+        const int x = x0 - F::HX + cc * F::CE, y = y0 - KH + row;
+        T *dst = buf + row * F::P + cc * F::CE;
+        const bool fill = x >= 0 && y >= 0 && x < n && y < n && (x & y) == 0;
+        if (fill) cp_async16(dst, in + (((uint64_t)y << r) + (uint64_t)x));
+        else *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    cp_async_commit();
+}
+
+// Copy the tile (rows [KH, KH + RHO), chunks [HC, HC + CPR)) to HBM, whole
+// 32-byte sectors where a tile row spans them (see StencilGroup).
+template <typename T, int S, int KH>
+__device__ __forceinline__ void fused_store(const T *buf, T *__restrict__ out, int r,
+                                            int x0, int y0)
+{
+    using F = FusedShape<T, S, KH>;
+    for (int i = threadIdx.x; i < F::RHO * F::CPR; i += kStencilThreads) {
+        const int ty = i / F::CPR, cx = i - ty * F::CPR;
+        const uint32_t x = (uint32_t)x0 + (uint32_t)(cx * F::CE), y = (uint32_t)(y0 + ty);
+        if (!in_gasket(x & F::GROUP_MASK, y)) continue;
+        const T *src = buf + (KH + ty) * F::P + (F::HC + cx) * F::CE;
+        *reinterpret_cast<uint4 *>(out + ((uint64_t)y << r) + x) =
+            *reinterpret_cast<const uint4 *>(src);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// CA, bit-sliced.  In shared memory a staged row is a string of bits, one
+// cell per bit (bit j of a row = column x0 - 16 + j: a 16-cell halo on each
+// side, then padding to whole 32-bit words), and the B3/S23 rule runs on 32
+// cells at a time: the eight neighbour planes (the rows above and below and
+// the row itself, shifted by one column either way with funnel shifts) are
+// summed by a tree of bitwise full adders, and the bits of the count decide
+// the next state.  One warp owns one tile at a time, so the steps need only
+// __syncwarp.  States are 0/1 bytes in HBM: 16-byte chunks are packed to 16
+// bits when staged and unpacked when stored.
+// ---------------------------------------------------------------------------
+template <int S, int KH> struct BitShape {
+    static constexpr int RHO = 1 << S;
+    static constexpr int HW = RHO / 16 + 2;          // staged 16-cell half-words per row
+    static constexpr int WPR = (HW + 1) / 2;         // 32-bit words per row
+    static constexpr int ROWS = RHO + 2 * KH;
+    static constexpr int WORDS = ROWS * WPR;
+    static constexpr int WARPS = kStencilThreads / 32;
+    static constexpr uint32_t GROUP_MASK = StencilGroup<uint8_t, S>::GROUP_MASK;
+};
+
+// Bit i of the result = byte i of a chunk of 0/1 bytes.
+__device__ __forceinline__ uint32_t pack16(uint4 c)
+{
+    // byte j of a word sits at bit 8j; two shifted ORs bring it to bit j
+    auto nib = [](uint32_t w) {
+        w |= w >> 7;
+        w |= w >> 14;
+        return w & 0xFu;
+    };
+    return nib(c.x) | (nib(c.y) << 4) | (nib(c.z) << 8) | (nib(c.w) << 12);
+}
+
+// Byte i of the result = bit i of b (0/1 bytes).
+__device__ __forceinline__ uint4 unpack16(uint32_t b)
+{
+    // nib * (1 + 2^7 + 2^14 + 2^21) puts bit j of the nibble at bit 8j; the
+    // four shifted copies do not overlap, so no carry disturbs them
+    auto bytes = [](uint32_t nib) { return (nib * 0x00204081u) & 0x01010101u; };
+    return make_uint4(bytes(b & 0xFu), bytes((b >> 4) & 0xFu), bytes((b >> 8) & 0xFu),
+                      bytes((b >> 12) & 0xFu));
+}
+
+// Bits i of 16 with (i & yl) == 0 (yl = y mod 16): the gasket cells of a
+// 16-cell chunk at a column x with (x & y) == 0, x a multiple of 16.
+__device__ __forceinline__ uint32_t member_bits16(uint32_t yl)
+{
+    uint32_t m = 0xFFFFu;
+    if (yl & 1u) m &= 0x5555u;
+    if (yl & 2u) m &= 0x3333u;
+    if (yl & 4u) m &= 0x0F0Fu;
+    if (yl & 8u) m &= 0x00FFu;
+    return m;
+}
+
+__device__ __forceinline__ void full_add(uint32_t a, uint32_t b, uint32_t c, uint32_t &sum,
+                                         uint32_t &carry)
+{
+    sum = a ^ b ^ c;
+    carry = (a & b) | (c & (a ^ b));
+}
+
+// Stage the tile at (x0, y0) with its halo as bits, and the gasket mask of
+// every staged bit (0 off the grid, off the gasket and in padding).
+template <int S, int KH>
+__device__ __forceinline__ void bits_stage(uint32_t *bits, uint32_t *mask,
+                                           const uint8_t *__restrict__ in, int r, int x0, int y0,
+                                           int lane)
+{
+    using B = BitShape<S, KH>;
+    constexpr int HPR = 2 * B::WPR;                  // half-words per row, padding included
+    const int n = 1 << r;
+    uint16_t *bh = reinterpret_cast<uint16_t *>(bits);
+    uint16_t *mh = reinterpret_cast<uint16_t *>(mask);
+#pragma unroll 4
+    for (int i = lane; i < B::ROWS * HPR; i += 32) {
+        const int row = i / HPR, h = i - row * HPR;
+        const int x = x0 - 16 + 16 * h, y = y0 - KH + row;
+        uint32_t v = 0u, m = 0u;
+        if (h < B::HW && x >= 0 && y >= 0 && x < n && y < n && (x & y) == 0) {
+            v = pack16(__ldg(reinterpret_cast<const uint4 *>(in + (((uint64_t)y << r) +
+                                                                    (uint64_t)x))));
+            m = member_bits16((uint32_t)y & 15u);
+        }
+        bh[i] = (uint16_t)v;
+        mh[i] = (uint16_t)m;
+    }
+}
+
+// Row v of a staged bit-string with its left and right neighbours' planes
+// (bit j <- bit j-1 and bit j <- bit j+1; words past the row's ends are not
+// staged and read as 0 -- the address read is the word itself).
+struct BitRow {
+    uint32_t v, l, r;
+};
+template <int WPR>
+__device__ __forceinline__ BitRow bit_row(const uint32_t *row, int w)
+{
+    const bool hl = w > 0, hr = w < WPR - 1;
+    const uint32_t vl = row[hl ? w - 1 : w] & (hl ? 0xFFFFFFFFu : 0u);
+    const uint32_t vr = row[hr ? w + 1 : w] & (hr ? 0xFFFFFFFFu : 0u);
+    const uint32_t v = row[w];
+    return BitRow{v, __funnelshift_l(vl, v, 1), __funnelshift_r(v, vr, 1)};
+}
+
+// One step over the window rows [s, ROWS - s): src -> dst.  The lanes form
+// G = 32 / WPR groups; lane (g, w) updates word w of a run of consecutive
+// rows, carrying down the run each row's horizontal sums: the 3-cell sum
+// (l + v + r) serves the rows above and below it, the 2-cell sum (l + r) the
+// row itself, so a row costs one full adder, one half adder and the merge:
+//   count = up3 + mid2 + dn3 = s0 + 2 s1 + 4 (t1 + t2).
+template <int S, int KH>
+__device__ __forceinline__ void bits_ca_step(const uint32_t *src, uint32_t *dst,
+                                             const uint32_t *mask, int s, int lane)
+{
+    using B = BitShape<S, KH>;
+    constexpr int G = 32 / B::WPR;
+    const int g = lane / B::WPR, w = lane - g * B::WPR;
+    if (g >= G) return;                               // idle lanes (32 not a multiple of WPR)
+    const int rows = B::ROWS - 2 * s, run = (rows + G - 1) / G;
+    const int first = s + g * run;
+    const int last = min(first + run, B::ROWS - s);
+    if (first >= last) return;
+    BitRow u = bit_row<B::WPR>(src + (first - 1) * B::WPR, w);
+    uint32_t us, uc;                                  // 3-sum of the row above
+    full_add(u.l, u.v, u.r, us, uc);
+    BitRow m = bit_row<B::WPR>(src + first * B::WPR, w);
+    uint32_t ms3, mc3;                                // 3-sum of the current row
+    full_add(m.l, m.v, m.r, ms3, mc3);
+    for (int row = first; row < last; ++row) {
+        const BitRow d = bit_row<B::WPR>(src + (row + 1) * B::WPR, w);
+        uint32_t ds3, dc3;
+        full_add(d.l, d.v, d.r, ds3, dc3);
+        const uint32_t ms2 = m.l ^ m.r, mc2 = m.l & m.r;   // 2-sum of the current row
+        uint32_t s0, c1, t0, t1;
+        full_add(us, ms2, ds3, s0, c1);
+        full_add(uc, mc2, dc3, t0, t1);
+        const uint32_t s1 = t0 ^ c1, t2 = t0 & c1;
+        // alive next iff count is 3, or count is 2 and alive: s1 set, no
+        // weight-4 bit, and s0 or the cell itself
+        dst[row * B::WPR + w] = (s0 | m.v) & s1 & ~(t1 | t2) & mask[row * B::WPR + w];
+        us = ms3;
+        uc = mc3;
+        m = d;
+        ms3 = ds3;
+        mc3 = dc3;
+    }
+}
+
+// Unpack the tile rows (rows [KH, KH + RHO), half-words 1 .. RHO/16) to HBM,
+// whole 32-byte sectors where a tile row spans them.
+template <int S, int KH>
+__device__ __forceinline__ void bits_store(const uint32_t *bits, uint8_t *__restrict__ out,
+                                           int r, int x0, int y0, int lane)
+{
+    using B = BitShape<S, KH>;
+    constexpr int CPR = B::RHO / 16, HPR = 2 * B::WPR;
+    const uint16_t *bh = reinterpret_cast<const uint16_t *>(bits);
+    for (int i = lane; i < B::RHO * CPR; i += 32) {
+        const int ty = i / CPR, cx = i - ty * CPR;
+        const uint32_t x = (uint32_t)(x0 + 16 * cx), y = (uint32_t)(y0 + ty);
+        if (!in_gasket(x & B::GROUP_MASK, y)) continue;
+        const uint32_t v = bh[(KH + ty) * HPR + 1 + cx];
+        *reinterpret_cast<uint4 *>(out + ((uint64_t)y << r) + x) = unpack16(v);
+    }
+}
+
+template <int S, int KH, int MAP>
+__global__ void __launch_bounds__(kStencilThreads, 6)
+ca_bits_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int r, int order,
+               uint64_t ntiles, int k)
+{
+    using B = BitShape<S, KH>;
+    __shared__ uint32_t sm[B::WARPS][3][B::WORDS];     // two states and the mask, per warp
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *st0 = sm[warp][0], *st1 = sm[warp][1], *mk = sm[warp][2];
+
+    const int rb = r - S;
+    LambdaLane ll;
+    ll.init(lane, rb, order);
+    const uint32_t W = pi_word(order, rb);
+    const uint64_t stride = (uint64_t)gridDim.x * B::WARPS;
+
+    for (uint64_t q = (uint64_t)blockIdx.x * B::WARPS + warp; q < ntiles; q += stride) {
+        const uint2 c = decode_tile<MAP>(q, ntiles, rb, W, ll);     // warp-collective
+        if (c.x == kNoTile) continue;                                // uniform in the warp
+        const int x0 = (int)(c.x << S), y0 = (int)(c.y << S);
+        bits_stage<S, KH>(st0, mk, in, r, x0, y0, lane);
+        __syncwarp();
+        for (int s = 1; s <= k; ++s) {
+            bits_ca_step<S, KH>((s & 1) ? st0 : st1, (s & 1) ? st1 : st0, mk, s, lane);
+            __syncwarp();
+        }
+        bits_store<S, KH>((k & 1) ? st1 : st0, out, r, x0, y0, lane);
+        __syncwarp();                    // the buffers are read before the next staging
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Diffusion.  One CTA per tile; thread t owns the staged float4 chunks
+// c = t + 256 j for the whole tile.  Whether each of a chunk's four cells is
+// a gasket cell, and its gasket degree, depend only on the position, so they
+// are worked out once per tile into one word per chunk (byte i = degree of
+// cell i, or kNotCell), and chunks holding no gasket cell are skipped at
+// every step (they are 0 in both state buffers).
+// ---------------------------------------------------------------------------
+constexpr uint32_t kNotCell = 0xFFu;
+constexpr uint32_t kDeadChunk = 0xFFFFFFFFu;
+
+// 0x01 in byte i for each set bit i of a 4-bit mask.
+__device__ __forceinline__ uint32_t spread4(uint32_t m) { return (m * 0x00204081u) & 0x01010101u; }
+
+// Bits i of 4 with (i & y) == 0: the gasket cells of a 4-cell chunk at a
+// column x with (x & y) == 0, x a multiple of 4 (table by y mod 4).
+__device__ __forceinline__ uint32_t member_bits4(uint32_t y) { return (0x135Fu >> (4u * (y & 3u))) & 0xFu; }
+
+// Degree word of the chunk at (x, y), x a multiple of 4 (kDeadChunk when it
+// holds no gasket cell).  In a chunk with (x & y) == 0, cell i's left and
+// right neighbours inside the chunk are members iff bits i-1, i+1 of the
+// row's member mask are set; across the chunk's edges, and above and below,
+// the neighbour chunk is tested whole.
+__device__ __forceinline__ uint32_t chunk_degrees(int x, int y, int n)
+{
+    if (x < 0 || y < 0 || x >= n || y >= n || (x & y) != 0) return kDeadChunk;
+    const uint32_t m = member_bits4((uint32_t)y);
+    const uint32_t pl = x > 0 && ((x - 1) & y) == 0;
+    const uint32_t pr = x + 4 < n && ((x + 4) & y) == 0;
+    const uint32_t mu = (y > 0 && (x & (y - 1)) == 0) ? member_bits4((uint32_t)(y - 1)) : 0u;
+    const uint32_t md = (y + 1 < n && (x & (y + 1)) == 0) ? member_bits4((uint32_t)(y + 1)) : 0u;
+    const uint32_t ml = ((m << 1) | pl) & 0xFu, mr = (m >> 1) | (pr << 3);
+    const uint32_t deg = spread4(ml) + spread4(mr) + spread4(mu) + spread4(md);
+    return deg | (spread4(~m & 0xFu) * kNotCell);
+}
+
+__device__ __forceinline__ float degree_cell(uint32_t word, int i, float u, float l, float rr,
+                                             float up, float dn, float alpha)
+{
+    const uint32_t d = (word >> (8 * i)) & 0xFFu;
+    // (float)d for d <= 4: the low mantissa bits of 2^23 + d, minus 2^23
+    const float degf = __uint_as_float(0x4B000000u | d) - 8388608.0f;
+    return d == kNotCell ? 0.0f : diffuse_update(u, l, rr, up, dn, degf, alpha);
+}
+
+// (4 resident CTAs: the shared-memory limit of the 64-tiles with an 8-row
+// halo; the bound keeps the unrolled chunk loop from taking more registers)
+template <int S, int KH, int MAP>
+__global__ void __launch_bounds__(kStencilThreads, 4)
+diffuse_fused_kernel(const float *__restrict__ in, float *__restrict__ out, int r, int order,
+                     uint64_t ntiles, int k, float alpha)
+{
+    using F = FusedShape<float, S, KH>;
+    constexpr int CH = F::ROWS * F::PC;
+    constexpr int PER = (CH + kStencilThreads - 1) / kStencilThreads;
+    extern __shared__ __align__(16) unsigned char fused_smem[];
+    float *b0 = reinterpret_cast<float *>(fused_smem);
+    float *b1 = reinterpret_cast<float *>(fused_smem + F::BUF);
+    __shared__ uint2 coord;
+
+    const int n = 1 << r, rb = r - S;
+    LambdaLane ll;
+    ll.init(threadIdx.x & 31, rb, order);
+    const uint32_t W = pi_word(order, rb);
+
+    for (uint64_t q = blockIdx.x; q < ntiles; q += gridDim.x) {
+        if (threadIdx.x < 32) {
+            const uint2 c = decode_tile<MAP>(q, ntiles, rb, W, ll);
+            if (threadIdx.x == 0) coord = c;
+        }
+        __syncthreads();                 // coord visible; last tile's buffers free
+        const uint2 c = coord;
+        if (c.x == kNoTile) {            // uniform: an empty bounding-box tile
+            __syncthreads();
+            continue;
+        }
+        const int x0 = (int)(c.x << S), y0 = (int)(c.y << S);
+        uint32_t deg[PER];
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            const int ch = threadIdx.x + j * kStencilThreads;
+            deg[j] = kDeadChunk;
+            if (ch < CH) {
+                const int row = ch / F::PC, cc = ch - row * F::PC;
+                const int x = x0 - F::HX + 4 * cc, y = y0 - KH + row;
+                deg[j] = chunk_degrees(x, y, n);
+                float *d0 = b0 + row * F::P + 4 * cc;
+                if (deg[j] != kDeadChunk) {
+                    cp_async16(d0, in + (((uint64_t)y << r) + (uint64_t)x));
+                } else {
+                    *reinterpret_cast<float4 *>(d0) = make_float4(0.f, 0.f, 0.f, 0.f);
+                    *reinterpret_cast<float4 *>(b1 + (d0 - b0)) = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+        }
+        cp_async_commit();
+        cp_async_wait<0>();
+        __syncthreads();
+        for (int s = 1; s <= k; ++s) {
+            const float *src = (s & 1) ? b0 : b1;
+            float *dst = (s & 1) ? b1 : b0;
+#pragma unroll
+            for (int j = 0; j < PER; ++j) {
+                const int ch = threadIdx.x + j * kStencilThreads;
+                if (deg[j] == kDeadChunk) continue;       // also every ch >= CH
+                const int row = ch / F::PC, cc = ch - row * F::PC;
+                if (row < s || row >= F::ROWS - s) continue;
+                const float *mid = src + row * F::P + 4 * cc;
+                const float4 cu = *reinterpret_cast<const float4 *>(mid - F::P);
+                const float4 cm = *reinterpret_cast<const float4 *>(mid);
+                const float4 cd = *reinterpret_cast<const float4 *>(mid + F::P);
+                // neighbours left and right of the chunk (not staged at the
+                // region's edge: read inside the chunk, then use 0)
+                const bool hl = cc > 0, hr = cc < F::PC - 1;
+                const float lv = mid[hl ? -1 : 0], rv = mid[hr ? 4 : 3];
+                const float l = hl ? lv : 0.f, rr = hr ? rv : 0.f;
+                const uint32_t w = deg[j];
+                float4 o;
+                o.x = degree_cell(w, 0, cm.x, l, cm.y, cu.x, cd.x, alpha);
+                o.y = degree_cell(w, 1, cm.y, cm.x, cm.z, cu.y, cd.y, alpha);
+                o.z = degree_cell(w, 2, cm.z, cm.y, cm.w, cu.z, cd.z, alpha);
+                o.w = degree_cell(w, 3, cm.w, cm.z, rr, cu.w, cd.w, alpha);
+                *reinterpret_cast<float4 *>(dst + row * F::P + 4 * cc) = o;
+            }
+            __syncthreads();
+        }
+        fused_store<float, S, KH>((k & 1) ? b1 : b0, out, r, x0, y0);
+        // the next iteration's first barrier orders these reads before the
+        // next staging overwrites b0 / b1
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Launchers
+// ---------------------------------------------------------------------------
+// Grid of a fused kernel; the dynamic shared-memory limit is raised once per
+// device (bit d of `attr_devs`) for buffers above the default 48 KB.
+template <typename K>
+static cudaError_t fused_grid(K kern, int smem, uint64_t ntiles, const LaunchCfg &cfg,
+                              unsigned *grid, std::atomic<int> *occ,
+                              std::atomic<uint64_t> *attr_devs)
+{
+    if (smem > 48 * 1024) {
+        int dev = 0;
+        cudaError_t e = cudaGetDevice(&dev);
+        if (e != cudaSuccess) return e;
+        const uint64_t bit = 1ull << (dev & 63);
+        if ((attr_devs->load(std::memory_order_acquire) & bit) == 0) {
+            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            if (e != cudaSuccess) return e;
+            attr_devs->fetch_or(bit, std::memory_order_acq_rel);
+        }
+    }
+    return persistent_grid(kern, kStencilThreads, (size_t)smem, ntiles, cfg, grid, occ);
+}
+
+template <int S, int KH, int MAP>
+cudaError_t launch_ca_fused_t(int r, const uint8_t *in, uint8_t *out, int k, cudaStream_t st,
+                              const LaunchCfg &cfg)
+{
+    using B = BitShape<S, KH>;
+    const int rb = r - S;
+    const uint64_t ntiles = (MAP == kMapBBox) ? (1ull << (2 * rb)) : (uint64_t)pow3i(rb);
+    static std::atomic<int> occ{0};
+    auto kern = ca_bits_kernel<S, KH, MAP>;
+    unsigned grid = 1;
+    cudaError_t e = persistent_grid(kern, kStencilThreads, 0, (ntiles + B::WARPS - 1) / B::WARPS,
+                                    cfg, &grid, &occ);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kStencilThreads, 0, st>>>(in, out, r, cfg.order, ntiles, k);
+    return cudaGetLastError();
+}
+
+template <int S, int KH, int MAP>
+cudaError_t launch_diffuse_fused_t(int r, const float *in, float *out, float alpha, int k,
+                                   cudaStream_t st, const LaunchCfg &cfg)
+{
+    using F = FusedShape<float, S, KH>;
+    const int rb = r - S;
+    const uint64_t ntiles = (MAP == kMapBBox) ? (1ull << (2 * rb)) : (uint64_t)pow3i(rb);
+    static std::atomic<int> occ{0};
+    static std::atomic<uint64_t> attr{0};
+    auto kern = diffuse_fused_kernel<S, KH, MAP>;
+    unsigned grid = 1;
+    cudaError_t e = fused_grid(kern, 2 * F::BUF, ntiles, cfg, &grid, &occ, &attr);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kStencilThreads, 2 * F::BUF, st>>>(in, out, r, cfg.order, ntiles, k, alpha);
+    return cudaGetLastError();
+}
+
+// Halo depth instance for k fused steps: the smallest of 4, 8, 16 >= k.
+#define SG_FUSED_SWITCH(s, k, CALL)                                          \
+    do {                                                                     \
+        const int kh_ = (k) <= 4 ? 4 : (k) <= 8 ? 8 : 16;                    \
+        switch ((s) * 100 + kh_) {                                           \
+        case 404: return CALL(4, 4);                                         \
+        case 408: return CALL(4, 8);                                         \
+        case 416: return CALL(4, 16);                                        \
+        case 504: return CALL(5, 4);                                         \
+        case 508: return CALL(5, 8);                                         \
+        case 516: return CALL(5, 16);                                        \
+        case 604: return CALL(6, 4);                                         \
+        case 608: return CALL(6, 8);                                         \
+        case 616: return CALL(6, 16);                                        \
+        default: return cudaErrorInvalidValue;                               \
+        }                                                                    \
+    } while (0)
+
+cudaError_t launch_ca_fused(int r, int s, int map, const uint8_t *in, uint8_t *out, int k,
+                            cudaStream_t st, const LaunchCfg &cfg)
+{
+    if (k < 1 || k > 16) return cudaErrorInvalidValue;
+    if (map == kMapBBox) {
+#define CALL(S, KH) launch_ca_fused_t<S, KH, kMapBBox>(r, in, out, k, st, cfg)
+        SG_FUSED_SWITCH(s, k, CALL);
+#undef CALL
+    }
+#define CALL(S, KH) launch_ca_fused_t<S, KH, kMapLambda>(r, in, out, k, st, cfg)
+    SG_FUSED_SWITCH(s, k, CALL);
+#undef CALL
+}
+
+cudaError_t launch_diffuse_fused(int r, int s, int map, const float *in, float *out,
+                                 float alpha, int k, cudaStream_t st, const LaunchCfg &cfg)
+{
+    if (k < 1 || k > 16) return cudaErrorInvalidValue;
+    if (map == kMapBBox) {
+#define CALL(S, KH) launch_diffuse_fused_t<S, KH, kMapBBox>(r, in, out, alpha, k, st, cfg)
+        SG_FUSED_SWITCH(s, k, CALL);
+#undef CALL
+    }
+#define CALL(S, KH) launch_diffuse_fused_t<S, KH, kMapLambda>(r, in, out, alpha, k, st, cfg)
+    SG_FUSED_SWITCH(s, k, CALL);
+#undef CALL
+}
+
+}  // namespace sg

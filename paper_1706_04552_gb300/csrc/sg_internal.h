@@ -46,6 +46,10 @@ cudaError_t launch_ca(int r, int s, int map, const uint8_t *in, uint8_t *out,
                       cudaStream_t st, const LaunchCfg &cfg);
 cudaError_t launch_diffuse(int r, int s, int map, const float *in, float *out,
                            float alpha, cudaStream_t st, const LaunchCfg &cfg);
+cudaError_t launch_ca_fused(int r, int s, int map, const uint8_t *in, uint8_t *out, int k,
+                            cudaStream_t st, const LaunchCfg &cfg);
+cudaError_t launch_diffuse_fused(int r, int s, int map, const float *in, float *out,
+                                 float alpha, int k, cudaStream_t st, const LaunchCfg &cfg);
 cudaError_t launch_block_map(int rb, int order, uint32_t *bx, uint32_t *by,
                              cudaStream_t st);
 

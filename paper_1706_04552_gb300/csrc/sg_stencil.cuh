@@ -216,7 +216,17 @@ __device__ __forceinline__ void ca_compute_group(const uint8_t *sm,
     }
 }
 
-// Diffusion: u' = u + alpha * (sum of gasket 4-neighbours - deg * u).
+// Diffusion: u' = u + alpha * (sum of gasket 4-neighbours - deg * u).  Off-
+// gasket cells are 0, so the sum runs over the plain 4-neighbourhood.  Every
+// diffusion kernel evaluates a cell through diffuse_update, so they agree bit
+// for bit.
+__device__ __forceinline__ float diffuse_update(float u, float l, float rr, float up, float dn,
+                                                float degf, float alpha)
+{
+    const float sum = (l + rr) + (up + dn);
+    return u + alpha * (sum - degf * u);
+}
+
 __device__ __forceinline__ float diffuse_cell(uint32_t x, uint32_t y, uint32_t n,
                                               float u, float l, float rr, float up,
                                               float dn, float alpha)
@@ -224,8 +234,7 @@ __device__ __forceinline__ float diffuse_cell(uint32_t x, uint32_t y, uint32_t n
     if (!in_gasket(x, y)) return 0.0f;
     const int deg = (x > 0u && in_gasket(x - 1u, y)) + (x + 1u < n && in_gasket(x + 1u, y)) +
                     (y > 0u && in_gasket(x, y - 1u)) + (y + 1u < n && in_gasket(x, y + 1u));
-    const float sum = (l + rr) + (up + dn);
-    return u + alpha * (sum - (float)deg * u);
+    return diffuse_update(u, l, rr, up, dn, (float)deg, alpha);
 }
 
 template <int S>

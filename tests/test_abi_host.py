@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol(L):
 
 
 def test_abi_version_and_status_strings(L):
-    assert sg.sg_abi_version() == 1
+    assert sg.sg_abi_version() == 2
     assert sg.sg_status_str(0) == "SG_OK"
     for code in range(1, 6):
         assert sg.sg_status_str(code).startswith("SG_E")
@@ -110,6 +110,29 @@ def test_bad_launch_options_are_rejected_before_launch(L):
     fill = sg.launch_opts(store="fill")
     assert sg.sg_map_write_ex(8, 8, 0, 0, FAKE, 2, 1, fill) == sg.SG_EUNSUPPORTED
     assert sg.sg_map_write_ex(8, 16, 0, 0, FAKE + 4, 2, 1, fill) == sg.SG_EINVAL
+
+
+def test_fused_steps_validate_before_launch(L):
+    # every case below is refused on the host, so no kernel is launched
+    ca, df = sg.sg_ca_steps, sg.sg_diffuse_steps
+    for k in (0, -1, sg.FUSE_MAX + 1):
+        assert ca(8, 16, 0, FAKE, FAKE + 8192, k) == sg.SG_EINVAL
+        assert df(8, 16, 0, FAKE, FAKE + 8192, 0.2, k) == sg.SG_EINVAL
+    for rho in (1, 2, 4, 8):                                  # tiles too narrow to fuse
+        assert ca(8, rho, 0, FAKE, FAKE + 8192, 4) == sg.SG_EUNSUPPORTED
+        assert df(8, rho, 0, FAKE, FAKE + 8192, 0.2, 4) == sg.SG_EUNSUPPORTED
+    assert ca(8, 16, 2, FAKE, FAKE + 8192, 4) == sg.SG_EUNSUPPORTED      # intra-block map
+    assert ca(8, 16, 9, FAKE, FAKE + 8192, 4) == sg.SG_EINVAL            # bad map
+    assert ca(8, 16, 0, FAKE, FAKE, 4) == sg.SG_EINVAL                   # in == out
+    assert ca(8, 16, 0, 0, FAKE, 4) == sg.SG_EINVAL                      # null in
+    assert ca(8, 16, 0, FAKE + 8, FAKE + 8192, 4) == sg.SG_EINVAL        # misaligned
+    assert ca(17, 16, 0, FAKE, FAKE + 8192, 4) == sg.SG_EINVAL           # bad level
+    assert ca(3, 16, 0, FAKE, FAKE + 8192, 4) == sg.SG_EINVAL            # rho > n
+    assert df(8, 16, 0, FAKE, FAKE + 8192, float("inf"), 4) == sg.SG_EINVAL
+    assert df(8, 16, 0, FAKE, FAKE + 4, 0.2, 4) == sg.SG_EINVAL          # misaligned out
+    bad = sg.launch_opts(ctas_per_sm=-3)
+    assert ca(8, 16, 0, FAKE, FAKE + 8192, 4, bad) == sg.SG_EINVAL
+    assert df(8, 16, 0, FAKE, FAKE + 8192, 0.2, 4, bad) == sg.SG_EINVAL
 
 
 def test_stencils_reject_intra_block_maps(L):

@@ -147,3 +147,163 @@ def test_lookup_table_rank_and_unrolled_slots(S):
     cells = {_unrolled(S, e) for e in range(3 ** S)}
     assert len(cells) == 3 ** S
     assert all(x & y == 0 and 0 <= x < R and 0 <= y < R for x, y in cells)
+
+
+# ------------------------------------------------------------------------
+# The bit-sliced fused CA (sg_ca_steps), restated word for word in numpy:
+# staging packs 16-byte chunks of 0/1 bytes to 16 bits, each step sums the
+# eight neighbour planes with full adders, and the store unpacks bits back
+# to bytes.  Run over every tile of a small gasket, it must reproduce k
+# steps of the oracle.  (The kernel walks each word down a run of rows and
+# carries the row sums along; the arithmetic per row is the one below.)
+# ------------------------------------------------------------------------
+_M32 = 0xFFFFFFFF
+
+
+def _pack16(chunk):
+    v = 0
+    for j, w in enumerate(chunk.view("<u4")):
+        w = int(w)
+        w |= w >> 7
+        w |= w >> 14
+        v |= (w & 0xF) << (4 * j)
+    return v
+
+
+def _unpack16(b):
+    out = []
+    for j in range(4):
+        nib = (b >> (4 * j)) & 0xF
+        out.append(((nib * 0x00204081) & 0x01010101) & _M32)
+    return np.array(out, dtype="<u4").view(np.uint8)
+
+
+def _member_bits16(yl):
+    m = 0xFFFF
+    for bit, keep in ((1, 0x5555), (2, 0x3333), (4, 0x0F0F), (8, 0x00FF)):
+        if yl & bit:
+            m &= keep
+    return m
+
+
+def _full_add(a, b, c):
+    return a ^ b ^ c, (a & b) | (c & (a ^ b))
+
+
+def _bits_ca(r, S, KH, k, state):
+    rho, n = 1 << S, 1 << r
+    HW = rho // 16 + 2
+    WPR = (HW + 1) // 2
+    HPR, ROWS = 2 * WPR, rho + 2 * KH
+    gmask = ~((32 if rho >= 32 else 16) - 1)
+    out = np.zeros_like(state)
+    bxs, bys = oracle.block_map(r - S, 1)
+    for tbx, tby in zip(bxs.tolist(), bys.tolist()):
+        x0, y0 = tbx << S, tby << S
+        half = np.zeros((ROWS, HPR), dtype=np.uint64)
+        mhalf = np.zeros((ROWS, HPR), dtype=np.uint64)
+        for row in range(ROWS):
+            for h in range(HPR):
+                x, y = x0 - 16 + 16 * h, y0 - KH + row
+                if h < HW and 0 <= x < n and 0 <= y < n and (x & y) == 0:
+                    half[row, h] = _pack16(np.ascontiguousarray(state[y, x:x + 16]))
+                    mhalf[row, h] = _member_bits16(y & 15)
+        cur = half[:, 0::2] | (half[:, 1::2] << np.uint64(16))
+        mask = mhalf[:, 0::2] | (mhalf[:, 1::2] << np.uint64(16))
+        z = np.zeros(1, dtype=np.uint64)
+        one, s31 = np.uint64(1), np.uint64(31)
+        m32 = np.uint64(_M32)
+        for s in range(1, k + 1):
+            nxt = cur.copy()
+            for row in range(s, ROWS - s):
+                a, b, c = cur[row - 1], cur[row], cur[row + 1]
+                planes = []
+                for v in (a, b, c):
+                    vl = np.concatenate([z, v[:-1]])
+                    vr = np.concatenate([v[1:], z])
+                    planes.append((((v << one) | (vl >> s31)) & m32,
+                                   (v >> one) | ((vr << s31) & m32)))
+                (aL, aR), (bL, bR), (cL, cR) = planes
+                us, uc = _full_add(aL, a, aR)          # 3-sum of the row above
+                ds, dc = _full_add(cL, c, cR)          # 3-sum of the row below
+                ms, mc = bL ^ bR, bL & bR              # 2-sum of the row itself
+                s0, c1 = _full_add(us, ms, ds)
+                t0, t1 = _full_add(uc, mc, dc)
+                s1, t2 = t0 ^ c1, t0 & c1
+                nxt[row] = (s0 | b) & s1 & (~(t1 | t2) & m32) & mask[row]
+            cur = nxt
+        for ty in range(rho):
+            for cx in range(rho // 16):
+                x, y = x0 + 16 * cx, y0 + ty
+                if ((x & gmask) & y) != 0:
+                    continue
+                h = 1 + cx
+                bits = (int(cur[KH + ty, h // 2]) >> (16 * (h % 2))) & 0xFFFF
+                out[y, x:x + 16] = _unpack16(bits)
+    return out
+
+
+@pytest.mark.parametrize("r,S,KH,k", [(6, 4, 4, 3), (7, 5, 8, 7), (8, 6, 16, 16),
+                                      (6, 4, 16, 13)])
+def test_bit_sliced_ca_restated_matches_oracle(r, S, KH, k):
+    from paper_1706_04552_gb300 import inputs
+    s0 = inputs.ca_seed_grid(r, 0.45, 21 + r)
+    want = oracle.ca_steps(r, s0, k)
+    assert np.array_equal(_bits_ca(r, S, KH, k, s0), want)
+
+
+def test_pack_and_unpack_are_inverse_on_every_pattern():
+    for b in range(1 << 16):
+        chunk = _unpack16(b)
+        assert set(chunk.tolist()) <= {0, 1}
+        assert _pack16(chunk) == b
+
+
+# ------------------------------------------------------------------------
+# The fused diffusion's per-chunk degree word, restated: byte i = number of
+# in-grid gasket 4-neighbours of cell (x + i, y), or 0xFF off the gasket;
+# 0xFFFFFFFF for a chunk with no gasket cell.  Checked against brute force
+# for every 4-cell chunk of the grid and its one-chunk border.
+# ------------------------------------------------------------------------
+def _spread4(m):
+    return (m * 0x00204081) & 0x01010101
+
+
+def _member_bits4(y):
+    return (0x135F >> (4 * (y & 3))) & 0xF
+
+
+def _chunk_degrees(x, y, n):
+    if x < 0 or y < 0 or x >= n or y >= n or (x & y) != 0:
+        return 0xFFFFFFFF
+    m = _member_bits4(y)
+    pl = int(x > 0 and ((x - 1) & y) == 0)
+    pr = int(x + 4 < n and ((x + 4) & y) == 0)
+    mu = _member_bits4(y - 1) if (y > 0 and (x & (y - 1)) == 0) else 0
+    md = _member_bits4(y + 1) if (y + 1 < n and (x & (y + 1)) == 0) else 0
+    ml, mr = ((m << 1) | pl) & 0xF, (m >> 1) | (pr << 3)
+    deg = _spread4(ml) + _spread4(mr) + _spread4(mu) + _spread4(md)
+    return (deg | (_spread4(~m & 0xF) * 0xFF)) & 0xFFFFFFFF
+
+
+@pytest.mark.parametrize("r", [2, 3, 6])
+def test_chunk_degree_words_match_brute_force(r):
+    n = 1 << r
+    mem = oracle.member_grid(r).astype(bool)
+
+    def member(x, y):
+        return 0 <= x < n and 0 <= y < n and bool(mem[y, x])
+    for y in range(-1, n + 1):
+        for x in range(-4, n + 4, 4):
+            word = _chunk_degrees(x, y, n)
+            if not any(member(x + i, y) for i in range(4)):
+                assert word == 0xFFFFFFFF, (x, y)
+                continue
+            for i in range(4):
+                b = (word >> (8 * i)) & 0xFF
+                if not member(x + i, y):
+                    assert b == 0xFF, (x, y, i)
+                else:
+                    d = sum(member(x + i + dx, y + dy)
+                            for dx, dy in ((-1, 0), (1, 0), (0, -1), (0, 1)))
+                    assert b == d, (x, y, i)
