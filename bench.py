@@ -453,6 +453,21 @@ def batched_workload(sg, torch, dev, stream):
     t_b = timed(batched)
     t_bg = timed(lambda: g.launch(stream))
     g.close()
+    # the same 64 steps as launches of `fuse` fused steps (bit-sliced tiles),
+    # autotuned for that launch shape, captured in one graph
+    fb = sg.CABatch(levels, a, b, autotune=w["autotune_steps"], stream=stream, fuse=w["fuse"])
+    gf = fb.graph(steps, 0, fuse=w["fuse"])
+    t_fg = timed(lambda: gf.launch(stream))
+    gf.close()
+    fo = fb.opts
+    res["batched_fused_graph"] = {
+        "ms": round(t_fg, 3), "GCells_s": _rate(cells, t_fg), "steps_per_launch": w["fuse"],
+        "launches": -(-steps // w["fuse"]),
+        "tuned": {"rho": fb.rho, "order": "interleaved" if fo.order == 1 else "rowmajor",
+                  "ctas_per_sm": fo.ctas_per_sm},
+        "speedup_over_batched_graph": round(t_bg / t_fg, 3),
+        "speedup_over_per_gasket_graph": round(t_pig / t_fg, 3)}
+    del fb
     res.update({
         "per_gasket_eager": {"ms": round(t_pi, 3), "GCells_s": _rate(cells, t_pi),
                              "launches": steps * len(levels)},
@@ -599,11 +614,13 @@ def serving_workload():
     from paper_1706_04552_gb300.serve import ServeConfig, Server, make_trace, summarize
     out = {}
     for tag, rate in (("offered_2000rps", 2000.0), ("offered_20000rps", 20000.0)):
-        for mode in ("batched", "per_gasket"):
-            cfg = ServeConfig(rate=rate, duration=2.0 if rate <= 2000 else 0.5, mode=mode)
+        for name, mode, fuse in (("batched", "batched", 1), ("per_gasket", "per_gasket", 1),
+                                 ("batched_fused16", "batched", 16)):
+            cfg = ServeConfig(rate=rate, duration=2.0 if rate <= 2000 else 0.5, mode=mode,
+                              fuse=fuse)
             server = Server(cfg)
             res = server.run(make_trace(cfg))
-            out.setdefault(tag, {})[mode] = summarize(res, cfg)
+            out.setdefault(tag, {})[name] = summarize(res, cfg)
             del server
     return out
 
@@ -700,7 +717,53 @@ def compare_workloads(sg, torch, dev, stream, w, grid_u8, headline_launch_ms):
                                           "line_GBps": round(lb / (statistics.mean(per) / 1e3) / 1e9, 1)}
         del a, b, bufs
     torch.cuda.empty_cache()
+    # the same step sequences with k steps fused per launch
+    res.update(fused_stencils(sg, torch, dev, stream, rs, res))
     return res
+
+
+def fused_stencils(sg, torch, dev, stream, r, single):
+    """The level-r stencil sequences (256 CA steps, 100 diffusion steps) run
+    as launches of k fused steps (sg_ca_steps / sg_diffuse_steps): rate in
+    cell-steps per second and the ratio to the single-step launches."""
+    from paper_1706_04552_gb300 import inputs, workloads
+    s = workloads.STENCILS
+    n, cells = 1 << r, 3 ** r
+    out = {}
+    for kind in ("ca", "diffusion"):
+        if kind == "ca":
+            idx, vals = inputs.ca_seed_sparse(r, s["ca_p"], s["ca_seed"])
+            dt, total, k, rho = torch.uint8, s["ca_steps"], s["ca_fuse"], s["ca_fuse_rho"]
+        else:
+            idx, vals = inputs.uniform_sparse(r, s["diff_seed"])
+            dt, total, k, rho = torch.float32, s["diff_steps"], s["diff_fuse"], s["diff_fuse_rho"]
+        a = torch.zeros(n * n, dtype=dt, device=dev)
+        a[torch.from_numpy(idx).to(dev)] = torch.from_numpy(vals).to(dev)
+        bufs = [a, torch.zeros_like(a)]
+        chunks = [k] * (total // k) + ([total % k] if total % k else [])
+        pos = [0]
+
+        def launch():
+            kk = chunks[pos[0] % len(chunks)]
+            pos[0] += 1
+            if kind == "ca":
+                sg.ca_steps(bufs[0], bufs[1], r, rho, kk, "lambda", stream)
+            else:
+                sg.diffuse_steps(bufs[0], bufs[1], r, rho, kk, s["alpha"], "lambda", stream)
+            bufs.reverse()
+        for _ in range(len(chunks)):
+            launch()                                   # warm-up: one whole sequence
+        pos[0] = 0
+        ms, per = time_launches(launch, len(chunks), stream)
+        rate = cells * total / (ms / 1e3) / 1e9
+        base = single.get(f"{kind}_r{r}_lambda", {}).get("GCells_s")
+        out[f"{kind}_r{r}_fused"] = {
+            "rho": rho, "steps": total, "steps_per_launch": k, "launches": len(chunks),
+            "us_per_step": round(ms * 1e3 / total, 2), "GCells_s": round(rate, 3),
+            "speedup_vs_single_step": round(rate / base, 3) if base else None}
+        del a, bufs
+        torch.cuda.empty_cache()
+    return out
 
 
 def measure_e2e(sg, torch, dev, stream, w, grp, steps):

@@ -297,6 +297,22 @@ SG_API sg_status sg_batch_ca_graph_create(const sg_batch_plan *plan, int steps,
 SG_API sg_status sg_graph_launch(void *graph, void *stream);
 SG_API sg_status sg_graph_destroy(void *graph);
 
+/* k fused steps of every gasket of the batch in one launch (k = 1 .. SG_FUSE_MAX;
+ * k = 1 is sg_batch_ca_step): parity 0 reads buf_a and writes k steps later
+ * into buf_b, parity 1 the reverse, as for sg_ca_steps.  A warp takes one
+ * work item at a time and runs its tile's k steps bit-sliced in shared
+ * memory; results equal k single batch steps. */
+SG_API sg_status sg_batch_ca_steps(const sg_batch_plan *plan, int parity, int k,
+                                   const sg_launch_opts *opts, void *stream);
+
+/* Capture `steps` steps as launches of k fused steps (the last launch takes
+ * the remainder), parities alternating from start_parity: after
+ * ceil(steps / k) launches the state is in buf_a if that count is even
+ * (start_parity 0).  Otherwise as sg_batch_ca_graph_create. */
+SG_API sg_status sg_batch_ca_graph_create_fused(const sg_batch_plan *plan, int steps, int k,
+                                                int start_parity, const sg_launch_opts *opts,
+                                                void **graph);
+
 /* Autotune a batch: time `trial_steps` parity-0 steps for every rho in
  * {16, 32, 64} allowed by the smallest level, both walking orders and
  * CTAs per SM in {occupancy maximum, 2, 4, 8}; plan the batch with the
@@ -309,6 +325,15 @@ SG_API sg_status sg_batch_ca_autotune(int count, const int *levels, uint8_t *con
                                       uint64_t workspace_bytes, int trial_steps,
                                       sg_batch_plan *plan, sg_launch_opts *opts_out,
                                       void *stream);
+
+/* sg_batch_ca_autotune for launches of k fused steps (sg_batch_ca_steps):
+ * times `trial_launches` parity-0 launches of k steps per candidate (buf_a is
+ * left as it was; buf_b is overwritten). */
+SG_API sg_status sg_batch_ca_autotune_fused(int count, const int *levels, uint8_t *const *buf_a,
+                                            uint8_t *const *buf_b, void *workspace,
+                                            uint64_t workspace_bytes, int trial_launches, int k,
+                                            sg_batch_plan *plan, sg_launch_opts *opts_out,
+                                            void *stream);
 
 /*
  * sg_batch_ca_step_noalloc -- one batch step for callers that cannot allocate

@@ -139,6 +139,14 @@ def lib() -> ctypes.CDLL:
         L.sg_graph_destroy.restype = i32
         L.sg_batch_ca_autotune.argtypes = [i32, vp, vp, vp, vp, u64, i32, p_plan, p_opts, vp]
         L.sg_batch_ca_autotune.restype = i32
+        L.sg_batch_ca_steps.argtypes = [p_plan, i32, i32, p_opts, vp]
+        L.sg_batch_ca_steps.restype = i32
+        L.sg_batch_ca_graph_create_fused.argtypes = [p_plan, i32, i32, i32, p_opts,
+                                                     ctypes.POINTER(vp)]
+        L.sg_batch_ca_graph_create_fused.restype = i32
+        L.sg_batch_ca_autotune_fused.argtypes = [i32, vp, vp, vp, vp, u64, i32, i32, p_plan,
+                                                 p_opts, vp]
+        L.sg_batch_ca_autotune_fused.restype = i32
         L.sg_device_status.argtypes = [vp]
         L.sg_device_status.restype = i32
         L.sg_abi_version.argtypes = []
@@ -379,11 +387,12 @@ class CABatch:
 
     levels: gasket levels; bufs_a / bufs_b: uint8 CUDA tensors of n_i*n_i
     cells (0 off the gasket; the state to step starts in bufs_a).  rho picks
-    the tile side; autotune=K times K steps per candidate and plans with the
-    fastest (rho, walking order, CTAs per SM).  The work list lives in a
-    workspace tensor this object owns."""
+    the tile side; autotune=K times K launches per candidate and plans with
+    the fastest (rho, walking order, CTAs per SM) for launches of `fuse`
+    steps (1: single steps, sg_batch_ca_step; more: sg_batch_ca_steps).  The
+    work list lives in a workspace tensor this object owns."""
 
-    def __init__(self, levels, bufs_a, bufs_b, rho=64, autotune=None, stream=None):
+    def __init__(self, levels, bufs_a, bufs_b, rho=64, autotune=None, stream=None, fuse=1):
         import torch
         self.levels = [int(r) for r in levels]
         count = len(self.levels)
@@ -405,7 +414,12 @@ class CABatch:
         self.opts = None
         st = _stream_handle(self.workspace, stream)
         with _on_device(self.workspace):
-            if autotune:
+            if autotune and int(fuse) > 1:
+                self.opts = LaunchOpts()
+                _check("sg_batch_ca_autotune_fused", int(lib().sg_batch_ca_autotune_fused(
+                    count, lv, pa, pb, self.workspace.data_ptr(), nbytes, int(autotune),
+                    int(fuse), ctypes.byref(self.plan), ctypes.byref(self.opts), st)))
+            elif autotune:
                 self.opts = LaunchOpts()
                 _check("sg_batch_ca_autotune", int(lib().sg_batch_ca_autotune(
                     count, lv, pa, pb, self.workspace.data_ptr(), nbytes, int(autotune),
@@ -427,13 +441,28 @@ class CABatch:
                 ctypes.byref(self.plan), int(parity), _opts_ref(opts),
                 _stream_handle(self.workspace, stream))))
 
-    def graph(self, steps, start_parity=0):
-        """A CUDA graph of `steps` consecutive steps (see Graph)."""
+    def steps(self, k, parity=0, stream=None, order=None, ctas_per_sm=None):
+        """k fused steps of every gasket in one launch (parity as for step)."""
+        opts = self.opts if (order is None and ctas_per_sm is None) else launch_opts(
+            order, None, ctas_per_sm)
+        with _on_device(self.workspace):
+            _check("sg_batch_ca_steps", int(lib().sg_batch_ca_steps(
+                ctypes.byref(self.plan), int(parity), int(k), _opts_ref(opts),
+                _stream_handle(self.workspace, stream))))
+
+    def graph(self, steps, start_parity=0, fuse=1):
+        """A CUDA graph of `steps` consecutive steps (see Graph), as launches
+        of `fuse` fused steps (the last launch takes the remainder)."""
         h = ctypes.c_void_p()
         with _on_device(self.workspace):
-            _check("sg_batch_ca_graph_create", int(lib().sg_batch_ca_graph_create(
-                ctypes.byref(self.plan), int(steps), int(start_parity), _opts_ref(self.opts),
-                ctypes.byref(h))))
+            if int(fuse) > 1:
+                _check("sg_batch_ca_graph_create_fused", int(lib().sg_batch_ca_graph_create_fused(
+                    ctypes.byref(self.plan), int(steps), int(fuse), int(start_parity),
+                    _opts_ref(self.opts), ctypes.byref(h))))
+            else:
+                _check("sg_batch_ca_graph_create", int(lib().sg_batch_ca_graph_create(
+                    ctypes.byref(self.plan), int(steps), int(start_parity),
+                    _opts_ref(self.opts), ctypes.byref(h))))
         return Graph(h, self)
 
 

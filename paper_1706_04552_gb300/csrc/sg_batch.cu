@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "sg.h"
+#include "sg_bits.cuh"
 #include "sg_stencil.cuh"
 
 namespace sg {
@@ -144,6 +145,72 @@ cudaError_t launch_batch(const sg_batch_plan *p, int parity, cudaStream_t st,
     }
 }
 
+// k fused steps of every gasket of the batch, bit-sliced (sg_bits.cuh): a
+// warp takes one work item at a time, finds its gasket, decodes its tile at
+// that gasket's level and runs the k steps of the tile in shared memory.
+template <int S, int KH>
+__global__ void __launch_bounds__(kStencilThreads, 6)
+ca_batch_bits_kernel(BatchView bv, uint32_t total, int parity, int order, int k)
+{
+    using B = BitShape<S, KH>;
+    __shared__ uint32_t sm[B::WARPS][3][B::WORDS];     // two states and the mask, per warp
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *st0 = sm[warp][0], *st1 = sm[warp][1], *mk = sm[warp][2];
+    LambdaLane ll;
+    ll.init(lane, 0, order);
+    const uint64_t stride = (uint64_t)gridDim.x * B::WARPS;
+    for (uint64_t q = (uint64_t)blockIdx.x * B::WARPS + warp; q < total; q += stride) {
+        const uint32_t i = batch_instance(bv.prefix, bv.count, (uint32_t)q);   // warp-uniform
+        const int r = __ldg(bv.level + i), rb = r - S;
+        const uint32_t local = (uint32_t)q - __ldg(bv.prefix + i);
+        ll.set_level(lane, rb);
+        const uint32_t W = pi_word(order, rb);
+        const uint32_t b = local / W, a = local - b * W;
+        const uint2 c = ll.decode(a, b);
+        const uint64_t pa = __ldg(bv.buf_a + i), pb = __ldg(bv.buf_b + i);
+        bits_tile_steps<S, KH>(st0, st1, mk, reinterpret_cast<const uint8_t *>(parity ? pb : pa),
+                               reinterpret_cast<uint8_t *>(parity ? pa : pb), r,
+                               (int)(c.x << S), (int)(c.y << S), k, lane);
+    }
+}
+
+template <int S, int KH>
+cudaError_t launch_batch_fused_t(const sg_batch_plan *p, int parity, int k, cudaStream_t st,
+                                 const LaunchCfg &cfg)
+{
+    using B = BitShape<S, KH>;
+    static std::atomic<int> occ{0};
+    unsigned grid = 1;
+    auto kern = ca_batch_bits_kernel<S, KH>;
+    cudaError_t e = persistent_grid(kern, kStencilThreads, 0,
+                                    ((uint64_t)p->total_tiles + B::WARPS - 1) / B::WARPS, cfg,
+                                    &grid, &occ);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, kStencilThreads, 0, st>>>(view_of(p), p->total_tiles, parity, cfg.order, k);
+    return cudaGetLastError();
+}
+
+// k steps (1 <= k <= SG_FUSE_MAX) of every gasket: one launch.
+cudaError_t launch_batch_k(const sg_batch_plan *p, int parity, int k, cudaStream_t st,
+                           const LaunchCfg &cfg)
+{
+    if (k == 1) return launch_batch(p, parity, st, cfg);
+    if (k < 1 || k > SG_FUSE_MAX) return cudaErrorInvalidValue;
+    const int kh = k <= 4 ? 4 : k <= 8 ? 8 : 16;
+    switch (p->rho * 100 + kh) {
+    case 1604: return launch_batch_fused_t<4, 4>(p, parity, k, st, cfg);
+    case 1608: return launch_batch_fused_t<4, 8>(p, parity, k, st, cfg);
+    case 1616: return launch_batch_fused_t<4, 16>(p, parity, k, st, cfg);
+    case 3204: return launch_batch_fused_t<5, 4>(p, parity, k, st, cfg);
+    case 3208: return launch_batch_fused_t<5, 8>(p, parity, k, st, cfg);
+    case 3216: return launch_batch_fused_t<5, 16>(p, parity, k, st, cfg);
+    case 6404: return launch_batch_fused_t<6, 4>(p, parity, k, st, cfg);
+    case 6408: return launch_batch_fused_t<6, 8>(p, parity, k, st, cfg);
+    case 6416: return launch_batch_fused_t<6, 16>(p, parity, k, st, cfg);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
 bool plan_ok(const sg_batch_plan *p)
 {
     return p != nullptr && p->workspace != nullptr && p->count >= 1 && p->count <= kMaxBatch &&
@@ -230,11 +297,18 @@ sg_status sg_batch_ca_step(const sg_batch_plan *plan, int parity, const sg_launc
     return e == cudaSuccess ? SG_OK : cuda_fail(e);
 }
 
-sg_status sg_batch_ca_graph_create(const sg_batch_plan *plan, int steps, int start_parity,
-                                   const sg_launch_opts *opts, void **graph)
+}  // extern "C"
+
+namespace sg {
+namespace {
+
+// Capture `steps` steps as launches of k fused steps (the last one takes
+// the remainder), parities alternating from start_parity, into a graph.
+sg_status capture_batch(const sg_batch_plan *plan, int steps, int k, int start_parity,
+                        const sg_launch_opts *opts, void **graph)
 {
     if (!plan_ok(plan) || graph == nullptr || steps < 1 || steps > 1000000 ||
-        (start_parity != 0 && start_parity != 1))
+        k < 1 || k > SG_FUSE_MAX || (start_parity != 0 && start_parity != 1))
         return SG_EINVAL;
     LaunchCfg cfg;
     if (!read_launch_opts(opts, &cfg)) return SG_EINVAL;
@@ -245,8 +319,12 @@ sg_status sg_batch_ca_graph_create(const sg_batch_plan *plan, int steps, int sta
     e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaError_t le = cudaSuccess;
-        for (int k = 0; k < steps && le == cudaSuccess; ++k)
-            le = launch_batch(plan, (start_parity + k) & 1, cs, cfg);
+        int parity = start_parity;
+        for (int done = 0; done < steps && le == cudaSuccess; parity ^= 1) {
+            const int kk = std::min(k, steps - done);
+            le = launch_batch_k(plan, parity, kk, cs, cfg);
+            done += kk;
+        }
         cudaGraph_t g = nullptr;
         e = cudaStreamEndCapture(cs, &g);
         if (le != cudaSuccess) e = le;
@@ -258,6 +336,35 @@ sg_status sg_batch_ca_graph_create(const sg_batch_plan *plan, int steps, int sta
         if (g) cudaGraphDestroy(g);
     }
     cudaStreamDestroy(cs);
+    return e == cudaSuccess ? SG_OK : cuda_fail(e);
+}
+
+}  // namespace
+}  // namespace sg
+
+extern "C" {
+
+sg_status sg_batch_ca_graph_create(const sg_batch_plan *plan, int steps, int start_parity,
+                                   const sg_launch_opts *opts, void **graph)
+{
+    return capture_batch(plan, steps, 1, start_parity, opts, graph);
+}
+
+sg_status sg_batch_ca_graph_create_fused(const sg_batch_plan *plan, int steps, int k,
+                                         int start_parity, const sg_launch_opts *opts,
+                                         void **graph)
+{
+    return capture_batch(plan, steps, k, start_parity, opts, graph);
+}
+
+sg_status sg_batch_ca_steps(const sg_batch_plan *plan, int parity, int k,
+                            const sg_launch_opts *opts, void *stream)
+{
+    if (!plan_ok(plan) || (parity != 0 && parity != 1) || k < 1 || k > SG_FUSE_MAX)
+        return SG_EINVAL;
+    LaunchCfg cfg;
+    if (!read_launch_opts(opts, &cfg)) return SG_EINVAL;
+    const cudaError_t e = launch_batch_k(plan, parity, k, (cudaStream_t)stream, cfg);
     return e == cudaSuccess ? SG_OK : cuda_fail(e);
 }
 
@@ -275,19 +382,27 @@ sg_status sg_graph_destroy(void *graph)
     return e == cudaSuccess ? SG_OK : cuda_fail(e);
 }
 
-sg_status sg_batch_ca_autotune(int count, const int *levels, uint8_t *const *buf_a,
-                               uint8_t *const *buf_b, void *workspace, uint64_t workspace_bytes,
-                               int trial_steps, sg_batch_plan *plan, sg_launch_opts *opts_out,
-                               void *stream)
+}  // extern "C"
+
+namespace sg {
+namespace {
+
+// Time `trial_steps` parity-0 launches of k steps for every (rho, walking
+// order, CTAs per SM) and plan with the fastest; results are cached per
+// (trial_steps, k, sorted levels).
+sg_status autotune(int count, const int *levels, uint8_t *const *buf_a, uint8_t *const *buf_b,
+                   void *workspace, uint64_t workspace_bytes, int trial_steps, int k,
+                   sg_batch_plan *plan, sg_launch_opts *opts_out, void *stream)
 {
     if (count < 1 || count > kMaxBatch || levels == nullptr || plan == nullptr ||
-        opts_out == nullptr || trial_steps < 1 || trial_steps > 1000)
+        opts_out == nullptr || trial_steps < 1 || trial_steps > 1000 || k < 1 ||
+        k > SG_FUSE_MAX)
         return SG_EINVAL;
     int min_level = 16;
     std::vector<int> sorted(levels, levels + count);
     std::sort(sorted.begin(), sorted.end());
     min_level = sorted.front();
-    std::string key = std::to_string(trial_steps) + ":";
+    std::string key = std::to_string(trial_steps) + "/" + std::to_string(k) + ":";
     for (int r : sorted) key += std::to_string(r) + ",";
     int best_rho = 0, best_order = 1, best_cps = 0;
     {
@@ -321,10 +436,10 @@ sg_status sg_batch_ca_autotune(int count, const int *levels, uint8_t *const *buf
                     cfg.ctas_per_sm = cps;
                     // repeated parity-0 steps read buffer a and rewrite buffer b:
                     // the caller's current state (a) is left as it was
-                    e = launch_batch(&p, 0, st, cfg);                    // warm-up
+                    e = launch_batch_k(&p, 0, k, st, cfg);               // warm-up
                     if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-                    for (int k = 0; k < trial_steps && e == cudaSuccess; ++k)
-                        e = launch_batch(&p, 0, st, cfg);
+                    for (int t = 0; t < trial_steps && e == cudaSuccess; ++t)
+                        e = launch_batch_k(&p, 0, k, st, cfg);
                     if (e == cudaSuccess) e = cudaEventRecord(e1, st);
                     if (e == cudaSuccess) e = cudaEventSynchronize(e1);
                     float ms = 0.f;
@@ -356,6 +471,29 @@ sg_status sg_batch_ca_autotune(int count, const int *levels, uint8_t *const *buf
     opts_out->store = SG_STORE_AUTO;
     opts_out->ctas_per_sm = best_cps;
     return SG_OK;
+}
+
+}  // namespace
+}  // namespace sg
+
+extern "C" {
+
+sg_status sg_batch_ca_autotune(int count, const int *levels, uint8_t *const *buf_a,
+                               uint8_t *const *buf_b, void *workspace, uint64_t workspace_bytes,
+                               int trial_steps, sg_batch_plan *plan, sg_launch_opts *opts_out,
+                               void *stream)
+{
+    return autotune(count, levels, buf_a, buf_b, workspace, workspace_bytes, trial_steps, 1,
+                    plan, opts_out, stream);
+}
+
+sg_status sg_batch_ca_autotune_fused(int count, const int *levels, uint8_t *const *buf_a,
+                                     uint8_t *const *buf_b, void *workspace,
+                                     uint64_t workspace_bytes, int trial_launches, int k,
+                                     sg_batch_plan *plan, sg_launch_opts *opts_out, void *stream)
+{
+    return autotune(count, levels, buf_a, buf_b, workspace, workspace_bytes, trial_launches, k,
+                    plan, opts_out, stream);
 }
 
 }  // extern "C"

@@ -1,0 +1,196 @@
+// sg_bits.cuh -- the bit-sliced B3/S23 CA on one staged tile, shared by the
+// fused single-gasket kernel (sg_fused.cu) and the fused batch kernel
+// (sg_batch.cu).
+#pragma once
+
+#include "sg_stencil.cuh"
+
+namespace sg {
+
+// ---------------------------------------------------------------------------
+// CA, bit-sliced.  In shared memory a staged row is a string of bits, one
+// cell per bit (bit j of a row = column x0 - 16 + j: a 16-cell halo on each
+// side, then padding to whole 32-bit words), and the B3/S23 rule runs on 32
+// cells at a time: the eight neighbour planes (the rows above and below and
+// the row itself, shifted by one column either way with funnel shifts) are
+// summed by a tree of bitwise full adders, and the bits of the count decide
+// the next state.  One warp owns one tile at a time, so the steps need only
+// __syncwarp.  States are 0/1 bytes in HBM: 16-byte chunks are packed to 16
+// bits when staged and unpacked when stored.
+// ---------------------------------------------------------------------------
+template <int S, int KH> struct BitShape {
+    static constexpr int RHO = 1 << S;
+    static constexpr int HW = RHO / 16 + 2;          // staged 16-cell half-words per row
+    static constexpr int WPR = (HW + 1) / 2;         // 32-bit words per row
+    static constexpr int ROWS = RHO + 2 * KH;
+    static constexpr int WORDS = ROWS * WPR;
+    static constexpr int WARPS = kStencilThreads / 32;
+    static constexpr uint32_t GROUP_MASK = StencilGroup<uint8_t, S>::GROUP_MASK;
+};
+
+// Bit i of the result = byte i of a chunk of 0/1 bytes.
+__device__ __forceinline__ uint32_t pack16(uint4 c)
+{
+    // byte j of a word sits at bit 8j; two shifted ORs bring it to bit j
+    auto nib = [](uint32_t w) {
+        w |= w >> 7;
+        w |= w >> 14;
+        return w & 0xFu;
+    };
+    return nib(c.x) | (nib(c.y) << 4) | (nib(c.z) << 8) | (nib(c.w) << 12);
+}
+
+// Byte i of the result = bit i of b (0/1 bytes).
+__device__ __forceinline__ uint4 unpack16(uint32_t b)
+{
+    // nib * (1 + 2^7 + 2^14 + 2^21) puts bit j of the nibble at bit 8j; the
+    // four shifted copies do not overlap, so no carry disturbs them
+    auto bytes = [](uint32_t nib) { return (nib * 0x00204081u) & 0x01010101u; };
+    return make_uint4(bytes(b & 0xFu), bytes((b >> 4) & 0xFu), bytes((b >> 8) & 0xFu),
+                      bytes((b >> 12) & 0xFu));
+}
+
+// Bits i of 16 with (i & yl) == 0 (yl = y mod 16): the gasket cells of a
+// 16-cell chunk at a column x with (x & y) == 0, x a multiple of 16.
+__device__ __forceinline__ uint32_t member_bits16(uint32_t yl)
+{
+    uint32_t m = 0xFFFFu;
+    if (yl & 1u) m &= 0x5555u;
+    if (yl & 2u) m &= 0x3333u;
+    if (yl & 4u) m &= 0x0F0Fu;
+    if (yl & 8u) m &= 0x00FFu;
+    return m;
+}
+
+__device__ __forceinline__ void full_add(uint32_t a, uint32_t b, uint32_t c, uint32_t &sum,
+                                         uint32_t &carry)
+{
+    sum = a ^ b ^ c;
+    carry = (a & b) | (c & (a ^ b));
+}
+
+// Stage the tile at (x0, y0) with its halo as bits, and the gasket mask of
+// every staged bit (0 off the grid, off the gasket and in padding).
+template <int S, int KH>
+__device__ __forceinline__ void bits_stage(uint32_t *bits, uint32_t *mask,
+                                           const uint8_t *__restrict__ in, int r, int x0, int y0,
+                                           int lane)
+{
+    using B = BitShape<S, KH>;
+    constexpr int HPR = 2 * B::WPR;                  // half-words per row, padding included
+    const int n = 1 << r;
+    uint16_t *bh = reinterpret_cast<uint16_t *>(bits);
+    uint16_t *mh = reinterpret_cast<uint16_t *>(mask);
+#pragma unroll 4
+    for (int i = lane; i < B::ROWS * HPR; i += 32) {
+        const int row = i / HPR, h = i - row * HPR;
+        const int x = x0 - 16 + 16 * h, y = y0 - KH + row;
+        uint32_t v = 0u, m = 0u;
+        if (h < B::HW && x >= 0 && y >= 0 && x < n && y < n && (x & y) == 0) {
+            v = pack16(__ldg(reinterpret_cast<const uint4 *>(in + (((uint64_t)y << r) +
+                                                                    (uint64_t)x))));
+            m = member_bits16((uint32_t)y & 15u);
+        }
+        bh[i] = (uint16_t)v;
+        mh[i] = (uint16_t)m;
+    }
+}
+
+// Row v of a staged bit-string with its left and right neighbours' planes
+// (bit j <- bit j-1 and bit j <- bit j+1; words past the row's ends are not
+// staged and read as 0 -- the address read is the word itself).
+struct BitRow {
+    uint32_t v, l, r;
+};
+template <int WPR>
+__device__ __forceinline__ BitRow bit_row(const uint32_t *row, int w)
+{
+    const bool hl = w > 0, hr = w < WPR - 1;
+    const uint32_t vl = row[hl ? w - 1 : w] & (hl ? 0xFFFFFFFFu : 0u);
+    const uint32_t vr = row[hr ? w + 1 : w] & (hr ? 0xFFFFFFFFu : 0u);
+    const uint32_t v = row[w];
+    return BitRow{v, __funnelshift_l(vl, v, 1), __funnelshift_r(v, vr, 1)};
+}
+
+// One step over the window rows [s, ROWS - s): src -> dst.  The lanes form
+// G = 32 / WPR groups; lane (g, w) updates word w of a run of consecutive
+// rows, carrying down the run each row's horizontal sums: the 3-cell sum
+// (l + v + r) serves the rows above and below it, the 2-cell sum (l + r) the
+// row itself, so a row costs one full adder, one half adder and the merge:
+//   count = up3 + mid2 + dn3 = s0 + 2 s1 + 4 (t1 + t2).
+template <int S, int KH>
+__device__ __forceinline__ void bits_ca_step(const uint32_t *src, uint32_t *dst,
+                                             const uint32_t *mask, int s, int lane)
+{
+    using B = BitShape<S, KH>;
+    constexpr int G = 32 / B::WPR;
+    const int g = lane / B::WPR, w = lane - g * B::WPR;
+    if (g >= G) return;                               // idle lanes (32 not a multiple of WPR)
+    const int rows = B::ROWS - 2 * s, run = (rows + G - 1) / G;
+    const int first = s + g * run;
+    const int last = min(first + run, B::ROWS - s);
+    if (first >= last) return;
+    BitRow u = bit_row<B::WPR>(src + (first - 1) * B::WPR, w);
+    uint32_t us, uc;                                  // 3-sum of the row above
+    full_add(u.l, u.v, u.r, us, uc);
+    BitRow m = bit_row<B::WPR>(src + first * B::WPR, w);
+    uint32_t ms3, mc3;                                // 3-sum of the current row
+    full_add(m.l, m.v, m.r, ms3, mc3);
+    for (int row = first; row < last; ++row) {
+        const BitRow d = bit_row<B::WPR>(src + (row + 1) * B::WPR, w);
+        uint32_t ds3, dc3;
+        full_add(d.l, d.v, d.r, ds3, dc3);
+        const uint32_t ms2 = m.l ^ m.r, mc2 = m.l & m.r;   // 2-sum of the current row
+        uint32_t s0, c1, t0, t1;
+        full_add(us, ms2, ds3, s0, c1);
+        full_add(uc, mc2, dc3, t0, t1);
+        const uint32_t s1 = t0 ^ c1, t2 = t0 & c1;
+        // alive next iff count is 3, or count is 2 and alive: s1 set, no
+        // weight-4 bit, and s0 or the cell itself
+        dst[row * B::WPR + w] = (s0 | m.v) & s1 & ~(t1 | t2) & mask[row * B::WPR + w];
+        us = ms3;
+        uc = mc3;
+        m = d;
+        ms3 = ds3;
+        mc3 = dc3;
+    }
+}
+
+// Unpack the tile rows (rows [KH, KH + RHO), half-words 1 .. RHO/16) to HBM,
+// whole 32-byte sectors where a tile row spans them.
+template <int S, int KH>
+__device__ __forceinline__ void bits_store(const uint32_t *bits, uint8_t *__restrict__ out,
+                                           int r, int x0, int y0, int lane)
+{
+    using B = BitShape<S, KH>;
+    constexpr int CPR = B::RHO / 16, HPR = 2 * B::WPR;
+    const uint16_t *bh = reinterpret_cast<const uint16_t *>(bits);
+    for (int i = lane; i < B::RHO * CPR; i += 32) {
+        const int ty = i / CPR, cx = i - ty * CPR;
+        const uint32_t x = (uint32_t)(x0 + 16 * cx), y = (uint32_t)(y0 + ty);
+        if (!in_gasket(x & B::GROUP_MASK, y)) continue;
+        const uint32_t v = bh[(KH + ty) * HPR + 1 + cx];
+        *reinterpret_cast<uint4 *>(out + ((uint64_t)y << r) + x) = unpack16(v);
+    }
+}
+
+// k steps of one tile by one warp: stage (tile + halo, from `in`), step in
+// shared memory, store the tile to `out`.  st0 / st1 / mk: the warp's two
+// state buffers and mask buffer, BitShape<S, KH>::WORDS words each.
+template <int S, int KH>
+__device__ __forceinline__ void bits_tile_steps(uint32_t *st0, uint32_t *st1, uint32_t *mk,
+                                                const uint8_t *__restrict__ in,
+                                                uint8_t *__restrict__ out, int r, int x0, int y0,
+                                                int k, int lane)
+{
+    bits_stage<S, KH>(st0, mk, in, r, x0, y0, lane);
+    __syncwarp();
+    for (int s = 1; s <= k; ++s) {
+        bits_ca_step<S, KH>((s & 1) ? st0 : st1, (s & 1) ? st1 : st0, mk, s, lane);
+        __syncwarp();
+    }
+    bits_store<S, KH>((k & 1) ? st1 : st0, out, r, x0, y0, lane);
+    __syncwarp();                        // the buffers are read before the next staging
+}
+
+}  // namespace sg

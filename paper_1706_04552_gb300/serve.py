@@ -16,6 +16,12 @@ of many resident gaskets of different levels.  The serving loop:
     iteration; a request completes when its last step has run;
   * reports per-request latency (arrival to completion) and throughput.
 
+With fuse > 1 an iteration advances a gasket by up to `fuse` steps at once:
+the active gaskets are grouped by the largest power of two k <= min(fuse,
+steps left in the head request), and each group is one batched launch of k
+fused steps (sg_batch_ca_steps).  A gasket never steps past its head
+request, so every result is still the plain per-gasket step sequence.
+
 mode="per_gasket" runs the same scheduler with one single-gasket launch per
 active gasket per iteration instead of the batched launch, for comparison.
 
@@ -47,6 +53,7 @@ class ServeConfig:
     ca_p: float = 0.3
     rho: int = 32
     mode: str = "batched"             # or "per_gasket"
+    fuse: int = 1                     # most steps one iteration advances a gasket (batched)
 
 
 def gasket_levels(cfg: ServeConfig) -> np.ndarray:
@@ -68,9 +75,21 @@ def make_trace(cfg: ServeConfig):
     return t, g, k
 
 
+def launch_groups(fuse: int) -> list[int]:
+    """Step counts of the launch groups an iteration may use: 1, 2, 4, ...
+    up to fuse."""
+    return [1 << j for j in range(int(fuse).bit_length()) if (1 << j) <= fuse]
+
+
+def steps_this_iteration(left: int, groups: list[int]) -> int:
+    """Steps a gasket whose head request has `left` steps to go advances in
+    one iteration: the largest group size not above `left`."""
+    return max(k for k in groups if k <= left)
+
+
 class _Gasket:
     __slots__ = ("gid", "level", "n2", "host", "cur", "nxt", "resident", "queue",
-                 "last_use", "steps_done")
+                 "last_use", "steps_done", "advance")
 
     def __init__(self, gid, level, host):
         self.gid = gid
@@ -82,6 +101,7 @@ class _Gasket:
         self.queue = []                   # [request index, steps left] in arrival order
         self.last_use = 0
         self.steps_done = 0
+        self.advance = 1                  # steps the current iteration takes
 
     @property
     def device_bytes(self):
@@ -113,8 +133,12 @@ class Server:
         self.evictions = 0
         self.loads = 0
         cnt = len(self.gaskets)
-        self.ws = torch.empty(int(sg.lib().sg_batch_workspace_bytes(cnt)), dtype=torch.uint8,
-                              device=self.dev)
+        if cfg.fuse < 1 or cfg.fuse > sg.FUSE_MAX:
+            raise ValueError(f"fuse must be 1..{sg.FUSE_MAX}")
+        # one work-list workspace per launch group (k = 1, 2, 4, ...)
+        self.ks = launch_groups(cfg.fuse)
+        wsb = int(sg.lib().sg_batch_workspace_bytes(cnt))
+        self.ws = [torch.empty(wsb, dtype=torch.uint8, device=self.dev) for _ in self.ks]
         self._lv = np.zeros(cnt, dtype=np.int32)
         self._pa = np.zeros(cnt, dtype=np.uint64)
         self._pb = np.zeros(cnt, dtype=np.uint64)
@@ -151,26 +175,37 @@ class Server:
         return True
 
     # ------------------------------------------------------------- stepping
+    def _steps_for(self, g):
+        return steps_this_iteration(g.queue[0][1], self.ks)
+
     def _step(self, active):
+        """Advance every active gasket; returns the number of launches."""
         sg = self.sg
         if self.cfg.mode == "per_gasket":
             for g in active:
                 sg.ca_step(g.cur, g.nxt, g.level, min(self.cfg.rho, 1 << g.level), "lambda",
                            self.stream)
-            return
-        m = len(active)
-        for j, g in enumerate(active):
-            self._lv[j] = g.level
-            self._pa[j] = g.cur.data_ptr()
-            self._pb[j] = g.nxt.data_ptr()
+            return len(active)
         L = sg.lib()
-        st = L.sg_batch_ca_plan(m, self._lv.ctypes.data, self._pa.ctypes.data,
-                                self._pb.ctypes.data, self.cfg.rho, self.ws.data_ptr(),
-                                self.ws.numel(), ctypes.byref(self._plan),
-                                self.stream.cuda_stream)
-        sg._check("sg_batch_ca_plan", int(st))
-        sg._check("sg_batch_ca_step", int(L.sg_batch_ca_step(
-            ctypes.byref(self._plan), 0, None, self.stream.cuda_stream)))
+        launches = 0
+        for slot, k in enumerate(self.ks):
+            group = [g for g in active if g.advance == k]
+            if not group:
+                continue
+            for j, g in enumerate(group):
+                self._lv[j] = g.level
+                self._pa[j] = g.cur.data_ptr()
+                self._pb[j] = g.nxt.data_ptr()
+            ws = self.ws[slot]
+            st = L.sg_batch_ca_plan(len(group), self._lv.ctypes.data, self._pa.ctypes.data,
+                                    self._pb.ctypes.data, self.cfg.rho, ws.data_ptr(),
+                                    ws.numel(), ctypes.byref(self._plan),
+                                    self.stream.cuda_stream)
+            sg._check("sg_batch_ca_plan", int(st))
+            sg._check("sg_batch_ca_steps", int(L.sg_batch_ca_steps(
+                ctypes.byref(self._plan), 0, k, None, self.stream.cuda_stream)))
+            launches += 1
+        return launches
 
     # ----------------------------------------------------------------- loop
     def run(self, trace, on_complete=None):
@@ -208,23 +243,24 @@ class Server:
             if not active:
                 raise RuntimeError("a requested gasket does not fit the device budget")
             self.tick += 1
+            for g in active:
+                g.advance = self._steps_for(g) if self.cfg.mode == "batched" else 1
             tb = time.perf_counter()
-            self._step(active)
+            launches += self._step(active)
             self.stream.synchronize()
             te = time.perf_counter()
             busy += te - tb
             iters += 1
-            launches += 1 if self.cfg.mode == "batched" else len(active)
             tdone = te - t0
             for g in active:
                 g.cur, g.nxt = g.nxt, g.cur
                 g.last_use = self.tick
-                g.steps_done += 1
-                cells += 3 ** g.level
+                g.steps_done += g.advance
+                cells += 3 ** g.level * g.advance
                 head = g.queue[0]
                 if np.isnan(start_at[head[0]]):
                     start_at[head[0]] = tb - t0
-                head[1] -= 1
+                head[1] -= g.advance
                 if head[1] == 0:
                     g.queue.pop(0)
                     done_at[head[0]] = tdone
@@ -251,7 +287,7 @@ class Server:
 def summarize(res, cfg: ServeConfig):
     lat_ms = res["latency_s"] * 1e3
     return {
-        "mode": cfg.mode,
+        "mode": cfg.mode if cfg.fuse == 1 else f"{cfg.mode}, up to {cfg.fuse} fused steps",
         "requests": int(res["requests"]),
         "offered_rate_rps": cfg.rate,
         "throughput_rps": round(res["requests"] / res["wall_s"], 1),

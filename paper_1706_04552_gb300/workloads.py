@@ -42,5 +42,6 @@ STENCILS = dict(levels=(14, 15), ca_p=0.3, ca_seed=0, ca_steps=256,
 # steps each: one launch per step over the prefix-summed work list (captured
 # in a CUDA graph, autotuned) against 64 separate per-gasket launches.
 BATCH = dict(count=64, level_lo=8, level_hi=14, level_seed=2, ca_p=0.3, ca_seed=2,
-             steps=64, autotune_steps=4)
+             steps=64, autotune_steps=4,
+             fuse=16)                   # steps per launch of the fused batched form
 

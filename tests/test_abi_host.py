@@ -187,3 +187,24 @@ def test_batch_plan_validation_is_host_side(L):
     h = ctypes.c_void_p()
     assert sg.lib().sg_batch_ca_graph_create(ctypes.byref(bad), 4, 0, None, ctypes.byref(h)) == sg.SG_EINVAL
     assert sg.lib().sg_graph_launch(None, None) == sg.SG_EINVAL
+    assert sg.lib().sg_batch_ca_steps(ctypes.byref(bad), 0, 4, None, None) == sg.SG_EINVAL
+    assert sg.lib().sg_batch_ca_graph_create_fused(ctypes.byref(bad), 16, 4, 0, None,
+                                                   ctypes.byref(h)) == sg.SG_EINVAL
+    # a well-formed plan (never launched: only its fields are checked here)
+    good = sg.BatchPlan()
+    good.workspace, good.workspace_bytes, good.count = FAKE, ws, n
+    good.rho, good.total_tiles, good.max_level = 16, 9 + 27 + 81, 10
+    for k in (0, -2, sg.FUSE_MAX + 1):
+        assert sg.lib().sg_batch_ca_steps(ctypes.byref(good), 0, k, None, None) == sg.SG_EINVAL
+        assert sg.lib().sg_batch_ca_graph_create_fused(ctypes.byref(good), 16, k, 0, None,
+                                                       ctypes.byref(h)) == sg.SG_EINVAL
+    assert sg.lib().sg_batch_ca_steps(ctypes.byref(good), 2, 4, None, None) == sg.SG_EINVAL
+    assert sg.lib().sg_batch_ca_graph_create_fused(ctypes.byref(good), 0, 4, 0, None,
+                                                   ctypes.byref(h)) == sg.SG_EINVAL
+    bad_opts = sg.launch_opts(order=3)
+    assert sg.lib().sg_batch_ca_steps(ctypes.byref(good), 0, 4, ctypes.byref(bad_opts),
+                                      None) == sg.SG_EINVAL
+    for k in (0, sg.FUSE_MAX + 1):
+        assert sg.lib().sg_batch_ca_autotune_fused(n, lv, pa, pb, FAKE + 0x900000, ws, 2, k,
+                                                   ctypes.byref(plan), ctypes.byref(sg.LaunchOpts()),
+                                                   None) == sg.SG_EINVAL

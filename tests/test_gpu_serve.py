@@ -68,3 +68,17 @@ def test_serve_per_gasket_mode(orc):
                       mode="per_gasket")
     s = _serve_and_check(orc, cfg)
     assert s["launches"] >= s["iterations"]
+
+
+def test_serve_fused_same_alone_and_in_the_mix(orc):
+    # iterations advance gaskets by up to 16 fused steps, grouped by the steps
+    # left in each head request; every result still equals stepping alone
+    cfg = ServeConfig(gaskets=48, level_max=11, rate=3000.0, duration=0.25, seed=8, fuse=16)
+    s = _serve_and_check(orc, cfg)
+    assert s["launches"] >= s["iterations"]
+
+
+def test_serve_fused_with_evictions_to_host(orc):
+    cfg = ServeConfig(gaskets=32, level_max=10, rate=3000.0, duration=0.2, seed=10,
+                      budget_bytes=3 << 20, fuse=8)
+    _serve_and_check(orc, cfg, expect_evictions=True)

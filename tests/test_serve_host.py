@@ -1,7 +1,8 @@
 """Host-side pieces of the server: the seeded level mix and request trace."""
 import numpy as np
 
-from paper_1706_04552_gb300.serve import ServeConfig, gasket_levels, make_trace
+from paper_1706_04552_gb300.serve import (ServeConfig, gasket_levels, launch_groups,
+                                          make_trace, steps_this_iteration)
 
 
 def test_levels_are_geometric_toward_small_levels():
@@ -27,3 +28,22 @@ def test_trace_is_poisson_and_seeded():
     assert k.min() >= 1 and k.max() <= 32
     t2, g2, k2 = make_trace(cfg)
     assert np.array_equal(t, t2) and np.array_equal(g, g2) and np.array_equal(k, k2)
+
+
+def test_fused_launch_groups_never_cross_a_request():
+    assert launch_groups(1) == [1]
+    assert launch_groups(16) == [1, 2, 4, 8, 16]
+    assert launch_groups(12) == [1, 2, 4, 8]
+    for fuse in (1, 2, 5, 8, 16):
+        groups = launch_groups(fuse)
+        for steps in range(1, 40):
+            # a request of `steps` steps is served in iterations that each
+            # take a group size <= the steps still left; they add up exactly
+            left, seen = steps, []
+            while left:
+                k = steps_this_iteration(left, groups)
+                assert 1 <= k <= min(left, fuse) and k in groups
+                seen.append(k)
+                left -= k
+            assert sum(seen) == steps
+            assert len(seen) <= steps // fuse + 5
