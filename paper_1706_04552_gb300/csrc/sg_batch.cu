@@ -153,9 +153,9 @@ __global__ void __launch_bounds__(kStencilThreads, 6)
 ca_batch_bits_kernel(BatchView bv, uint32_t total, int parity, int order, int k)
 {
     using B = BitShape<S, KH>;
-    __shared__ uint32_t sm[B::WARPS][3][B::WORDS];     // two states and the mask, per warp
+    __shared__ uint32_t sm[B::WARPS][3][B::BUFW];      // two states and the mask, per warp
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t *st0 = sm[warp][0], *st1 = sm[warp][1], *mk = sm[warp][2];
+    uint32_t *st0 = sm[warp][0] + 1, *st1 = sm[warp][1] + 1, *mk = sm[warp][2] + 1;
     LambdaLane ll;
     ll.init(lane, 0, order);
     const uint64_t stride = (uint64_t)gridDim.x * B::WARPS;

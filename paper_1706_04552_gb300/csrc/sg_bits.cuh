@@ -24,6 +24,10 @@ template <int S, int KH> struct BitShape {
     static constexpr int WPR = (HW + 1) / 2;         // 32-bit words per row
     static constexpr int ROWS = RHO + 2 * KH;
     static constexpr int WORDS = ROWS * WPR;
+    // a buffer holds one pad word before and after the rows, so that a
+    // row's neighbour words can be read at fixed offsets -1 / +1 (the pads'
+    // contents are never used: edge words are masked off)
+    static constexpr int BUFW = WORDS + 2;
     static constexpr int WARPS = kStencilThreads / 32;
     static constexpr uint32_t GROUP_MASK = StencilGroup<uint8_t, S>::GROUP_MASK;
 };
@@ -96,19 +100,16 @@ __device__ __forceinline__ void bits_stage(uint32_t *bits, uint32_t *mask,
     }
 }
 
-// Row v of a staged bit-string with its left and right neighbours' planes
-// (bit j <- bit j-1 and bit j <- bit j+1; words past the row's ends are not
-// staged and read as 0 -- the address read is the word itself).
+// Word w of a staged row and its left and right neighbour planes (bit j <-
+// bit j-1 and bit j <- bit j+1).  p points at the word; its neighbours are
+// read at p[-1] and p[+1] and masked with kl / kr, which are 0 at the row's
+// ends (there the reads land in the next or previous row, or in a pad word).
 struct BitRow {
     uint32_t v, l, r;
 };
-template <int WPR>
-__device__ __forceinline__ BitRow bit_row(const uint32_t *row, int w)
+__device__ __forceinline__ BitRow bit_row(const uint32_t *p, uint32_t kl, uint32_t kr)
 {
-    const bool hl = w > 0, hr = w < WPR - 1;
-    const uint32_t vl = row[hl ? w - 1 : w] & (hl ? 0xFFFFFFFFu : 0u);
-    const uint32_t vr = row[hr ? w + 1 : w] & (hr ? 0xFFFFFFFFu : 0u);
-    const uint32_t v = row[w];
+    const uint32_t v = p[0], vl = p[-1] & kl, vr = p[1] & kr;
     return BitRow{v, __funnelshift_l(vl, v, 1), __funnelshift_r(v, vr, 1)};
 }
 
@@ -130,14 +131,21 @@ __device__ __forceinline__ void bits_ca_step(const uint32_t *src, uint32_t *dst,
     const int first = s + g * run;
     const int last = min(first + run, B::ROWS - s);
     if (first >= last) return;
-    BitRow u = bit_row<B::WPR>(src + (first - 1) * B::WPR, w);
+    const uint32_t kl = w > 0 ? 0xFFFFFFFFu : 0u, kr = w < B::WPR - 1 ? 0xFFFFFFFFu : 0u;
+    const uint32_t *p = src + (first - 1) * B::WPR + w;
+    const BitRow u = bit_row(p, kl, kr);
     uint32_t us, uc;                                  // 3-sum of the row above
     full_add(u.l, u.v, u.r, us, uc);
-    BitRow m = bit_row<B::WPR>(src + first * B::WPR, w);
+    p += B::WPR;
+    BitRow m = bit_row(p, kl, kr);
     uint32_t ms3, mc3;                                // 3-sum of the current row
     full_add(m.l, m.v, m.r, ms3, mc3);
+    const uint32_t *pk = mask + first * B::WPR + w;
+    uint32_t *po = dst + first * B::WPR + w;
+#pragma unroll 2
     for (int row = first; row < last; ++row) {
-        const BitRow d = bit_row<B::WPR>(src + (row + 1) * B::WPR, w);
+        p += B::WPR;
+        const BitRow d = bit_row(p, kl, kr);
         uint32_t ds3, dc3;
         full_add(d.l, d.v, d.r, ds3, dc3);
         const uint32_t ms2 = m.l ^ m.r, mc2 = m.l & m.r;   // 2-sum of the current row
@@ -147,7 +155,9 @@ __device__ __forceinline__ void bits_ca_step(const uint32_t *src, uint32_t *dst,
         const uint32_t s1 = t0 ^ c1, t2 = t0 & c1;
         // alive next iff count is 3, or count is 2 and alive: s1 set, no
         // weight-4 bit, and s0 or the cell itself
-        dst[row * B::WPR + w] = (s0 | m.v) & s1 & ~(t1 | t2) & mask[row * B::WPR + w];
+        *po = (s0 | m.v) & s1 & ~(t1 | t2) & *pk;
+        po += B::WPR;
+        pk += B::WPR;
         us = ms3;
         uc = mc3;
         m = d;
@@ -176,7 +186,8 @@ __device__ __forceinline__ void bits_store(const uint32_t *bits, uint8_t *__rest
 
 // k steps of one tile by one warp: stage (tile + halo, from `in`), step in
 // shared memory, store the tile to `out`.  st0 / st1 / mk: the warp's two
-// state buffers and mask buffer, BitShape<S, KH>::WORDS words each.
+// state buffers and mask buffer, each pointing one word into a buffer of
+// BitShape<S, KH>::BUFW words (the pads).
 template <int S, int KH>
 __device__ __forceinline__ void bits_tile_steps(uint32_t *st0, uint32_t *st1, uint32_t *mk,
                                                 const uint8_t *__restrict__ in,

@@ -84,9 +84,9 @@ ca_bits_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int r,
                uint64_t ntiles, int k)
 {
     using B = BitShape<S, KH>;
-    __shared__ uint32_t sm[B::WARPS][3][B::WORDS];     // two states and the mask, per warp
+    __shared__ uint32_t sm[B::WARPS][3][B::BUFW];      // two states and the mask, per warp
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    uint32_t *st0 = sm[warp][0], *st1 = sm[warp][1], *mk = sm[warp][2];
+    uint32_t *st0 = sm[warp][0] + 1, *st1 = sm[warp][1] + 1, *mk = sm[warp][2] + 1;
 
     const int rb = r - S;
     LambdaLane ll;
@@ -103,50 +103,14 @@ ca_bits_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int r,
 }
 
 // ---------------------------------------------------------------------------
-// Diffusion.  One CTA per tile; thread t owns the staged float4 chunks
-// c = t + 256 j for the whole tile.  Whether each of a chunk's four cells is
-// a gasket cell, and its gasket degree, depend only on the position, so they
-// are worked out once per tile into one word per chunk (byte i = degree of
-// cell i, or kNotCell), and chunks holding no gasket cell are skipped at
-// every step (they are 0 in both state buffers).
+// Diffusion.  One CTA per tile.  Whether each of a chunk's four cells is a
+// gasket cell, and its gasket degree, depend only on the position: they are
+// worked out once per tile into one word per chunk (chunk_degrees).  The
+// chunks that hold gasket cells -- a third of a 64-tile's chunks -- are
+// compacted into a list while the tile is staged, and every step runs over
+// that list only, so the threads of a warp all do useful work; the other
+// chunks are 0 in both state buffers throughout.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kNotCell = 0xFFu;
-constexpr uint32_t kDeadChunk = 0xFFFFFFFFu;
-
-// 0x01 in byte i for each set bit i of a 4-bit mask.
-__device__ __forceinline__ uint32_t spread4(uint32_t m) { return (m * 0x00204081u) & 0x01010101u; }
-
-// Bits i of 4 with (i & y) == 0: the gasket cells of a 4-cell chunk at a
-// column x with (x & y) == 0, x a multiple of 4 (table by y mod 4).
-__device__ __forceinline__ uint32_t member_bits4(uint32_t y) { return (0x135Fu >> (4u * (y & 3u))) & 0xFu; }
-
-// Degree word of the chunk at (x, y), x a multiple of 4 (kDeadChunk when it
-// holds no gasket cell).  In a chunk with (x & y) == 0, cell i's left and
-// right neighbours inside the chunk are members iff bits i-1, i+1 of the
-// row's member mask are set; across the chunk's edges, and above and below,
-// the neighbour chunk is tested whole.
-__device__ __forceinline__ uint32_t chunk_degrees(int x, int y, int n)
-{
-    if (x < 0 || y < 0 || x >= n || y >= n || (x & y) != 0) return kDeadChunk;
-    const uint32_t m = member_bits4((uint32_t)y);
-    const uint32_t pl = x > 0 && ((x - 1) & y) == 0;
-    const uint32_t pr = x + 4 < n && ((x + 4) & y) == 0;
-    const uint32_t mu = (y > 0 && (x & (y - 1)) == 0) ? member_bits4((uint32_t)(y - 1)) : 0u;
-    const uint32_t md = (y + 1 < n && (x & (y + 1)) == 0) ? member_bits4((uint32_t)(y + 1)) : 0u;
-    const uint32_t ml = ((m << 1) | pl) & 0xFu, mr = (m >> 1) | (pr << 3);
-    const uint32_t deg = spread4(ml) + spread4(mr) + spread4(mu) + spread4(md);
-    return deg | (spread4(~m & 0xFu) * kNotCell);
-}
-
-__device__ __forceinline__ float degree_cell(uint32_t word, int i, float u, float l, float rr,
-                                             float up, float dn, float alpha)
-{
-    const uint32_t d = (word >> (8 * i)) & 0xFFu;
-    // (float)d for d <= 4: the low mantissa bits of 2^23 + d, minus 2^23
-    const float degf = __uint_as_float(0x4B000000u | d) - 8388608.0f;
-    return d == kNotCell ? 0.0f : diffuse_update(u, l, rr, up, dn, degf, alpha);
-}
-
 // (4 resident CTAs: the shared-memory limit of the 64-tiles with an 8-row
 // halo; the bound keeps the unrolled chunk loop from taking more registers)
 template <int S, int KH, int MAP>
@@ -161,16 +125,24 @@ diffuse_fused_kernel(const float *__restrict__ in, float *__restrict__ out, int 
     float *b0 = reinterpret_cast<float *>(fused_smem);
     float *b1 = reinterpret_cast<float *>(fused_smem + F::BUF);
     __shared__ uint2 coord;
+    __shared__ uint32_t live_n;
+    __shared__ uint16_t live_chunk[CH];          // staged chunk index (row * PC + column)
+    __shared__ uint32_t live_deg[CH];            // its degree word
 
     const int n = 1 << r, rb = r - S;
+    const int lane = threadIdx.x & 31;
+    const uint32_t lanes_below = (1u << lane) - 1u;
     LambdaLane ll;
-    ll.init(threadIdx.x & 31, rb, order);
+    ll.init(lane, rb, order);
     const uint32_t W = pi_word(order, rb);
 
     for (uint64_t q = blockIdx.x; q < ntiles; q += gridDim.x) {
         if (threadIdx.x < 32) {
             const uint2 c = decode_tile<MAP>(q, ntiles, rb, W, ll);
-            if (threadIdx.x == 0) coord = c;
+            if (threadIdx.x == 0) {
+                coord = c;
+                live_n = 0u;
+            }
         }
         __syncthreads();                 // coord visible; last tile's buffers free
         const uint2 c = coord;
@@ -179,18 +151,31 @@ diffuse_fused_kernel(const float *__restrict__ in, float *__restrict__ out, int 
             continue;
         }
         const int x0 = (int)(c.x << S), y0 = (int)(c.y << S);
-        uint32_t deg[PER];
+        // stage the live chunks, zero the rest in both buffers, list the live
+        // ones (warp-aggregated appends)
 #pragma unroll
         for (int j = 0; j < PER; ++j) {
             const int ch = threadIdx.x + j * kStencilThreads;
-            deg[j] = kDeadChunk;
+            uint32_t w = kDeadChunk;
+            int row = 0, cc = 0;
             if (ch < CH) {
-                const int row = ch / F::PC, cc = ch - row * F::PC;
-                const int x = x0 - F::HX + 4 * cc, y = y0 - KH + row;
-                deg[j] = chunk_degrees(x, y, n);
+                row = ch / F::PC;
+                cc = ch - row * F::PC;
+                w = chunk_degrees(x0 - F::HX + 4 * cc, y0 - KH + row, n);
+            }
+            const bool live = w != kDeadChunk;
+            const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, live);
+            uint32_t base = 0;
+            if (lane == 0 && ballot) base = atomicAdd(&live_n, (uint32_t)__popc(ballot));
+            base = __shfl_sync(0xFFFFFFFFu, base, 0);
+            if (ch < CH) {
                 float *d0 = b0 + row * F::P + 4 * cc;
-                if (deg[j] != kDeadChunk) {
+                if (live) {
+                    const int x = x0 - F::HX + 4 * cc, y = y0 - KH + row;
                     cp_async16(d0, in + (((uint64_t)y << r) + (uint64_t)x));
+                    const uint32_t pos = base + (uint32_t)__popc(ballot & lanes_below);
+                    live_chunk[pos] = (uint16_t)ch;
+                    live_deg[pos] = w;
                 } else {
                     *reinterpret_cast<float4 *>(d0) = make_float4(0.f, 0.f, 0.f, 0.f);
                     *reinterpret_cast<float4 *>(b1 + (d0 - b0)) = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -200,13 +185,12 @@ diffuse_fused_kernel(const float *__restrict__ in, float *__restrict__ out, int 
         cp_async_commit();
         cp_async_wait<0>();
         __syncthreads();
+        const uint32_t nlive = live_n;
         for (int s = 1; s <= k; ++s) {
             const float *src = (s & 1) ? b0 : b1;
             float *dst = (s & 1) ? b1 : b0;
-#pragma unroll
-            for (int j = 0; j < PER; ++j) {
-                const int ch = threadIdx.x + j * kStencilThreads;
-                if (deg[j] == kDeadChunk) continue;       // also every ch >= CH
+            for (uint32_t i = threadIdx.x; i < nlive; i += kStencilThreads) {
+                const int ch = (int)live_chunk[i];
                 const int row = ch / F::PC, cc = ch - row * F::PC;
                 if (row < s || row >= F::ROWS - s) continue;
                 const float *mid = src + row * F::P + 4 * cc;
@@ -218,7 +202,7 @@ diffuse_fused_kernel(const float *__restrict__ in, float *__restrict__ out, int 
                 const bool hl = cc > 0, hr = cc < F::PC - 1;
                 const float lv = mid[hl ? -1 : 0], rv = mid[hr ? 4 : 3];
                 const float l = hl ? lv : 0.f, rr = hr ? rv : 0.f;
-                const uint32_t w = deg[j];
+                const uint32_t w = live_deg[i];
                 float4 o;
                 o.x = degree_cell(w, 0, cm.x, l, cm.y, cu.x, cd.x, alpha);
                 o.y = degree_cell(w, 1, cm.y, cm.x, cm.z, cu.y, cd.y, alpha);
@@ -229,22 +213,23 @@ diffuse_fused_kernel(const float *__restrict__ in, float *__restrict__ out, int 
             __syncthreads();
         }
         fused_store<float, S, KH>((k & 1) ? b1 : b0, out, r, x0, y0);
-        // the next iteration's first barrier orders these reads before the
-        // next staging overwrites b0 / b1
+        // the next iteration's first barrier orders these reads (and those
+        // of live_n and the lists) before the next tile overwrites them
     }
 }
 
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-// Grid of a fused kernel; the dynamic shared-memory limit is raised once per
-// device (bit d of `attr_devs`) for buffers above the default 48 KB.
+// Grid of a fused kernel.  Its dynamic shared memory plus its static arrays
+// can pass the default 48 KB per CTA, so the dynamic limit is raised to the
+// size used, once per device (bit d of `attr_devs`).
 template <typename K>
 static cudaError_t fused_grid(K kern, int smem, uint64_t ntiles, const LaunchCfg &cfg,
                               unsigned *grid, std::atomic<int> *occ,
                               std::atomic<uint64_t> *attr_devs)
 {
-    if (smem > 48 * 1024) {
+    {
         int dev = 0;
         cudaError_t e = cudaGetDevice(&dev);
         if (e != cudaSuccess) return e;

@@ -237,6 +237,47 @@ __device__ __forceinline__ float diffuse_cell(uint32_t x, uint32_t y, uint32_t n
     return diffuse_update(u, l, rr, up, dn, (float)deg, alpha);
 }
 
+// Per-chunk degrees.  Whether each cell of a 4-cell chunk is a gasket cell,
+// and its gasket degree, depend only on the position: one word per chunk
+// holds them (byte i = degree of cell i, or kNotCell), computed with a few
+// word operations instead of four membership tests per cell.
+constexpr uint32_t kNotCell = 0xFFu;
+constexpr uint32_t kDeadChunk = 0xFFFFFFFFu;
+
+// 0x01 in byte i for each set bit i of a 4-bit mask.
+__device__ __forceinline__ uint32_t spread4(uint32_t m) { return (m * 0x00204081u) & 0x01010101u; }
+
+// Bits i of 4 with (i & y) == 0: the gasket cells of a 4-cell chunk at a
+// column x with (x & y) == 0, x a multiple of 4 (table by y mod 4).
+__device__ __forceinline__ uint32_t member_bits4(uint32_t y) { return (0x135Fu >> (4u * (y & 3u))) & 0xFu; }
+
+// Degree word of the chunk at (x, y), x a multiple of 4 (kDeadChunk when it
+// holds no gasket cell).  In a chunk with (x & y) == 0, cell i's left and
+// right neighbours inside the chunk are members iff bits i-1, i+1 of the
+// row's member mask are set; across the chunk's edges, and above and below,
+// the neighbour chunk is tested whole.
+__device__ __forceinline__ uint32_t chunk_degrees(int x, int y, int n)
+{
+    if (x < 0 || y < 0 || x >= n || y >= n || (x & y) != 0) return kDeadChunk;
+    const uint32_t m = member_bits4((uint32_t)y);
+    const uint32_t pl = x > 0 && ((x - 1) & y) == 0;
+    const uint32_t pr = x + 4 < n && ((x + 4) & y) == 0;
+    const uint32_t mu = (y > 0 && (x & (y - 1)) == 0) ? member_bits4((uint32_t)(y - 1)) : 0u;
+    const uint32_t md = (y + 1 < n && (x & (y + 1)) == 0) ? member_bits4((uint32_t)(y + 1)) : 0u;
+    const uint32_t ml = ((m << 1) | pl) & 0xFu, mr = (m >> 1) | (pr << 3);
+    const uint32_t deg = spread4(ml) + spread4(mr) + spread4(mu) + spread4(md);
+    return deg | (spread4(~m & 0xFu) * kNotCell);
+}
+
+__device__ __forceinline__ float degree_cell(uint32_t word, int i, float u, float l, float rr,
+                                             float up, float dn, float alpha)
+{
+    const uint32_t d = (word >> (8 * i)) & 0xFFu;
+    // (float)d for d <= 4: the low mantissa bits of 2^23 + d, minus 2^23
+    const float degf = __uint_as_float(0x4B000000u | d) - 8388608.0f;
+    return d == kNotCell ? 0.0f : diffuse_update(u, l, rr, up, dn, degf, alpha);
+}
+
 template <int S>
 __device__ __forceinline__ void diffuse_compute_group(const float *sm,
                                                       const StencilTile<float> *tiles,
@@ -249,17 +290,19 @@ __device__ __forceinline__ void diffuse_compute_group(const float *sm,
         if (tl.bx == kNoTile) continue;
         const uint32_t x = (tl.bx << S) + 4u * cx, y = (tl.by << S) + ty;
         if (!in_gasket(x & G::GROUP_MASK, y)) continue;   // sector holds no gasket cell
-        const uint32_t n = 1u << tl.r;
-        const float *mid = sm + t * G::TILE + (ty + 1) * G::P + 4 + 4 * cx;
-        const float4 cu = *reinterpret_cast<const float4 *>(mid - G::P);
-        const float4 cm = *reinterpret_cast<const float4 *>(mid);
-        const float4 cd = *reinterpret_cast<const float4 *>(mid + G::P);
-        const float l = mid[-1], rr = mid[4];
-        float4 o;
-        o.x = diffuse_cell(x + 0u, y, n, cm.x, l, cm.y, cu.x, cd.x, alpha);
-        o.y = diffuse_cell(x + 1u, y, n, cm.y, cm.x, cm.z, cu.y, cd.y, alpha);
-        o.z = diffuse_cell(x + 2u, y, n, cm.z, cm.y, cm.w, cu.z, cd.z, alpha);
-        o.w = diffuse_cell(x + 3u, y, n, cm.w, cm.z, rr, cu.w, cd.w, alpha);
+        const uint32_t w = chunk_degrees((int)x, (int)y, 1 << tl.r);
+        float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (w != kDeadChunk) {
+            const float *mid = sm + t * G::TILE + (ty + 1) * G::P + 4 + 4 * cx;
+            const float4 cu = *reinterpret_cast<const float4 *>(mid - G::P);
+            const float4 cm = *reinterpret_cast<const float4 *>(mid);
+            const float4 cd = *reinterpret_cast<const float4 *>(mid + G::P);
+            const float l = mid[-1], rr = mid[4];
+            o.x = degree_cell(w, 0, cm.x, l, cm.y, cu.x, cd.x, alpha);
+            o.y = degree_cell(w, 1, cm.y, cm.x, cm.z, cu.y, cd.y, alpha);
+            o.z = degree_cell(w, 2, cm.z, cm.y, cm.w, cu.z, cd.z, alpha);
+            o.w = degree_cell(w, 3, cm.w, cm.z, rr, cu.w, cd.w, alpha);
+        }
         *reinterpret_cast<float4 *>(tl.out + ((uint64_t)y << tl.r) + x) = o;
     }
 }
