@@ -132,13 +132,40 @@ struct OmegaWalker {
 // ---------------------------------------------------------------------------
 enum : int { kValConst = 0, kValLinear31 = 1, kValHash = 2 };
 
-// SplitMix64 output for generator state s (Steele, Lea & Flood, OOPSLA 2014).
-__device__ __forceinline__ uint64_t splitmix64(uint64_t s)
+// SplitMix64 (Steele, Lea & Flood, OOPSLA 2014): for generator state s,
+// z = s + gamma; z = (z ^ (z >> 30)) * M1; z = (z ^ (z >> 27)) * M2;
+// output z ^ (z >> 31).
+//
+// The high 32 bits of the output for state seedmix ^ key, key below 2^32.  The
+// written values use only bits 40..63 of the output (u8: h >> 56; f32:
+// h >> 40), and the finaliser's last step h = z ^ (z >> 31) leaves bits
+// 33..63 of z unchanged, so h >> 32 agrees with z >> 32 in every bit used
+// (bits 40..63); that step is skipped.  The rest is the same 64-bit
+// arithmetic written on 32-bit halves: the state's high half is the
+// constant high half of seedmix, each 64-bit shift is one funnel shift per
+// half, and the second product needs only its high half.
+__device__ __forceinline__ uint32_t splitmix64_hi(uint64_t seedmix, uint32_t key)
 {
-    uint64_t z = s + kGoldenGamma;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
+    constexpr uint32_t G_LO = (uint32_t)kGoldenGamma, G_HI = (uint32_t)(kGoldenGamma >> 32);
+    constexpr uint64_t M1 = 0xBF58476D1CE4E5B9ull, M2 = 0x94D049BB133111EBull;
+    constexpr uint32_t M1_LO = (uint32_t)M1, M1_HI = (uint32_t)(M1 >> 32);
+    constexpr uint32_t M2_LO = (uint32_t)M2, M2_HI = (uint32_t)(M2 >> 32);
+    const uint32_t s_lo = (uint32_t)seedmix ^ key, s_hi = (uint32_t)(seedmix >> 32);
+    // z = s + gamma
+    const uint32_t z_lo = s_lo + G_LO;
+    const uint32_t z_hi = s_hi + G_HI + (z_lo < s_lo ? 1u : 0u);
+    // z ^= z >> 30
+    const uint32_t t_lo = z_lo ^ __funnelshift_r(z_lo, z_hi, 30);
+    const uint32_t t_hi = z_hi ^ (z_hi >> 30);
+    // z *= M1 (mod 2^64)
+    const uint64_t p = (uint64_t)t_lo * M1_LO;
+    const uint32_t y_lo = (uint32_t)p;
+    const uint32_t y_hi = (uint32_t)(p >> 32) + t_lo * M1_HI + t_hi * M1_LO;
+    // z ^= z >> 27
+    const uint32_t w_lo = y_lo ^ __funnelshift_r(y_lo, y_hi, 27);
+    const uint32_t w_hi = y_hi ^ (y_hi >> 27);
+    // high half of z * M2 (mod 2^64)
+    return __umulhi(w_lo, M2_LO) + w_lo * M2_HI + w_hi * M2_LO;
 }
 
 // Value of the cell whose linear index (row-major, pitch n = 2^r) is
@@ -167,9 +194,9 @@ template <typename T, int VK> struct CellValue {
         } else if constexpr (VK == kValLinear31) {
             return (T)((base + koff) & 0xFFu);
         } else {
-            const uint64_t h = splitmix64(seedmix ^ (uint64_t)(base + koff));
-            if constexpr (sizeof(T) == 1) return (T)(h >> 56);
-            else return (float)(uint32_t)(h >> 40) * (1.0f / 16777216.0f);
+            const uint32_t hi = splitmix64_hi(seedmix, base + koff);   // bits 32..63
+            if constexpr (sizeof(T) == 1) return (T)(hi >> 24);
+            else return (float)(hi >> 8) * (1.0f / 16777216.0f);
         }
     }
 };

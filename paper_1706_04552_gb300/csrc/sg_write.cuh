@@ -521,13 +521,15 @@ write_fill_kernel(const __grid_constant__ CUtensorMap tmap, int r, int order, ui
     // issuing thread has waited (end of iteration k-1) until every store but
     // the newest ST-2 has read its slot, i.e. through the store of tile
     // k+1-ST, which is the last tile that used slot (k+1) % ST -- the slot
-    // iteration k+1 writes after that barrier.
-    uint64_t k = 0;
-    for (uint64_t q = team; q < ntiles; q += nteams, ++k) {
+    // iteration k+1 writes after that barrier.  (Tiles number below 2^32:
+    // fill needs rho * sizeof(T) >= 16, so r - s <= 12.)
+    int slot = 0;
+    for (uint32_t q = (uint32_t)team; q < (uint32_t)ntiles; q += (uint32_t)nteams) {
         const uint2 b = tw.next(q);                  // every warp of the team decodes
         const bool empty = MAP == kMapBBox && (b.x & b.y) != 0u;
         const uint32_t x0 = b.x << S, y0 = b.y << S;
-        uint8_t *tile = buf + (int)(k % ST) * TS::BUF;
+        uint8_t *tile = buf + slot * TS::BUF;
+        slot = slot + 1 == ST ? 0 : slot + 1;
         if (!empty) {
             const uint32_t base = CellValue<T, VK>::base_of(x0, y0, r);
 #pragma unroll

@@ -307,3 +307,47 @@ def test_chunk_degree_words_match_brute_force(r):
                     d = sum(member(x + i + dx, y + dy)
                             for dx, dy in ((-1, 0), (1, 0), (0, -1), (0, 1)))
                     assert b == d, (x, y, i)
+
+
+# ------------------------------------------------------------------------
+# The write kernels' hash: SplitMix64's high word computed on 32-bit halves
+# (splitmix64_hi), restated operation for operation and checked against the
+# 64-bit SplitMix64 of the input module on the bits the values use.
+# ------------------------------------------------------------------------
+def _splitmix64_hi(seedmix, key):
+    m = np.uint64(0xFFFFFFFF)
+    g = 0x9E3779B97F4A7C15
+    m1, m2 = 0xBF58476D1CE4E5B9, 0x94D049BB133111EB
+    u = lambda v: np.uint64(v)
+    key = key.astype(np.uint64)
+    s_lo = (u(seedmix) & m) ^ key
+    s_hi = u(seedmix) >> u(32)
+    z_lo = (s_lo + u(g & 0xFFFFFFFF)) & m
+    z_hi = (s_hi + u(g >> 32) + (z_lo < s_lo).astype(np.uint64)) & m
+
+    def fshr(lo, hi, n):                      # __funnelshift_r(lo, hi, n)
+        return ((lo >> u(n)) | (hi << u(32 - n))) & m
+    t_lo = z_lo ^ fshr(z_lo, z_hi, 30)
+    t_hi = z_hi ^ (z_hi >> u(30))
+    p = t_lo * u(m1 & 0xFFFFFFFF)             # < 2^64: exact in uint64
+    y_lo = p & m
+    y_hi = ((p >> u(32)) + ((t_lo * u(m1 >> 32)) & m) + ((t_hi * u(m1 & 0xFFFFFFFF)) & m)) & m
+    w_lo = y_lo ^ fshr(y_lo, y_hi, 27)
+    w_hi = y_hi ^ (y_hi >> u(27))
+    umulhi = (w_lo * u(m2 & 0xFFFFFFFF)) >> u(32)
+    return (umulhi + ((w_lo * u(m2 >> 32)) & m) + ((w_hi * u(m2 & 0xFFFFFFFF)) & m)) & m
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3, 12345, 2**63 + 7])
+def test_hash_high_word_matches_splitmix64(seed):
+    from paper_1706_04552_gb300 import inputs
+    rng = np.random.default_rng(seed % 1000)
+    keys = np.concatenate([np.arange(4096, dtype=np.uint64),
+                           rng.integers(0, 2**32, 200_000, dtype=np.uint64),
+                           np.array([2**32 - 1, 2**31, 2**31 - 1], dtype=np.uint64)])
+    with np.errstate(over="ignore"):
+        seedmix = (seed * 0x9E3779B97F4A7C15) & (2**64 - 1)
+        h = inputs.splitmix64_next(np.uint64(seedmix) ^ keys)
+    hi = _splitmix64_hi(seedmix, keys)
+    assert np.array_equal(hi >> np.uint64(24), h >> np.uint64(56))   # u8 values
+    assert np.array_equal(hi >> np.uint64(8), h >> np.uint64(40))    # f32 values
