@@ -144,6 +144,31 @@ class Server:
         self._pb = np.zeros(cnt, dtype=np.uint64)
         self._plan = sg.BatchPlan()
         self.tick = 0
+        self._warm_up()
+
+    def _warm_up(self):
+        """Launch every kernel the loop will use once, on a scratch gasket of
+        all-dead cells, so that the first requests do not pay for loading
+        kernels or for occupancy queries."""
+        torch, sg = self.torch, self.sg
+        r = max(6, self.cfg.rho.bit_length() - 1)
+        a = torch.zeros(1 << (2 * r), dtype=torch.uint8, device=self.dev)
+        b = torch.zeros_like(a)
+        if self.cfg.mode == "per_gasket":
+            sg.ca_step(a, b, r, self.cfg.rho, "lambda", self.stream)
+        else:
+            L = sg.lib()
+            lv = np.array([r], dtype=np.int32)
+            pa = np.array([a.data_ptr()], dtype=np.uint64)
+            pb = np.array([b.data_ptr()], dtype=np.uint64)
+            for slot, k in enumerate(self.ks):
+                ws = self.ws[slot]
+                sg._check("sg_batch_ca_plan", int(L.sg_batch_ca_plan(
+                    1, lv.ctypes.data, pa.ctypes.data, pb.ctypes.data, self.cfg.rho,
+                    ws.data_ptr(), ws.numel(), ctypes.byref(self._plan), self.stream.cuda_stream)))
+                sg._check("sg_batch_ca_steps", int(L.sg_batch_ca_steps(
+                    ctypes.byref(self._plan), 0, k, None, self.stream.cuda_stream)))
+        self.stream.synchronize()
 
     # ------------------------------------------------------------ residency
     def _evict_one(self, protect):
