@@ -358,6 +358,10 @@ def run_ours(args, grp: Group):
     out["e2e"] = measure_e2e(sg, torch, dev, stream, w, grp, min(args.steps, 4))
     if grp.rank == 0 and grp.world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(w)
+        try:
+            out["cpu_baseline_all_cores"] = cpu_baseline_all_cores(w)
+        except Exception as e:                      # reported, never fatal
+            out["cpu_baseline_all_cores"] = {"unavailable": f"{type(e).__name__}: {e}"}
     return out
 
 
@@ -802,6 +806,40 @@ def cpu_baseline(w):
     return {"value": round(3 ** r / dt / 1e9, 6), "unit": UNIT, "cores": 1,
             "kind": "oracle", "seconds": round(dt, 3),
             "sample": f"whole level-{r} uint8 grid ({n}x{n}), one pass, hash seed {w['seed']}",
+            "host": _host_desc()}
+
+
+def _oracle_band(job):
+    """One row band of the oracle's write pass (a worker of the all-cores
+    baseline): rows [y0, y1) of the level-r grid into a band buffer."""
+    import numpy as np
+    import oracle
+    r, y0, y1, seed = job
+    buf = np.zeros((y1 - y0, 1 << r), dtype=np.uint8)
+    oracle.map_write(r, buf, oracle.VAL_HASH, seed, y0=y0, y1=y1)
+    return y1 - y0
+
+
+def cpu_baseline_all_cores(w, band=1024):
+    """The same oracle pass over the whole level-16 grid, its row bands spread
+    over one process per host core (a spawn-context pool: this process has
+    used the GPU already, and a forked worker could hang).  The oracle's code
+    is unchanged; only its bands run side by side."""
+    import multiprocessing as mp
+    r, n = w["r"], 1 << w["r"]
+    cores = os.cpu_count() or 1
+    jobs = [(r, y0, y0 + band, w["seed"]) for y0 in range(0, n, band)]
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        pool.map(_oracle_band, [(r, 0, 1, w["seed"])] * cores)   # workers load the oracle
+        t0 = time.perf_counter()
+        rows = sum(pool.map(_oracle_band, jobs, chunksize=1))
+        dt = time.perf_counter() - t0
+    assert rows == n
+    return {"value": round(3 ** r / dt / 1e9, 6), "unit": UNIT, "cores": cores,
+            "kind": "oracle", "seconds": round(dt, 3),
+            "sample": (f"whole level-{r} uint8 grid ({n}x{n}), one pass, hash seed "
+                       f"{w['seed']}, {n // band} bands of {band} rows over {cores} processes"),
             "host": _host_desc()}
 
 

@@ -43,3 +43,11 @@ def test_clock_summary():
     assert s["sm_mhz"] == 2070 and s["sm_max_mhz"] == 2070
     assert s["reasons"] == ["sw_power_cap"] and s["samples"] == 3
     assert bench.summarize_clocks([])["samples"] == 0
+
+
+def test_all_cores_oracle_baseline_covers_the_grid():
+    # the bands of the all-cores baseline tile the grid exactly once
+    import bench
+    out = bench.cpu_baseline_all_cores(dict(r=8, seed=1), band=32)
+    assert out["kind"] == "oracle" and out["cores"] >= 1 and out["value"] > 0
+    assert "8 bands of 32 rows" in out["sample"]
