@@ -355,7 +355,10 @@ def run_ours(args, grp: Group):
         out["serving"] = serving_workload()
     del grid
     torch.cuda.empty_cache()
-    out["e2e"] = measure_e2e(sg, torch, dev, stream, w, grp, min(args.steps, 4))
+    copy = measure_e2e(sg, torch, dev, stream, w, grp, min(args.steps, 4))
+    mapped = measure_e2e_mapped(sg, torch, dev, stream, w, grp, 20)
+    out["e2e"] = dict(mapped if mapped["value"] >= copy["value"] else copy)
+    out["e2e_paths"] = {"mapped": mapped, "copy": copy}
     if grp.rank == 0 and grp.world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(w)
         try:
@@ -770,6 +773,37 @@ def fused_stencils(sg, torch, dev, stream, r, single):
     return out
 
 
+def measure_e2e_mapped(sg, torch, dev, stream, w, grp, steps):
+    """The same metric through the public API with the grid kept in pinned
+    host memory and written in place (sg_map_write_mapped): the kernel reads
+    and writes the touched chunks of the host grid over the host link
+    (NVLink-C2C), with read-merge-write stores that keep every other byte.
+    Each step ends with the stream synchronised, the result in host memory."""
+    from paper_1706_04552_gb300 import workloads
+    r, n = w["r"], 1 << w["r"]
+    m = workloads.WRITE_MAPPED
+    host = torch.zeros(n * n, dtype=torch.uint8, pin_memory=True)
+
+    def step():
+        sg.map_write_mapped(host, r, m["rho"], m["map"], w["value"], w["seed"], stream,
+                            order=m["order"], store=m["store"])
+
+    step()
+    torch.cuda.synchronize(dev)
+    grp.barrier()
+    ms, _ = time_launches(step, steps, stream)
+    ms = grp.max(ms)
+    del host
+    sector = touched_bytes(r, 1, 32)
+    return {"value": round(grp.world * 3 ** r * steps / (ms / 1e3) / 1e9, 4), "unit": UNIT,
+            "h2d_bytes_per_step": sector, "d2h_bytes_per_step": sector,
+            "steps": steps, "ms_per_step": round(ms / steps, 3),
+            "path": (f"grid in pinned host memory, written in place by the kernel over the "
+                     f"host link ({m['map']}, rho {m['rho']}, {m['order']}, {m['store']} "
+                     f"stores); bytes per step = the touched 32-byte sectors read and "
+                     f"written back")}
+
+
 def measure_e2e(sg, torch, dev, stream, w, grp, steps):
     """The same metric through the public API with the grid in pinned host
     memory: every step copies the grid in, runs the pass and copies it out."""
@@ -790,7 +824,8 @@ def measure_e2e(sg, torch, dev, stream, w, grp, steps):
     del host, dgrid
     return {"value": round(grp.world * 3 ** r * steps / (ms / 1e3) / 1e9, 4), "unit": UNIT,
             "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-            "steps": steps, "ms_per_step": round(ms / steps, 3)}
+            "steps": steps, "ms_per_step": round(ms / steps, 3),
+            "path": "grid copied from pinned host memory to the device, written, copied back"}
 
 
 def cpu_baseline(w):

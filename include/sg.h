@@ -202,6 +202,24 @@ SG_API sg_status sg_diffuse_step_ex(int r, int rho, sg_map map, const float *in,
                                     float alpha, const sg_launch_opts *opts, void *stream);
 
 /*
+ * sg_map_write_mapped -- the map-and-write pass on a grid that stays in host
+ * memory.  host_grid is page-locked host memory mapped into the device's
+ * address space (cudaHostAlloc, or pinned torch tensors, on a system with
+ * unified addressing); the kernel reads and writes it where it is, over the
+ * host link (NVLink-C2C on Grace), so only the touched chunks cross it: no
+ * staging copy of the whole grid is made.  The pointer is checked with
+ * cudaPointerGetAttributes before any launch (other memory: SG_EINVAL).
+ * Stores: SG_STORE_AUTO (staged where the tile rows allow it, else scatter),
+ * SG_STORE_STAGED or SG_STORE_SCATTER; SG_STORE_TMA and SG_STORE_FILL
+ * (bulk tensor copies) are SG_EUNSUPPORTED here.  Otherwise as sg_map_write_ex;
+ * the result is in host memory once the stream has completed.
+ */
+SG_API sg_status sg_map_write_mapped(int r, int rho, sg_map map, sg_dtype dtype,
+                                     void *host_grid, sg_value_kind value_kind,
+                                     uint64_t value_or_seed, const sg_launch_opts *opts,
+                                     void *stream);
+
+/*
  * sg_ca_steps / sg_diffuse_steps -- k consecutive steps of sg_ca_step /
  * sg_diffuse_step in one launch: out = step^k(in); `in` is not modified.
  * Every tile is staged in shared memory with a halo at least k cells deep

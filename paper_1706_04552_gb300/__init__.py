@@ -28,7 +28,8 @@ __all__ = [
     "sg_launch_stats", "sg_status_str", "sg_abi_version", "sg_device_status",
     "device_status",
     "CABatch", "Graph", "BatchPlan",
-    "map_write", "map_write_host", "ca_step", "diffuse_step", "ca_steps", "diffuse_steps",
+    "map_write", "map_write_host", "map_write_mapped", "sg_map_write_mapped", "ca_step",
+    "diffuse_step", "ca_steps", "diffuse_steps",
     "block_map", "launch_stats",
     "MAPS", "DTYPES", "VALUES", "ORDERS", "STORES",
 ]
@@ -114,6 +115,8 @@ def lib() -> ctypes.CDLL:
         L.sg_ca_step_ex.restype = i32
         L.sg_diffuse_step_ex.argtypes = [i32, i32, i32, vp, vp, ctypes.c_float, p_opts, vp]
         L.sg_diffuse_step_ex.restype = i32
+        L.sg_map_write_mapped.argtypes = [i32, i32, i32, i32, vp, i32, u64, p_opts, vp]
+        L.sg_map_write_mapped.restype = i32
         L.sg_ca_steps.argtypes = [i32, i32, i32, vp, vp, i32, p_opts, vp]
         L.sg_ca_steps.restype = i32
         L.sg_diffuse_steps.argtypes = [i32, i32, i32, vp, vp, ctypes.c_float, i32, p_opts, vp]
@@ -213,6 +216,12 @@ def sg_diffuse_step_ex(r, rho, map_kind, in_ptr, out_ptr, alpha, opts=None, stre
                                         _opts_ref(opts), stream))
 
 
+def sg_map_write_mapped(r, rho, map_kind, dtype, host_ptr, value_kind, value_or_seed,
+                        opts=None, stream=0) -> int:
+    return int(lib().sg_map_write_mapped(r, rho, map_kind, dtype, host_ptr, value_kind,
+                                         value_or_seed & (2**64 - 1), _opts_ref(opts), stream))
+
+
 def sg_ca_steps(r, rho, map_kind, in_ptr, out_ptr, k, opts=None, stream=0) -> int:
     return int(lib().sg_ca_steps(r, rho, map_kind, in_ptr, out_ptr, k, _opts_ref(opts), stream))
 
@@ -308,6 +317,34 @@ def map_write_host(host_grid, dev_grid, r: int, rho: int, map="lambda", value="h
         dev_grid.copy_(host_grid, non_blocking=True)
         map_write(dev_grid, r, rho, map, value, value_or_seed, st, order=order, store=store)
         host_grid.copy_(dev_grid, non_blocking=True)
+    return host_grid
+
+
+def map_write_mapped(host_grid, r: int, rho: int, map="lambda", value="hash", value_or_seed=1,
+                     stream=None, order=None, store=None, device=None):
+    """Write pass on a grid kept in pinned host memory, read and written in
+    place by the kernel over the host link (sg_map_write_mapped).  Returns
+    without synchronising: the result is in ``host_grid`` once the stream is
+    complete."""
+    import torch
+    if host_grid.is_cuda or not host_grid.is_contiguous() or not host_grid.is_pinned():
+        raise TypeError("host_grid: expected a contiguous pinned CPU tensor")
+    if host_grid.dtype not in (torch.uint8, torch.float32):
+        raise TypeError("host_grid: expected uint8 or float32")
+    if host_grid.numel() != 1 << (2 * r):
+        raise ValueError(f"host_grid: expected {1 << (2 * r)} elements for level {r}")
+    dt = DTYPES["u8"] if host_grid.dtype == torch.uint8 else DTYPES["f32"]
+    vk = VALUES[value] if isinstance(value, str) else int(value)
+    opts = launch_opts(order, store, None)
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    if stream is None:
+        st = torch.cuda.current_stream(dev).cuda_stream
+    else:
+        st = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    with torch.cuda.device(dev):
+        _check("sg_map_write_mapped", sg_map_write_mapped(r, rho, _map_id(map), dt,
+                                                          host_grid.data_ptr(), vk,
+                                                          value_or_seed, opts, st))
     return host_grid
 
 

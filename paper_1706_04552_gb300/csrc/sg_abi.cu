@@ -199,6 +199,46 @@ sg_status sg_map_write_ex(int r, int rho, sg_map map, sg_dtype dtype, void *grid
                                    value_or_seed, (cudaStream_t)stream, cfg));
 }
 
+sg_status sg_map_write_mapped(int r, int rho, sg_map map, sg_dtype dtype, void *host_grid,
+                              sg_value_kind value_kind, uint64_t value_or_seed,
+                              const sg_launch_opts *opts, void *stream)
+{
+    int s = 0;
+    if (!valid_level_tile(r, rho, &s)) return SG_EINVAL;
+    if (map < SG_MAP_LAMBDA || map > SG_MAP_LAMBDA_UNROLL) return SG_EINVAL;
+    if (value_kind < SG_VAL_CONST || value_kind > SG_VAL_HASH) return SG_EINVAL;
+    if (host_grid == nullptr) return SG_EINVAL;
+    if (dtype != SG_U8 && dtype != SG_F32) return SG_EINVAL;
+    LaunchCfg cfg;
+    if (!read_launch_opts(opts, &cfg)) return SG_EINVAL;
+    const int elem = dtype == SG_U8 ? 1 : 4;
+    // only the paths that move data with plain loads and stores
+    if (cfg.store == SG_STORE_TMA || cfg.store == SG_STORE_FILL) return SG_EUNSUPPORTED;
+    // the pointer must be page-locked host memory mapped into the device's
+    // address space; anything else is refused before a launch
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, host_grid) != cudaSuccess) {
+        cudaGetLastError();                           // reset the runtime's last error
+        set_last_error_message("sg_map_write_mapped: pointer attributes unavailable");
+        return SG_EINVAL;
+    }
+    if (attr.type != cudaMemoryTypeHost || attr.devicePointer == nullptr) {
+        set_last_error_message("sg_map_write_mapped: not page-locked host memory mapped "
+                               "into the device");
+        return SG_EINVAL;
+    }
+    void *grid = attr.devicePointer;
+    if (!aligned(grid, (uintptr_t)elem)) return SG_EINVAL;
+    const bool can_stage = rho * elem >= 16 && aligned(grid, 16);
+    if (cfg.store == SG_STORE_STAGED && !can_stage) return SG_EUNSUPPORTED;
+    if (cfg.store == SG_STORE_AUTO) cfg.store = can_stage ? kStoreStaged : kStoreScatter;
+    if (dtype == SG_U8)
+        return finish(launch_write_u8(r, s, (int)map, (int)value_kind, (uint8_t *)grid,
+                                      value_or_seed, (cudaStream_t)stream, cfg));
+    return finish(launch_write_f32(r, s, (int)map, (int)value_kind, (float *)grid,
+                                   value_or_seed, (cudaStream_t)stream, cfg));
+}
+
 sg_status sg_map_write(int r, int rho, sg_map map, sg_dtype dtype, void *grid,
                        sg_value_kind value_kind, uint64_t value_or_seed, void *stream)
 {

@@ -29,6 +29,11 @@ WRITE_HEADLINE = dict(r=16, dtype="u8", value="hash", seed=1,
 # (read-merge-write of whole chunks; the library default).
 WRITE_PRESERVE = dict(map="lambda_unroll", rho=32, order="rowmajor", store="staged")
 
+# The same pass on a grid kept in pinned host memory, read and written in
+# place over the host link (sg_map_write_mapped): staged (read-merge-write)
+# stores, the fastest measured form there.
+WRITE_MAPPED = dict(map="lambda_unroll", rho=64, order="rowmajor", store="staged")
+
 # Stencils at levels 14 and 15: 256 CA steps from Bernoulli(0.3) seeded with
 # 0; 100 diffusion steps (alpha = 0.2) from U[0,1) seeded with 0.
 STENCILS = dict(levels=(14, 15), ca_p=0.3, ca_seed=0, ca_steps=256,

@@ -208,3 +208,17 @@ def test_batch_plan_validation_is_host_side(L):
         assert sg.lib().sg_batch_ca_autotune_fused(n, lv, pa, pb, FAKE + 0x900000, ws, 2, k,
                                                    ctypes.byref(plan), ctypes.byref(sg.LaunchOpts()),
                                                    None) == sg.SG_EINVAL
+
+
+def test_mapped_write_refuses_memory_it_cannot_check(L):
+    # ordinary (unregistered) host memory, a null pointer and the bulk-copy
+    # store paths are refused before any launch
+    import numpy as np
+    buf = np.zeros(1 << 16, dtype=np.uint8)
+    ptr = buf.ctypes.data
+    assert sg.sg_map_write_mapped(8, 16, 0, 0, ptr, 2, 1) == sg.SG_EINVAL
+    assert sg.sg_map_write_mapped(8, 16, 0, 0, 0, 2, 1) == sg.SG_EINVAL
+    for store in ("tma", "fill"):
+        assert sg.sg_map_write_mapped(8, 16, 0, 0, ptr, 2, 1,
+                                      sg.launch_opts(store=store)) == sg.SG_EUNSUPPORTED
+    assert sg.sg_map_write_mapped(17, 16, 0, 0, ptr, 2, 1) == sg.SG_EINVAL

@@ -467,3 +467,33 @@ def test_diffusion_full_size_light_cones(orc, r):
         assert not got[want == 0].any()
         worst = max(worst, max_rel_err(got, want))
     assert worst <= DIFF_TOL, worst
+
+
+# ------------------------------------------------- write pass on host memory
+@pytest.mark.parametrize("dtype", ["u8", "f32"])
+@pytest.mark.parametrize("store", [None, "staged", "scatter"])
+def test_mapped_write_on_pinned_host_memory(orc, dtype, store):
+    # the kernel reads and writes a pinned host grid in place; off-gasket
+    # content is kept, gasket cells get the values of the oracle
+    for r, mapk, rho in ((8, "lambda_unroll", 16), (11, "lambda", 32), (11, "bbox", 64),
+                         (10, "lambda_lut", 4)):
+        n = 1 << r
+        npdt = np.uint8 if dtype == "u8" else np.float32
+        noise = inputs.uniform_grid(r, 77).astype(np.float32) * 200.0
+        noise[orc.member_grid(r) == 0] = 7.0            # off the gasket: arbitrary content
+        init = noise.astype(npdt)
+        host = torch.from_numpy(init.ravel().copy()).pin_memory()
+        elem = 1 if dtype == "u8" else 4
+        if store == "staged" and rho * elem < 16:
+            continue
+        sg.map_write_mapped(host, r, rho, mapk, "hash", 5, store=store)
+        torch.cuda.synchronize()
+        want = init.copy()
+        orc.map_write(r, want, orc.VAL_HASH, 5)
+        got = host.numpy().reshape(n, n)
+        assert np.array_equal(got.view(np.uint8), want.view(np.uint8)), (r, mapk, rho, store)
+
+
+def test_mapped_write_refuses_device_memory():
+    g = torch.zeros(1 << 16, dtype=torch.uint8, device=DEV)
+    assert sg.sg_map_write_mapped(8, 16, 0, 0, g.data_ptr(), 2, 1) == sg.SG_EINVAL
