@@ -144,7 +144,18 @@ class Server:
         self._pb = np.zeros(cnt, dtype=np.uint64)
         self._plan = sg.BatchPlan()
         self.tick = 0
+        self._preload()
         self._warm_up()
+
+    def _preload(self):
+        """Bring gaskets onto the device, in order, while they fit the budget:
+        the resident state a server starts from (the rest load on demand)."""
+        for g in self.gaskets:
+            if self.used + g.device_bytes > self.cfg.budget_bytes:
+                break
+            self._make_resident(g, set())
+        self.loads = 0
+        self.stream.synchronize()
 
     def _warm_up(self):
         """Launch every kernel the loop will use once, on a scratch gasket of

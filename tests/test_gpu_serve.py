@@ -46,7 +46,8 @@ def _serve_and_check(orc, cfg, expect_evictions=False):
     s = summarize(res, cfg)
     assert s["requests"] == len(t)
     if expect_evictions:
-        assert s["evictions"] > 0 and s["loads"] > cfg.gaskets
+        # gaskets go out to host memory and come back (preloading is not counted)
+        assert s["evictions"] > 0 and s["loads"] > 0
     return s
 
 
