@@ -109,10 +109,12 @@ ca_bits_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int r,
 // chunks that hold gasket cells -- a third of a 64-tile's chunks -- are
 // compacted into a list while the tile is staged, and every step runs over
 // that list only, so the threads of a warp all do useful work; the other
-// chunks are 0 in both state buffers throughout.
+// chunks are 0 in both state buffers throughout.  The list is built in
+// row-major chunk order (warp ballots and one scan), so neighbouring threads
+// read neighbouring chunks.
 // ---------------------------------------------------------------------------
-// (4 resident CTAs: the shared-memory limit of the 64-tiles with an 8-row
-// halo; the bound keeps the unrolled chunk loop from taking more registers)
+// (at most 64 registers a thread: the unrolled chunk sweeps would take
+// more; shared memory allows 3-4 resident CTAs of 64-tiles anyway)
 template <int S, int KH, int MAP>
 __global__ void __launch_bounds__(kStencilThreads, 4)
 diffuse_fused_kernel(const float *__restrict__ in, float *__restrict__ out, int r, int order,
@@ -124,8 +126,10 @@ diffuse_fused_kernel(const float *__restrict__ in, float *__restrict__ out, int 
     extern __shared__ __align__(16) unsigned char fused_smem[];
     float *b0 = reinterpret_cast<float *>(fused_smem);
     float *b1 = reinterpret_cast<float *>(fused_smem + F::BUF);
+    constexpr int WARPS = kStencilThreads / 32;
     __shared__ uint2 coord;
     __shared__ uint32_t live_n;
+    __shared__ uint32_t warp_base[PER][WARPS];   // list position of each warp's first live chunk
     __shared__ uint16_t live_chunk[CH];          // staged chunk index (row * PC + column)
     __shared__ uint32_t live_deg[CH];            // its degree word
 
@@ -139,10 +143,7 @@ diffuse_fused_kernel(const float *__restrict__ in, float *__restrict__ out, int 
     for (uint64_t q = blockIdx.x; q < ntiles; q += gridDim.x) {
         if (threadIdx.x < 32) {
             const uint2 c = decode_tile<MAP>(q, ntiles, rb, W, ll);
-            if (threadIdx.x == 0) {
-                coord = c;
-                live_n = 0u;
-            }
+            if (threadIdx.x == 0) coord = c;
         }
         __syncthreads();                 // coord visible; last tile's buffers free
         const uint2 c = coord;
@@ -151,38 +152,51 @@ diffuse_fused_kernel(const float *__restrict__ in, float *__restrict__ out, int 
             continue;
         }
         const int x0 = (int)(c.x << S), y0 = (int)(c.y << S);
-        // stage the live chunks, zero the rest in both buffers, list the live
-        // ones (warp-aggregated appends)
+        const int warp = threadIdx.x >> 5;
+        // stage the live chunks and zero the rest in both buffers; count each
+        // warp's live chunks per sweep j (chunk ch = threadIdx.x + 256 j, so
+        // (j, warp, lane) is row-major chunk order)
+        uint32_t deg[PER], ballot[PER];
 #pragma unroll
         for (int j = 0; j < PER; ++j) {
             const int ch = threadIdx.x + j * kStencilThreads;
-            uint32_t w = kDeadChunk;
-            int row = 0, cc = 0;
+            deg[j] = kDeadChunk;
             if (ch < CH) {
-                row = ch / F::PC;
-                cc = ch - row * F::PC;
-                w = chunk_degrees(x0 - F::HX + 4 * cc, y0 - KH + row, n);
-            }
-            const bool live = w != kDeadChunk;
-            const uint32_t ballot = __ballot_sync(0xFFFFFFFFu, live);
-            uint32_t base = 0;
-            if (lane == 0 && ballot) base = atomicAdd(&live_n, (uint32_t)__popc(ballot));
-            base = __shfl_sync(0xFFFFFFFFu, base, 0);
-            if (ch < CH) {
+                const int row = ch / F::PC, cc = ch - row * F::PC;
+                const int x = x0 - F::HX + 4 * cc, y = y0 - KH + row;
+                deg[j] = chunk_degrees(x, y, n);
                 float *d0 = b0 + row * F::P + 4 * cc;
-                if (live) {
-                    const int x = x0 - F::HX + 4 * cc, y = y0 - KH + row;
+                if (deg[j] != kDeadChunk) {
                     cp_async16(d0, in + (((uint64_t)y << r) + (uint64_t)x));
-                    const uint32_t pos = base + (uint32_t)__popc(ballot & lanes_below);
-                    live_chunk[pos] = (uint16_t)ch;
-                    live_deg[pos] = w;
                 } else {
                     *reinterpret_cast<float4 *>(d0) = make_float4(0.f, 0.f, 0.f, 0.f);
                     *reinterpret_cast<float4 *>(b1 + (d0 - b0)) = make_float4(0.f, 0.f, 0.f, 0.f);
                 }
             }
+            ballot[j] = __ballot_sync(0xFFFFFFFFu, deg[j] != kDeadChunk);
+            if (lane == 0) warp_base[j][warp] = (uint32_t)__popc(ballot[j]);
         }
         cp_async_commit();
+        __syncthreads();
+        if (threadIdx.x == 0) {          // exclusive scan over (j, warp): row-major order
+            uint32_t acc = 0;
+            for (int j = 0; j < PER; ++j)
+                for (int w8 = 0; w8 < WARPS; ++w8) {
+                    const uint32_t cnt = warp_base[j][w8];
+                    warp_base[j][w8] = acc;
+                    acc += cnt;
+                }
+            live_n = acc;
+        }
+        __syncthreads();
+        // the list of live chunks, in row-major order
+#pragma unroll
+        for (int j = 0; j < PER; ++j) {
+            if (deg[j] == kDeadChunk) continue;
+            const uint32_t pos = warp_base[j][warp] + (uint32_t)__popc(ballot[j] & lanes_below);
+            live_chunk[pos] = (uint16_t)(threadIdx.x + j * kStencilThreads);
+            live_deg[pos] = deg[j];
+        }
         cp_async_wait<0>();
         __syncthreads();
         const uint32_t nlive = live_n;
@@ -214,7 +228,7 @@ diffuse_fused_kernel(const float *__restrict__ in, float *__restrict__ out, int 
         }
         fused_store<float, S, KH>((k & 1) ? b1 : b0, out, r, x0, y0);
         // the next iteration's first barrier orders these reads (and those
-        // of live_n and the lists) before the next tile overwrites them
+        // of live_n, warp_base and the lists) before the next tile rewrites them
     }
 }
 
