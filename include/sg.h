@@ -211,8 +211,10 @@ SG_API sg_status sg_diffuse_step_ex(int r, int rho, sg_map map, const float *in,
  * cudaPointerGetAttributes before any launch (other memory: SG_EINVAL).
  * Stores: SG_STORE_AUTO (staged where the tile rows allow it, else scatter),
  * SG_STORE_STAGED or SG_STORE_SCATTER; SG_STORE_TMA and SG_STORE_FILL
- * (bulk tensor copies) are SG_EUNSUPPORTED here.  Otherwise as sg_map_write_ex;
- * the result is in host memory once the stream has completed.
+ * (bulk tensor copies) are SG_EUNSUPPORTED here.  The allocation must hold
+ * the whole n*n grid (its size cannot be queried; a shorter one is the
+ * caller's error, as for a device grid).  Otherwise as sg_map_write_ex; the
+ * result is in host memory once the stream has completed.
  */
 SG_API sg_status sg_map_write_mapped(int r, int rho, sg_map map, sg_dtype dtype,
                                      void *host_grid, sg_value_kind value_kind,
