@@ -73,16 +73,43 @@ def unit_files(unit: str) -> list[str]:
     return sorted(seen)
 
 
+def code_text(src: str) -> str:
+    """C/C++/CUDA source with comments removed and whitespace runs collapsed:
+    what the compiler sees, up to the preprocessor (string and character
+    literals are kept as they are)."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            out.append(" ")
+            i = n if j < 0 else j + 2
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def unit_digest(unit: str) -> str:
-    """Hash of the compile flags and the sources one translation unit is built
-    from: it changes exactly when that unit's kernels may have changed."""
+    """Hash of the compile flags and the code one translation unit is built
+    from (comments and layout excluded): it changes when that unit's kernels
+    may have changed, not when only their documentation did."""
     h = hashlib.sha256()
     # flags without the include directories, whose paths differ by machine
     h.update(" ".join(f for f in NVCC_FLAGS if not os.path.isabs(f)).encode())
     for f in unit_files(unit):
         h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            h.update(code_text(fh.read()).encode())
     return h.hexdigest()
 
 

@@ -1,6 +1,8 @@
 """Host-side pieces of bench.py: the algorithmic-bytes formula (checked by
 brute force over small grids), the clock-sample summary and the row-band cell
 count of the reference arm."""
+import os
+
 import numpy as np
 import pytest
 
@@ -51,3 +53,28 @@ def test_all_cores_oracle_baseline_covers_the_grid():
     out = bench.cpu_baseline_all_cores(dict(r=8, seed=1), band=32)
     assert out["kind"] == "oracle" and out["cores"] >= 1 and out["value"] > 0
     assert "8 bands of 32 rows" in out["sample"]
+
+
+def test_unit_digest_follows_code_not_comments(tmp_path, monkeypatch):
+    from paper_1706_04552_gb300 import build as b
+    assert b.code_text('a; // c\n/* d */ "e//f" \'/\' b') == 'a; "e//f" \'/\' b'
+    files = [os.path.basename(f) for f in b.unit_files("sg_write_u8.cu")]
+    for want in ("sg_write_u8.cu", "sg_write.cuh", "sg_device.cuh", "sg_tma.cuh", "sg.h"):
+        assert want in files
+    # a copy of the sources: a comment edit keeps the digest, a code edit changes it
+    import shutil
+    csrc = tmp_path / "csrc"
+    shutil.copytree(b.CSRC, csrc)
+    monkeypatch.setattr(b, "CSRC", str(csrc))
+    d0 = b.unit_digest("sg_write_u8.cu")
+    p = csrc / "sg_device.cuh"
+    p.write_text(p.read_text() + "\n// a note\n")
+    assert b.unit_digest("sg_write_u8.cu") == d0
+    p.write_text(p.read_text() + "\nconstexpr int kUnused = 1;\n")
+    assert b.unit_digest("sg_write_u8.cu") != d0
+
+
+def test_recorded_traffic_needs_the_current_digest():
+    import bench
+    # the committed record names a kernel; an unknown key or unit gives None
+    assert bench.recorded_traffic("no_such_kernel", "sg_write_u8.cu") is None
