@@ -2,17 +2,22 @@
 // cellular automaton (uint8) and explicit diffusion (float32).
 //
 // The embedded layout keeps (x +- 1, y +- 1) a neighbourhood of the gasket
-// (Section I), so a tile's update needs the tile plus a one-cell halo.  A CTA
-// processes TPC tiles at a time (TPC * tile work ~ 256 threads):
+// (Section I), so a tile's update needs the tile plus a one-cell halo.  For
+// rho >= 16 (CA) / rho >= 4 (diffusion) a CTA processes groups of TPC tiles
+// (TPC * tile chunks ~ 256 threads; stencil_pipeline in sg_stencil.cuh):
 //   1. decode:  one warp per tile runs the lambda(omega) reduction of
 //               Theorem 1 (LambdaLane) or the bounding-box identity map;
-//   2. stage:   the tile's interior is copied to shared memory in 16-byte
-//               chunks, and only chunks holding gasket cells are read from
-//               HBM; the halo is read cell by cell and only at gasket cells
-//               (in a non-empty tile, the gasket structure leaves at most the
-//               right column, the bottom row and five isolated cells);
-//   3. compute: each thread produces one 16-byte chunk of the output tile
-//               from shared memory and stores it if it holds gasket cells.
+//   2. stage:   the tile and a one-chunk halo are copied to shared memory in
+//               16-byte chunks with cp.async, double-buffered (the next
+//               group's copies are in flight while this one is computed);
+//               only chunks holding in-grid gasket cells are read from HBM,
+//               the others are zero-filled;
+//   3. compute: each thread produces 16-byte chunks of the output tile from
+//               shared memory and stores them by whole 32-byte sectors where
+//               the sector holds gasket cells.
+// Smaller tiles take one cell per thread and read the halo cell by cell (in
+// a non-empty tile the gasket leaves at most the right column, the bottom
+// row and five isolated cells of it).
 // Off-gasket cells are 0 in every state (precondition of the ABI), so a
 // neighbour sum over the plain neighbourhood only ever sees gasket cells.
 //

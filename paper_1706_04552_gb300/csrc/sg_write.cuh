@@ -2,7 +2,7 @@
 // gasket cell of a level-r grid receives v(x, y), nothing else changes.
 //
 // Persistent kernels serve the four maps.  A "team" (one warp, or the whole
-// 256-thread CTA for big tiles) owns one tile at a time and walks its share
+// CTA for big tiles) owns one tile at a time and walks its share
 // of the tile list with a fixed stride:
 //   lambda (all three intra-tile variants): the team decodes its tile with
 //     the warp-parallel lambda(omega) of Theorem 1 (LambdaLane), walking the
@@ -18,7 +18,7 @@
 //   further unrolling: slot e is mapped by lambda applied at thread level
 //     (Section III-D, Further Unrolling).
 //
-// Two ways to store:
+// Four ways to store:
 //   scatter: each thread stores its cells directly.  Only gasket bytes may
 //     change, so stores are per cell and the L2 merges them into partially
 //     written 32-byte sectors, which it must fill from DRAM before writing
@@ -38,6 +38,10 @@
 //     for a read-modify-write).  Chunks of one sector are handled together
 //     whenever the sector lies inside one tile, so the L2 sees whole-sector
 //     writes and needs no fill.
+//   fill: write-only; the tile is built in shared memory (0 at every
+//     off-gasket cell, v at the gasket cells) and leaves with one bulk tensor
+//     store.  Equal to the others whenever the grid is 0 off the gasket (the
+//     paper's zero matrix and the stencils' invariant), and reads nothing.
 #pragma once
 
 #include "sg_device.cuh"
