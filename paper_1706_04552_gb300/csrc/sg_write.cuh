@@ -1,5 +1,7 @@
 // sg_write.cuh -- the map-and-write pass (Section IV of the paper): every
-// gasket cell of a level-r grid receives v(x, y), nothing else changes.
+// gasket cell of a level-r grid receives v(x, y); nothing else changes,
+// except under fill stores (below), which write 0 to the off-gasket cells
+// of the tiles they touch.
 //
 // Persistent kernels serve the four maps.  A "team" (one warp, or the whole
 // CTA for big tiles) owns one tile at a time and walks its share
