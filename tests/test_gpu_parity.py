@@ -497,3 +497,27 @@ def test_mapped_write_on_pinned_host_memory(orc, dtype, store):
 def test_mapped_write_refuses_device_memory():
     g = torch.zeros(1 << 16, dtype=torch.uint8, device=DEV)
     assert sg.sg_map_write_mapped(8, 16, 0, 0, g.data_ptr(), 2, 1) == sg.SG_EINVAL
+
+
+@pytest.mark.slow
+def test_mapped_write_level16_sampled(orc):
+    # the end-to-end configuration of the benchmark: the level-16 grid in
+    # pinned host memory, written in place, sampled against the oracle; and
+    # the whole grid against the device pass, byte for byte
+    from paper_1706_04552_gb300 import workloads
+    m = workloads.WRITE_MAPPED
+    r, n = 16, 1 << 16
+    host = torch.zeros(n * n, dtype=torch.uint8).pin_memory()
+    sg.map_write_mapped(host, r, m["rho"], m["map"], "hash", 1, order=m["order"],
+                        store=m["store"])
+    torch.cuda.synchronize()
+    xs, ys = _sample_cells(r, 100_000, 9)
+    got = host.numpy()[ys * n + xs]
+    want = orc.write_expected_at(r, np.uint8, orc.VAL_HASH, 1, xs, ys,
+                                 np.zeros(len(xs), dtype=np.uint8))
+    assert np.array_equal(got, want)
+    g = torch.zeros(n * n, dtype=torch.uint8, device=DEV)
+    sg.map_write(g, r, 64, "lambda_unroll", "hash", 1, order="interleaved", store="fill")
+    for y0 in range(0, n, 8192):
+        band = slice(y0 * n, (y0 + 8192) * n)
+        assert torch.equal(g[band].cpu(), host[band]), y0
