@@ -136,7 +136,8 @@ enum : int { kValConst = 0, kValLinear31 = 1, kValHash = 2 };
 // z = s + gamma; z = (z ^ (z >> 30)) * M1; z = (z ^ (z >> 27)) * M2;
 // output z ^ (z >> 31).
 //
-// The high 32 bits of the output for state seedmix ^ key, key below 2^32.  The
+// splitmix64_hi_state: the high 32 bits of the output for the state
+// seedmix ^ key, key below 2^32, given as its halves (s_lo, s_hi).  The
 // written values use only bits 40..63 of the output (u8: h >> 56; f32:
 // h >> 40), and the finaliser's last step h = z ^ (z >> 31) leaves bits
 // 33..63 of z unchanged, so h >> 32 agrees with z >> 32 in every bit used
@@ -144,19 +145,23 @@ enum : int { kValConst = 0, kValLinear31 = 1, kValHash = 2 };
 // arithmetic written on 32-bit halves: the state's high half is the
 // constant high half of seedmix, each 64-bit shift is one funnel shift per
 // half, and the second product needs only its high half.
-__device__ __forceinline__ uint32_t splitmix64_hi(uint64_t seedmix, uint32_t key)
+__device__ __forceinline__ uint32_t splitmix64_hi_state(uint32_t s_lo, uint32_t s_hi)
 {
     constexpr uint32_t G_LO = (uint32_t)kGoldenGamma, G_HI = (uint32_t)(kGoldenGamma >> 32);
     constexpr uint64_t M1 = 0xBF58476D1CE4E5B9ull, M2 = 0x94D049BB133111EBull;
     constexpr uint32_t M1_LO = (uint32_t)M1, M1_HI = (uint32_t)(M1 >> 32);
     constexpr uint32_t M2_LO = (uint32_t)M2, M2_HI = (uint32_t)(M2 >> 32);
-    const uint32_t s_lo = (uint32_t)seedmix ^ key, s_hi = (uint32_t)(seedmix >> 32);
-    // z = s + gamma
+    // z = s + gamma: the high half is one of two values (carry or not), and
+    // so is the high half after the first xor-shift; both pairs depend only
+    // on the seed and are computed once per thread
+    const uint32_t zh0 = s_hi + G_HI, zh1 = zh0 + 1u;
+    const uint32_t th0 = zh0 ^ (zh0 >> 30), th1 = zh1 ^ (zh1 >> 30);
     const uint32_t z_lo = s_lo + G_LO;
-    const uint32_t z_hi = s_hi + G_HI + (z_lo < s_lo ? 1u : 0u);
+    const bool carry = z_lo < s_lo;
+    const uint32_t z_hi = carry ? zh1 : zh0;
     // z ^= z >> 30
     const uint32_t t_lo = z_lo ^ __funnelshift_r(z_lo, z_hi, 30);
-    const uint32_t t_hi = z_hi ^ (z_hi >> 30);
+    const uint32_t t_hi = carry ? th1 : th0;
     // z *= M1 (mod 2^64)
     const uint64_t p = (uint64_t)t_lo * M1_LO;
     const uint32_t y_lo = (uint32_t)p;
@@ -171,9 +176,12 @@ __device__ __forceinline__ uint32_t splitmix64_hi(uint64_t seedmix, uint32_t key
 // Value of the cell whose linear index (row-major, pitch n = 2^r) is
 // base + koff, for r <= 16 (so the index, which is also the hash key y*n + x,
 // fits in 32 bits).  The write kernels split the index into a per-tile base
-// and a per-thread offset that is the same for every tile, so each cell
-// costs one add before the hash.  For the linear value the split is the
-// same with x*31 + y in place of the index.
+// ((y0 << r) | x0, x0 and y0 multiples of rho) and a per-thread offset that
+// is the same for every tile ((ty << r) | tx, tx and ty below rho).  Their
+// bits are disjoint, so base + koff = base ^ koff, and the hash state
+// seedmix ^ key is (seedmix ^ base) ^ koff: one xor per cell after a per-tile
+// xor.  For the linear value the split is the same with x*31 + y in place of
+// the index (an add there: those bits overlap).
 template <typename T, int VK> struct CellValue {
     uint64_t seedmix;      // seed * gamma
     uint32_t cval;         // the constant's bits
@@ -194,7 +202,10 @@ template <typename T, int VK> struct CellValue {
         } else if constexpr (VK == kValLinear31) {
             return (T)((base + koff) & 0xFFu);
         } else {
-            const uint32_t hi = splitmix64_hi(seedmix, base + koff);   // bits 32..63
+            // bits 32..63 of the hash; (seedmix ^ base) is the same for the
+            // whole tile, so it is computed once per tile
+            const uint32_t hi = splitmix64_hi_state(((uint32_t)seedmix ^ base) ^ koff,
+                                                    (uint32_t)(seedmix >> 32));
             if constexpr (sizeof(T) == 1) return (T)(hi >> 24);
             else return (float)(hi >> 8) * (1.0f / 16777216.0f);
         }

@@ -469,6 +469,16 @@ write_tma_kernel(const __grid_constant__ CUtensorMap tmap, int r, int order, uin
 }
 
 
+// One element into shared memory at a shared-window address.
+__device__ __forceinline__ void st_shared(uint32_t addr, uint8_t v)
+{
+    asm volatile("st.shared.u8 [%0], %1;" ::"r"(addr), "r"((uint32_t)v));
+}
+__device__ __forceinline__ void st_shared(uint32_t addr, float v)
+{
+    asm volatile("st.shared.f32 [%0], %1;" ::"r"(addr), "f"(v));
+}
+
 // ---------------------------------------------------------------------------
 // Fill stores (write-only): the tile is built in shared memory -- 0 at every
 // off-gasket cell, v(x, y) at every gasket cell -- and written back whole
@@ -511,13 +521,18 @@ write_fill_kernel(const __grid_constant__ CUtensorMap tmap, int r, int order, ui
     // per-thread, tile-independent parts of each cell: value-key offset and
     // shared-memory offset (slots off the gasket are dropped: for a tile that
     // holds gasket cells, (x & y) == 0 iff (tx & ty) == 0)
-    uint32_t koff[ITERS], soff[ITERS];
+    // The shared-memory address is that of the cell in slot 0 (~0u for a
+    // slot that is no gasket cell); slot k is k * BUF bytes further, a
+    // constant in the sweep over the slots below, which is unrolled, so a
+    // cell's store needs no address arithmetic.
+    const uint32_t buf_s = (uint32_t)__cvta_generic_to_shared(buf);
+    uint32_t koff[ITERS], cell[ITERS];
 #pragma unroll
     for (int j = 0; j < ITERS; ++j) {
         const uint32_t tx = off[j] & (RHO - 1), ty = (off[j] >> 8) & (RHO - 1);
         const bool keep = off[j] != ~0u && (!TS::SUBBOX || (tx & ty) == 0u);
         koff[j] = CellValue<T, VK>::offset_of(tx, ty, r);
-        soff[j] = keep ? ty * RHO + tx : ~0u;
+        cell[j] = keep ? buf_s + (ty * RHO + tx) * (uint32_t)sizeof(T) : ~0u;
     }
     const CellValue<T, VK> cv{seedmix, (uint32_t)vs};
     TileWalker<MAP> tw;
@@ -529,25 +544,34 @@ write_fill_kernel(const __grid_constant__ CUtensorMap tmap, int r, int order, ui
     // k+1-ST, which is the last tile that used slot (k+1) % ST -- the slot
     // iteration k+1 writes after that barrier.  (Tiles number below 2^32:
     // fill needs rho * sizeof(T) >= 16, so r - s <= 12.)
-    int slot = 0;
-    for (uint32_t q = (uint32_t)team; q < (uint32_t)ntiles; q += (uint32_t)nteams) {
-        const uint2 b = tw.next(q);                  // every warp of the team decodes
-        const bool empty = MAP == kMapBBox && (b.x & b.y) != 0u;
-        const uint32_t x0 = b.x << S, y0 = b.y << S;
-        uint8_t *tile = buf + slot * TS::BUF;
-        slot = slot + 1 == ST ? 0 : slot + 1;
-        if (!empty) {
-            const uint32_t base = CellValue<T, VK>::base_of(x0, y0, r);
+    const uint32_t nt = (uint32_t)ntiles, stride = (uint32_t)nteams;
+    uint32_t q = (uint32_t)team;
+    while (q < nt) {
 #pragma unroll
-            for (int j = 0; j < ITERS; ++j)
-                if (soff[j] != ~0u) reinterpret_cast<T *>(tile)[soff[j]] = cv(base, koff[j]);
-            fence_proxy_async_shared();
-        }
-        team_sync<TEAM>();
-        if (t == 0) {
-            if (!empty) tma_store_2d(&tmap, (int)x0, (int)y0, tile);
-            bulk_commit();                 // one group per tile (empty for an empty tile)
-            bulk_wait_read<ST - 2>();
+        for (int sl = 0; sl < ST; ++sl) {
+            if (q >= nt) break;
+            const uint2 b = tw.next(q);              // every warp of the team decodes
+            const bool empty = MAP == kMapBBox && (b.x & b.y) != 0u;
+            const uint32_t x0 = b.x << S, y0 = b.y << S;
+            if (!empty) {
+                const uint32_t base = CellValue<T, VK>::base_of(x0, y0, r);
+#pragma unroll
+                for (int j = 0; j < ITERS; ++j) {
+                    // the member lists (lookup table, unrolling) fill every
+                    // thread's first slots: only the last one may be empty
+                    const bool full = !TS::SUBBOX && (j + 1) * TEAM <= TS::NSLOT;
+                    if (full || cell[j] != ~0u)
+                        st_shared(cell[j] + (uint32_t)(sl * TS::BUF), cv(base, koff[j]));
+                }
+                fence_proxy_async_shared();
+            }
+            team_sync<TEAM>();
+            if (t == 0) {
+                if (!empty) tma_store_2d(&tmap, (int)x0, (int)y0, buf + sl * TS::BUF);
+                bulk_commit();             // one group per tile (empty for an empty tile)
+                bulk_wait_read<ST - 2>();
+            }
+            q += stride;
         }
     }
     if (t == 0) bulk_wait_all();

@@ -322,13 +322,17 @@ def _splitmix64_hi(seedmix, key):
     key = key.astype(np.uint64)
     s_lo = (u(seedmix) & m) ^ key
     s_hi = u(seedmix) >> u(32)
+    zh0 = (s_hi + u(g >> 32)) & m             # the two values of the high half
+    zh1 = (zh0 + u(1)) & m
+    th0, th1 = zh0 ^ (zh0 >> u(30)), zh1 ^ (zh1 >> u(30))
     z_lo = (s_lo + u(g & 0xFFFFFFFF)) & m
-    z_hi = (s_hi + u(g >> 32) + (z_lo < s_lo).astype(np.uint64)) & m
+    carry = z_lo < s_lo
+    z_hi = np.where(carry, zh1, zh0)
 
     def fshr(lo, hi, n):                      # __funnelshift_r(lo, hi, n)
         return ((lo >> u(n)) | (hi << u(32 - n))) & m
     t_lo = z_lo ^ fshr(z_lo, z_hi, 30)
-    t_hi = z_hi ^ (z_hi >> u(30))
+    t_hi = np.where(carry, th1, th0)
     p = t_lo * u(m1 & 0xFFFFFFFF)             # < 2^64: exact in uint64
     y_lo = p & m
     y_hi = ((p >> u(32)) + ((t_lo * u(m1 >> 32)) & m) + ((t_hi * u(m1 & 0xFFFFFFFF)) & m)) & m
@@ -351,3 +355,20 @@ def test_hash_high_word_matches_splitmix64(seed):
     hi = _splitmix64_hi(seedmix, keys)
     assert np.array_equal(hi >> np.uint64(24), h >> np.uint64(56))   # u8 values
     assert np.array_equal(hi >> np.uint64(8), h >> np.uint64(40))    # f32 values
+
+
+@pytest.mark.parametrize("r,S", [(6, 4), (10, 5), (16, 6), (16, 4)])
+def test_tile_base_and_offset_bits_are_disjoint(r, S):
+    # key = base + koff with base = (y0 << r) | x0 and koff = (ty << r) | tx:
+    # the kernels xor the two instead of adding them
+    rng = np.random.default_rng(r * 10 + S)
+    nb = 1 << (r - S)
+    bx = rng.integers(0, nb, 5000, dtype=np.uint64)
+    by = rng.integers(0, nb, 5000, dtype=np.uint64)
+    tx = rng.integers(0, 1 << S, 5000, dtype=np.uint64)
+    ty = rng.integers(0, 1 << S, 5000, dtype=np.uint64)
+    rs, ss = np.uint64(r), np.uint64(S)
+    base = ((by << ss) << rs) | (bx << ss)
+    koff = (ty << rs) | tx
+    assert np.array_equal(base + koff, base ^ koff)
+    assert np.all(base + koff < np.uint64(1 << (2 * r)))
