@@ -15,8 +15,8 @@
 // registers:
 //   sub-box (lambda, bounding box): every slot of the rho x rho tile, each
 //     tested with (x & y) == 0 (Section III-D, Bounding Sub-boxes);
-//   lookup table: the 3^s member slots in row-major order, built once per
-//     CTA in shared memory (Section III-D, Shared Lookup Table);
+//   lookup table: the 3^s member slots in row-major order (Section III-D,
+//     Shared Lookup Table); each thread computes its own entries once;
 //   further unrolling: slot e is mapped by lambda applied at thread level
 //     (Section III-D, Further Unrolling).
 //
@@ -75,20 +75,33 @@ template <typename T, int S, bool STAGED> struct WriteTeam {
                                        : (S >= 5 ? kWriteThreads : 32);
 };
 
-// Row-major rank of member slot (tx, ty) among the 3^S members of a level-S
-// tile: all members of earlier rows, then the members of row ty left of tx.
-// Row t holds 2^(S - popcount(t)) members (the subsets of ~t); inside a row
-// the members, ordered by tx, are the bits of tx at the zero positions of ty.
+// Member slot e (0 <= e < 3^S) of a level-S tile in row-major order, the
+// order of the paper's lookup table.  Row t holds 2^(S - popcount(t))
+// members (the subsets of ~t), so of the rows that share the bits of t above
+// bit b, those with bit b clear hold twice as many members as those with it
+// set: 2 m 3^b against m 3^b, m = 2^(zero bits above b).  Walking the bits
+// from the top picks the row of member e in S steps; e's rank inside the row
+// then gives tx, its bits placed at the zero positions of ty.  Returns
+// tx | ty << 8.
 template <int S>
-__device__ __forceinline__ int member_rank(int tx, int ty)
+__device__ __forceinline__ uint32_t member_rowmajor(int e)
 {
-    int rank = 0;
-    for (int t = 0; t < ty; ++t) rank += 1 << (S - __popc(t));
-    int k = 0, bit = 0;
+    int ty = 0, m = 1;
+#pragma unroll
+    for (int b = S - 1; b >= 0; --b) {
+        const int clear = 2 * m * pow3i(b);     // members in the rows with bit b clear
+        if (e < clear) {
+            m *= 2;
+        } else {
+            e -= clear;
+            ty |= 1 << b;
+        }
+    }
+    int tx = 0, k = 0;
 #pragma unroll
     for (int b = 0; b < S; ++b)
-        if (!((ty >> b) & 1)) { k |= ((tx >> b) & 1) << bit; ++bit; }
-    return rank + k;
+        if (!((ty >> b) & 1)) { tx |= ((e >> k) & 1) << b; ++k; }
+    return (uint32_t)tx | ((uint32_t)ty << 8);
 }
 
 // Slot e of a level-S tile under further unrolling: lambda of Theorem 1 at
@@ -113,22 +126,18 @@ __device__ __forceinline__ uint32_t unrolled_offset(int e)
 }
 
 // This thread's tile-independent offsets (tx | ty << 8, or ~0u): slots of the
-// sub-box, or member slots from the lookup table or the unrolled map.
-template <int S, int MAP, int TEAM, int ITERS, int CTA_THREADS = kWriteThreads>
-__device__ __forceinline__ void intra_tile_offsets(uint32_t (&off)[ITERS], int t_in_team,
-                                                   uint16_t *lut)
+// sub-box, or member slots from the lookup table or the unrolled map.  A
+// thread computes the table entries it visits itself, once, and keeps them in
+// registers for every tile, instead of reading a table built in shared memory.
+template <int S, int MAP, int TEAM, int ITERS>
+__device__ __forceinline__ void intra_tile_offsets(uint32_t (&off)[ITERS], int t_in_team)
 {
     constexpr int RHO = 1 << S, SLOTS = RHO * RHO, MEMBERS = pow3i(S);
     if constexpr (MAP == kMapLut) {
-        for (int slot = threadIdx.x; slot < SLOTS; slot += CTA_THREADS) {
-            const int tx = slot & (RHO - 1), ty = slot >> S;
-            if ((tx & ty) == 0) lut[member_rank<S>(tx, ty)] = (uint16_t)(tx | (ty << 8));
-        }
-        __syncthreads();
 #pragma unroll
         for (int j = 0; j < ITERS; ++j) {
             const int e = t_in_team + j * TEAM;
-            off[j] = (e < MEMBERS) ? (uint32_t)lut[e] : ~0u;
+            off[j] = (e < MEMBERS) ? member_rowmajor<S>(e) : ~0u;
         }
     } else if constexpr (MAP == kMapUnroll) {
 #pragma unroll
@@ -187,7 +196,6 @@ write_scatter_kernel(T *__restrict__ grid, int r, int order, uint64_t vs, uint64
     constexpr int NSLOT = SUBBOX ? WS::SLOTS : WS::MEMBERS;
     constexpr int ITERS = (NSLOT + TEAM - 1) / TEAM;
     constexpr int TEAMS_PER_CTA = kWriteThreads / TEAM;
-    __shared__ uint16_t lut[MAP == kMapLut ? WS::MEMBERS : 1];
 
     const int t_in_team = threadIdx.x % TEAM;
     const uint64_t team = (uint64_t)blockIdx.x * TEAMS_PER_CTA + threadIdx.x / TEAM;
@@ -195,7 +203,7 @@ write_scatter_kernel(T *__restrict__ grid, int r, int order, uint64_t vs, uint64
     const uint64_t seedmix = vs * kGoldenGamma;
 
     uint32_t off[ITERS];
-    intra_tile_offsets<S, MAP, TEAM, ITERS>(off, t_in_team, lut);
+    intra_tile_offsets<S, MAP, TEAM, ITERS>(off, t_in_team);
     // tile-independent parts of each cell: grid offset (ty << r | tx, masked
     // to the tile so every address stays inside it) and value-key offset;
     // slots off the gasket are dropped (in a tile holding gasket cells,
@@ -281,7 +289,6 @@ write_staged_kernel(T *__restrict__ grid, int r, int order, uint64_t vs, uint64_
     constexpr int ITERS = (NSLOT + TEAM - 1) / TEAM;
     constexpr int CPT = (WS::CHUNKS + TEAM - 1) / TEAM;      // chunks per thread
     constexpr int TEAMS_PER_CTA = kWriteThreads / TEAM;
-    __shared__ uint16_t lut[MAP == kMapLut ? WS::MEMBERS : 1];
     __shared__ __align__(16) T tile[TEAMS_PER_CTA][WS::SLOTS];
 
     const int t_in_team = threadIdx.x % TEAM;
@@ -292,7 +299,7 @@ write_staged_kernel(T *__restrict__ grid, int r, int order, uint64_t vs, uint64_
     T *my = tile[team_in_cta];
 
     uint32_t off[ITERS];
-    intra_tile_offsets<S, MAP, TEAM, ITERS>(off, t_in_team, lut);
+    intra_tile_offsets<S, MAP, TEAM, ITERS>(off, t_in_team);
     uint32_t koff[ITERS], soff[ITERS];
 #pragma unroll
     for (int j = 0; j < ITERS; ++j) {
@@ -376,7 +383,6 @@ write_tma_kernel(const __grid_constant__ CUtensorMap tmap, int r, int order, uin
     __shared__ __align__(8) uint64_t full[TEAMS][ST];
     __shared__ uint2 coord[TEAMS][ST];
     __shared__ int abort_team[TEAMS];
-    __shared__ uint16_t lut[MAP == kMapLut ? pow3i(S) : 1];
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int tm = tid / TEAM, t = tid % TEAM;
@@ -389,7 +395,7 @@ write_tma_kernel(const __grid_constant__ CUtensorMap tmap, int r, int order, uin
     uint8_t *buf = dsm + (size_t)tm * ST * TS::BUF;
 
     uint32_t off[ITERS];
-    intra_tile_offsets<S, MAP, TEAM, ITERS, kTmaThreads>(off, t, lut);
+    intra_tile_offsets<S, MAP, TEAM, ITERS>(off, t);
     uint32_t koff[ITERS], soff[ITERS];
 #pragma unroll
     for (int j = 0; j < ITERS; ++j) {
@@ -498,7 +504,6 @@ write_fill_kernel(const __grid_constant__ CUtensorMap tmap, int r, int order, ui
     constexpr int ITERS = TS::ITERS;
     static_assert(ST >= 2, "the slot ring needs two slots");
     extern __shared__ uint8_t dsm_raw[];
-    __shared__ uint16_t lut[MAP == kMapLut ? pow3i(S) : 1];
 
     const int tid = threadIdx.x, lane = tid & 31;
     const int tm = tid / TEAM, t = tid % TEAM;
@@ -516,8 +521,8 @@ write_fill_kernel(const __grid_constant__ CUtensorMap tmap, int r, int order, ui
         reinterpret_cast<uint4 *>(dsm)[i] = make_uint4(0u, 0u, 0u, 0u);
     fence_proxy_async_shared();        // the zeros are read by other teams' bulk stores too
     uint32_t off[ITERS];
-    intra_tile_offsets<S, MAP, TEAM, ITERS, kTmaThreads>(off, t, lut);   // syncs the CTA
-    if constexpr (MAP != kMapLut) __syncthreads();
+    intra_tile_offsets<S, MAP, TEAM, ITERS>(off, t);
+    __syncthreads();                   // every slot zeroed before any team stores
     // per-thread, tile-independent parts of each cell: value-key offset and
     // shared-memory offset (slots off the gasket are dropped: for a tile that
     // holds gasket cells, (x & y) == 0 iff (tx & ty) == 0)

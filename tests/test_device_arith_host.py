@@ -108,14 +108,23 @@ def test_incremental_walk_of_the_launch_index(stride):
                 q += stride
 
 
-def _member_rank(S, tx, ty):
-    rank = sum(1 << (S - bin(t).count("1")) for t in range(ty))
-    k = bit = 0
-    for bpos in range(S):
-        if not (ty >> bpos) & 1:
-            k |= ((tx >> bpos) & 1) << bit
-            bit += 1
-    return rank + k
+def _member_rowmajor(S, e):
+    """member_rowmajor<S>(e): row by the halves' member counts, then tx by
+    placing e's bits at the zero bits of ty."""
+    ty, m = 0, 1
+    for b in range(S - 1, -1, -1):
+        clear = 2 * m * 3 ** b
+        if e < clear:
+            m *= 2
+        else:
+            e -= clear
+            ty |= 1 << b
+    tx = k = 0
+    for b in range(S):
+        if not (ty >> b) & 1:
+            tx |= ((e >> k) & 1) << b
+            k += 1
+    return tx, ty
 
 
 def _unrolled(S, e):
@@ -134,16 +143,11 @@ def _unrolled(S, e):
 
 
 @pytest.mark.parametrize("S", range(0, 7))
-def test_lookup_table_rank_and_unrolled_slots(S):
+def test_lookup_table_entries_and_unrolled_slots(S):
     R = 1 << S
-    ranks = {}
-    for ty in range(R):
-        for tx in range(R):
-            if tx & ty == 0:
-                ranks[_member_rank(S, tx, ty)] = (ty, tx)
-    # every member gets a distinct rank in 0 .. 3^S - 1, in row-major order
-    assert sorted(ranks) == list(range(3 ** S))
-    assert [ranks[i] for i in range(3 ** S)] == sorted(ranks.values())
+    # the table entries, in row-major order: every member exactly once
+    members = [(tx, ty) for ty in range(R) for tx in range(R) if tx & ty == 0]
+    assert [_member_rowmajor(S, e) for e in range(3 ** S)] == members
     cells = {_unrolled(S, e) for e in range(3 ** S)}
     assert len(cells) == 3 ** S
     assert all(x & y == 0 and 0 <= x < R and 0 <= y < R for x, y in cells)
