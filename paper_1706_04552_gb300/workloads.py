@@ -23,7 +23,7 @@ WRITE_SWEEP = dict(levels=tuple(range(8, 17)), rhos=(8, 16, 32, 64),
 # the bounding box gets its own best rho and the same store path.
 WRITE_HEADLINE = dict(r=16, dtype="u8", value="hash", seed=1,
                       map="lambda_unroll", rho=64, order="interleaved", store="fill",
-                      bbox_rho=64, f32_rho=16)
+                      bbox_rho=64, f32_rho=32)
 
 # The same pass with stores that keep arbitrary off-gasket content
 # (read-merge-write of whole chunks; the library default).
