@@ -235,28 +235,6 @@ diffuse_fused_kernel(const float *__restrict__ in, float *__restrict__ out, int 
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
-// Grid of a fused kernel.  Its dynamic shared memory plus its static arrays
-// can pass the default 48 KB per CTA, so the dynamic limit is raised to the
-// size used, once per device (bit d of `attr_devs`).
-template <typename K>
-static cudaError_t fused_grid(K kern, int smem, uint64_t ntiles, const LaunchCfg &cfg,
-                              unsigned *grid, std::atomic<int> *occ,
-                              std::atomic<uint64_t> *attr_devs)
-{
-    {
-        int dev = 0;
-        cudaError_t e = cudaGetDevice(&dev);
-        if (e != cudaSuccess) return e;
-        const uint64_t bit = 1ull << (dev & 63);
-        if ((attr_devs->load(std::memory_order_acquire) & bit) == 0) {
-            e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            if (e != cudaSuccess) return e;
-            attr_devs->fetch_or(bit, std::memory_order_acq_rel);
-        }
-    }
-    return persistent_grid(kern, kStencilThreads, (size_t)smem, ntiles, cfg, grid, occ);
-}
-
 template <int S, int KH, int MAP>
 cudaError_t launch_ca_fused_t(int r, const uint8_t *in, uint8_t *out, int k, cudaStream_t st,
                               const LaunchCfg &cfg)
@@ -285,7 +263,7 @@ cudaError_t launch_diffuse_fused_t(int r, const float *in, float *out, float alp
     static std::atomic<uint64_t> attr{0};
     auto kern = diffuse_fused_kernel<S, KH, MAP>;
     unsigned grid = 1;
-    cudaError_t e = fused_grid(kern, 2 * F::BUF, ntiles, cfg, &grid, &occ, &attr);
+    cudaError_t e = dyn_smem_grid(kern, 2 * F::BUF, ntiles, cfg, &grid, &occ, &attr);
     if (e != cudaSuccess) return e;
     kern<<<grid, kStencilThreads, 2 * F::BUF, st>>>(in, out, r, cfg.order, ntiles, k, alpha);
     return cudaGetLastError();

@@ -2,9 +2,11 @@
 // cellular automaton (uint8) and explicit diffusion (float32).
 //
 // The embedded layout keeps (x +- 1, y +- 1) a neighbourhood of the gasket
-// (Section I), so a tile's update needs the tile plus a one-cell halo.  For
-// rho >= 16 (CA) / rho >= 4 (diffusion) a CTA processes groups of TPC tiles
-// (TPC * tile chunks ~ 256 threads; stencil_pipeline in sg_stencil.cuh):
+// (Section I), so a tile's update needs the tile plus a one-cell halo.  The
+// CA at rho = 32, 64 and diffusion at rho = 16, 32 run one warp per tile
+// (below).  For the other vector sizes -- CA rho = 16, diffusion rho = 4,
+// 8, 64 -- a CTA processes groups of TPC tiles (TPC * tile chunks ~ 256
+// threads; stencil_pipeline in sg_stencil.cuh):
 //   1. decode:  one warp per tile runs the lambda(omega) reduction of
 //               Theorem 1 (LambdaLane) or the bounding-box identity map;
 //   2. stage:   the tile and a one-chunk halo are copied to shared memory in
@@ -56,6 +58,85 @@ ca_vec_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int r,
         ca_compute_group<S>(buf, slot);
     };
     stencil_pipeline<uint8_t, S>(sm, tiles, groups, decode, compute);
+}
+
+// ---------------------------------------------------------------------------
+// One warp per tile (CA for rho = 32, 64; diffusion for rho = 16, 32).  Each
+// warp stages its own tile and halo (cp.async, chunks without in-grid gasket
+// cells zero-filled), waits for its own copies, and computes the tile: no
+// CTA barrier anywhere, so a warp that waits for memory holds up no other
+// warp, and eight resident warps per CTA keep the SM busy.  Measured faster
+// than the CTA-wide pipeline at these sizes; larger float tiles do not fit
+// eight warps' shared memory, and at rho = 16 a byte tile gives a warp too
+// little work.
+// ---------------------------------------------------------------------------
+constexpr int kWarpTileWarps = kStencilThreads / 32;
+
+template <typename T, int S>
+__device__ __forceinline__ void warp_stage(T *sm, const T *__restrict__ in, int r, int x0, int y0,
+                                           int lane)
+{
+    using G = StencilGroup<T, S>;
+    const int n = 1 << r;
+    for (int i = lane; i < G::STAGED; i += 32) {
+        const int row = i / G::PC, cc = i - row * G::PC;
+        const int x = x0 + (cc - 1) * G::CE, y = y0 + row - 1;
+        T *dst = sm + row * G::P + cc * G::CE;
+        const bool fill = x >= 0 && y >= 0 && x < n && y < n && (x & y) == 0;
+        if (fill) cp_async16(dst, in + (((uint64_t)y << r) + (uint64_t)x));
+        else *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncwarp();
+}
+
+template <int S, int MAP>
+__global__ void __launch_bounds__(kStencilThreads)
+ca_warp_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int r, int order,
+               uint64_t ntiles)
+{
+    using G = StencilGroup<uint8_t, S>;
+    extern __shared__ __align__(16) unsigned char warp_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t *sm = warp_smem + warp * G::TILE;
+    const int rb = r - S;
+    LambdaLane ll;
+    ll.init(lane, rb, order);
+    const uint32_t W = pi_word(order, rb);
+    const uint64_t stride = (uint64_t)gridDim.x * kWarpTileWarps;
+    for (uint64_t q = (uint64_t)blockIdx.x * kWarpTileWarps + warp; q < ntiles; q += stride) {
+        const uint2 c = decode_tile<MAP>(q, ntiles, rb, W, ll);     // warp-collective
+        if (c.x == kNoTile) continue;                                // uniform in the warp
+        warp_stage<uint8_t, S>(sm, in, r, (int)(c.x << S), (int)(c.y << S), lane);
+        const StencilTile<uint8_t> tl{c.x, c.y, r, in, out};
+        for (int k = lane; k < G::CHUNKS; k += 32) ca_chunk<S>(sm, tl, 0, k);
+        __syncwarp();                    // the tile is read before the next staging
+    }
+}
+
+template <int S, int MAP>
+__global__ void __launch_bounds__(kStencilThreads)
+diffuse_warp_kernel(const float *__restrict__ in, float *__restrict__ out, int r, int order,
+                    uint64_t ntiles, float alpha)
+{
+    using G = StencilGroup<float, S>;
+    extern __shared__ __align__(16) unsigned char warp_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float *sm = reinterpret_cast<float *>(warp_smem) + warp * G::TILE;
+    const int rb = r - S;
+    LambdaLane ll;
+    ll.init(lane, rb, order);
+    const uint32_t W = pi_word(order, rb);
+    const uint64_t stride = (uint64_t)gridDim.x * kWarpTileWarps;
+    for (uint64_t q = (uint64_t)blockIdx.x * kWarpTileWarps + warp; q < ntiles; q += stride) {
+        const uint2 c = decode_tile<MAP>(q, ntiles, rb, W, ll);     // warp-collective
+        if (c.x == kNoTile) continue;                                // uniform in the warp
+        warp_stage<float, S>(sm, in, r, (int)(c.x << S), (int)(c.y << S), lane);
+        const StencilTile<float> tl{c.x, c.y, r, in, out};
+        for (int k = lane; k < G::CHUNKS; k += 32) diffuse_chunk<S>(sm, tl, 0, k, alpha);
+        __syncwarp();                    // the tile is read before the next staging
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -223,7 +304,16 @@ cudaError_t launch_ca_t(int r, const uint8_t *in, uint8_t *out, cudaStream_t st,
     const uint64_t groups = (ntiles + TPC - 1) / TPC;
     unsigned grid = 1;
     cudaError_t e;
-    if constexpr (S >= 4) {
+    if constexpr (S >= 5) {
+        static std::atomic<int> occ{0};
+        static std::atomic<uint64_t> attr{0};
+        auto k = ca_warp_kernel<S, MAP>;
+        constexpr int smem = kWarpTileWarps * StencilGroup<uint8_t, (S >= 4 ? S : 4)>::TILE;
+        e = dyn_smem_grid(k, smem, (ntiles + kWarpTileWarps - 1) / kWarpTileWarps, cfg, &grid,
+                          &occ, &attr);
+        if (e != cudaSuccess) return e;
+        k<<<grid, kStencilThreads, smem, st>>>(in, out, r, cfg.order, ntiles);
+    } else if constexpr (S == 4) {
         static std::atomic<int> occ{0};
         auto k = ca_vec_kernel<S, MAP>;
         e = persistent_grid(k, kStencilThreads, 0, groups, cfg, &grid, &occ);
@@ -250,7 +340,17 @@ cudaError_t launch_diffuse_t(int r, const float *in, float *out, float alpha,
     const uint64_t groups = (ntiles + TPC - 1) / TPC;
     unsigned grid = 1;
     cudaError_t e;
-    if constexpr (S >= 2) {
+    if constexpr (S == 4 || S == 5) {
+        static std::atomic<int> occ{0};
+        static std::atomic<uint64_t> attr{0};
+        auto k = diffuse_warp_kernel<S, MAP>;
+        constexpr int smem = kWarpTileWarps * StencilGroup<float, (S >= 2 ? S : 2)>::TILE *
+                             (int)sizeof(float);
+        e = dyn_smem_grid(k, smem, (ntiles + kWarpTileWarps - 1) / kWarpTileWarps, cfg, &grid,
+                          &occ, &attr);
+        if (e != cudaSuccess) return e;
+        k<<<grid, kStencilThreads, smem, st>>>(in, out, r, cfg.order, ntiles, alpha);
+    } else if constexpr (S >= 2) {
         static std::atomic<int> occ{0};
         auto k = diffuse_vec_kernel<S, MAP>;
         e = persistent_grid(k, kStencilThreads, 0, groups, cfg, &grid, &occ);

@@ -183,18 +183,16 @@ __device__ __forceinline__ void stage_group_async(T *sm, const StencilTile<T> *t
     }
 }
 
-// The CA's next state for every interior chunk of the group's tiles.
+// The CA's next state of interior chunk k of staged tile t (buffer sm).
 template <int S>
-__device__ __forceinline__ void ca_compute_group(const uint8_t *sm,
-                                                 const StencilTile<uint8_t> *tiles)
+__device__ __forceinline__ void ca_chunk(const uint8_t *sm, const StencilTile<uint8_t> &tl, int t,
+                                         int k)
 {
     using G = StencilGroup<uint8_t, S>;
-    for (int c = threadIdx.x; c < G::TPC * G::CHUNKS; c += kStencilThreads) {
-        const int t = c / G::CHUNKS, k = c % G::CHUNKS, ty = k / G::CPR, cx = k % G::CPR;
-        const StencilTile<uint8_t> tl = tiles[t];
-        if (tl.bx == kNoTile) continue;
+    {
+        const int ty = k / G::CPR, cx = k % G::CPR;
         const uint32_t x = (tl.bx << S) + 16u * cx, y = (tl.by << S) + ty;
-        if (!in_gasket(x & G::GROUP_MASK, y)) continue;   // sector holds no gasket cell
+        if (!in_gasket(x & G::GROUP_MASK, y)) return;     // sector holds no gasket cell
         const uint8_t *up = sm + t * G::TILE + ty * G::P + 16 + 16 * cx;
         const uint8_t *mid = up + G::P, *dn = mid + G::P;
         const uint4 cu = *reinterpret_cast<const uint4 *>(up);
@@ -213,6 +211,19 @@ __device__ __forceinline__ void ca_compute_group(const uint8_t *sm,
         o.z = life_rule(cnt.z, cm.z, m.z);
         o.w = life_rule(cnt.w, cm.w, m.w);
         *reinterpret_cast<uint4 *>(tl.out + ((uint64_t)y << tl.r) + x) = o;
+    }
+}
+
+// The CA's next state for every interior chunk of the group's tiles.
+template <int S>
+__device__ __forceinline__ void ca_compute_group(const uint8_t *sm,
+                                                 const StencilTile<uint8_t> *tiles)
+{
+    using G = StencilGroup<uint8_t, S>;
+    for (int c = threadIdx.x; c < G::TPC * G::CHUNKS; c += kStencilThreads) {
+        const int t = c / G::CHUNKS, k = c % G::CHUNKS;
+        if (tiles[t].bx == kNoTile) continue;
+        ca_chunk<S>(sm, tiles[t], t, k);
     }
 }
 
@@ -279,17 +290,14 @@ __device__ __forceinline__ float degree_cell(uint32_t word, int i, float u, floa
 }
 
 template <int S>
-__device__ __forceinline__ void diffuse_compute_group(const float *sm,
-                                                      const StencilTile<float> *tiles,
-                                                      float alpha)
+__device__ __forceinline__ void diffuse_chunk(const float *sm, const StencilTile<float> &tl, int t,
+                                              int k, float alpha)
 {
     using G = StencilGroup<float, S>;
-    for (int c = threadIdx.x; c < G::TPC * G::CHUNKS; c += kStencilThreads) {
-        const int t = c / G::CHUNKS, k = c % G::CHUNKS, ty = k / G::CPR, cx = k % G::CPR;
-        const StencilTile<float> tl = tiles[t];
-        if (tl.bx == kNoTile) continue;
+    {
+        const int ty = k / G::CPR, cx = k % G::CPR;
         const uint32_t x = (tl.bx << S) + 4u * cx, y = (tl.by << S) + ty;
-        if (!in_gasket(x & G::GROUP_MASK, y)) continue;   // sector holds no gasket cell
+        if (!in_gasket(x & G::GROUP_MASK, y)) return;     // sector holds no gasket cell
         const uint32_t w = chunk_degrees((int)x, (int)y, 1 << tl.r);
         float4 o = make_float4(0.f, 0.f, 0.f, 0.f);
         if (w != kDeadChunk) {
@@ -304,6 +312,19 @@ __device__ __forceinline__ void diffuse_compute_group(const float *sm,
             o.w = degree_cell(w, 3, cm.w, cm.z, rr, cu.w, cd.w, alpha);
         }
         *reinterpret_cast<float4 *>(tl.out + ((uint64_t)y << tl.r) + x) = o;
+    }
+}
+
+template <int S>
+__device__ __forceinline__ void diffuse_compute_group(const float *sm,
+                                                      const StencilTile<float> *tiles,
+                                                      float alpha)
+{
+    using G = StencilGroup<float, S>;
+    for (int c = threadIdx.x; c < G::TPC * G::CHUNKS; c += kStencilThreads) {
+        const int t = c / G::CHUNKS, k = c % G::CHUNKS;
+        if (tiles[t].bx == kNoTile) continue;
+        diffuse_chunk<S>(sm, tiles[t], t, k, alpha);
     }
 }
 
@@ -338,6 +359,27 @@ __device__ __forceinline__ void stencil_pipeline(T *sm, StencilTile<T> *tiles, u
         cb = nb;
     }
     cp_async_wait<0>();
+}
+
+// Persistent grid of a kernel that takes `smem` bytes of dynamic shared
+// memory.  With its static arrays that can pass the default 48 KB per CTA,
+// so the dynamic limit is raised to the size used, once per device (bit d
+// of `attr_devs`).
+template <typename K>
+inline cudaError_t dyn_smem_grid(K kern, int smem, uint64_t units, const LaunchCfg &cfg,
+                                 unsigned *grid, std::atomic<int> *occ,
+                                 std::atomic<uint64_t> *attr_devs)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const uint64_t bit = 1ull << (dev & 63);
+    if ((attr_devs->load(std::memory_order_acquire) & bit) == 0) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr_devs->fetch_or(bit, std::memory_order_acq_rel);
+    }
+    return persistent_grid(kern, kStencilThreads, (size_t)smem, units, cfg, grid, occ);
 }
 
 }  // namespace sg
