@@ -119,18 +119,60 @@ ca_batch_kernel(BatchView bv, uint32_t total, int parity, int order)
     stencil_pipeline<uint8_t, S>(sm, tiles, groups, decode, compute);
 }
 
+// One step with one warp per work item (rho = 32, 64): the item's tile is
+// staged and computed by the warp alone, as in the single-gasket kernel.
+template <int S>
+__global__ void __launch_bounds__(kStencilThreads)
+ca_batch_warp_kernel(BatchView bv, uint32_t total, int parity, int order)
+{
+    using G = StencilGroup<uint8_t, S>;
+    extern __shared__ __align__(16) unsigned char warp_smem[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint8_t *sm = warp_smem + warp * G::TILE;
+    LambdaLane ll;
+    ll.init(lane, 0, order);
+    const uint64_t stride = (uint64_t)gridDim.x * kWarpTileWarps;
+    for (uint64_t q = (uint64_t)blockIdx.x * kWarpTileWarps + warp; q < total; q += stride) {
+        const uint32_t i = batch_instance(bv.prefix, bv.count, (uint32_t)q);   // warp-uniform
+        const int r = __ldg(bv.level + i), rb = r - S;
+        const uint32_t local = (uint32_t)q - __ldg(bv.prefix + i);
+        ll.set_level(lane, rb);
+        const uint32_t W = pi_word(order, rb);
+        const uint32_t b = local / W, a = local - b * W;
+        const uint2 c = ll.decode(a, b);
+        const uint64_t pa = __ldg(bv.buf_a + i), pb = __ldg(bv.buf_b + i);
+        const uint8_t *in = reinterpret_cast<const uint8_t *>(parity ? pb : pa);
+        uint8_t *out = reinterpret_cast<uint8_t *>(parity ? pa : pb);
+        warp_stage<uint8_t, S>(sm, in, r, (int)(c.x << S), (int)(c.y << S), lane);
+        const StencilTile<uint8_t> tl{c.x, c.y, r, in, out};
+        for (int k = lane; k < G::CHUNKS; k += 32) ca_chunk<S>(sm, tl, 0, k);
+        __syncwarp();                    // the tile is read before the next staging
+    }
+}
+
 template <int S>
 cudaError_t launch_batch_t(const sg_batch_plan *p, int parity, cudaStream_t st,
                            const LaunchCfg &cfg)
 {
     static std::atomic<int> occ{0};
-    constexpr int TPC = StencilGroup<uint8_t, S>::TPC;
     unsigned grid = 1;
-    const uint64_t groups = (p->total_tiles + TPC - 1) / TPC;
-    auto k = ca_batch_kernel<S>;
-    cudaError_t e = persistent_grid(k, kStencilThreads, 0, groups, cfg, &grid, &occ);
-    if (e != cudaSuccess) return e;
-    k<<<grid, kStencilThreads, 0, st>>>(view_of(p), p->total_tiles, parity, cfg.order);
+    cudaError_t e;
+    if constexpr (S >= 5) {
+        static std::atomic<uint64_t> attr{0};
+        auto k = ca_batch_warp_kernel<S>;
+        constexpr int smem = kWarpTileWarps * StencilGroup<uint8_t, S>::TILE;
+        e = dyn_smem_grid(k, smem, ((uint64_t)p->total_tiles + kWarpTileWarps - 1) / kWarpTileWarps,
+                          cfg, &grid, &occ, &attr);
+        if (e != cudaSuccess) return e;
+        k<<<grid, kStencilThreads, smem, st>>>(view_of(p), p->total_tiles, parity, cfg.order);
+    } else {
+        constexpr int TPC = StencilGroup<uint8_t, S>::TPC;
+        const uint64_t groups = (p->total_tiles + TPC - 1) / TPC;
+        auto k = ca_batch_kernel<S>;
+        e = persistent_grid(k, kStencilThreads, 0, groups, cfg, &grid, &occ);
+        if (e != cudaSuccess) return e;
+        k<<<grid, kStencilThreads, 0, st>>>(view_of(p), p->total_tiles, parity, cfg.order);
+    }
     return cudaGetLastError();
 }
 

@@ -70,27 +70,6 @@ ca_vec_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int r,
 // eight warps' shared memory, and at rho = 16 a byte tile gives a warp too
 // little work.
 // ---------------------------------------------------------------------------
-constexpr int kWarpTileWarps = kStencilThreads / 32;
-
-template <typename T, int S>
-__device__ __forceinline__ void warp_stage(T *sm, const T *__restrict__ in, int r, int x0, int y0,
-                                           int lane)
-{
-    using G = StencilGroup<T, S>;
-    const int n = 1 << r;
-    for (int i = lane; i < G::STAGED; i += 32) {
-        const int row = i / G::PC, cc = i - row * G::PC;
-        const int x = x0 + (cc - 1) * G::CE, y = y0 + row - 1;
-        T *dst = sm + row * G::P + cc * G::CE;
-        const bool fill = x >= 0 && y >= 0 && x < n && y < n && (x & y) == 0;
-        if (fill) cp_async16(dst, in + (((uint64_t)y << r) + (uint64_t)x));
-        else *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
-    }
-    cp_async_commit();
-    cp_async_wait<0>();
-    __syncwarp();
-}
-
 template <int S, int MAP>
 __global__ void __launch_bounds__(kStencilThreads)
 ca_warp_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int r, int order,

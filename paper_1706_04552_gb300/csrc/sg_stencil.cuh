@@ -361,6 +361,30 @@ __device__ __forceinline__ void stencil_pipeline(T *sm, StencilTile<T> *tiles, u
     cp_async_wait<0>();
 }
 
+// One warp stages one tile and its one-chunk halo into sm (cp.async, chunks
+// without in-grid gasket cells zero-filled) and waits for its own copies:
+// the warp-per-tile stencils need no CTA barrier.
+constexpr int kWarpTileWarps = kStencilThreads / 32;
+
+template <typename T, int S>
+__device__ __forceinline__ void warp_stage(T *sm, const T *__restrict__ in, int r, int x0, int y0,
+                                           int lane)
+{
+    using G = StencilGroup<T, S>;
+    const int n = 1 << r;
+    for (int i = lane; i < G::STAGED; i += 32) {
+        const int row = i / G::PC, cc = i - row * G::PC;
+        const int x = x0 + (cc - 1) * G::CE, y = y0 + row - 1;
+        T *dst = sm + row * G::P + cc * G::CE;
+        const bool fill = x >= 0 && y >= 0 && x < n && y < n && (x & y) == 0;
+        if (fill) cp_async16(dst, in + (((uint64_t)y << r) + (uint64_t)x));
+        else *reinterpret_cast<uint4 *>(dst) = make_uint4(0u, 0u, 0u, 0u);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncwarp();
+}
+
 // Persistent grid of a kernel that takes `smem` bytes of dynamic shared
 // memory.  With its static arrays that can pass the default 48 KB per CTA,
 // so the dynamic limit is raised to the size used, once per device (bit d
