@@ -356,9 +356,13 @@ def run_ours(args, grp: Group):
     del grid
     torch.cuda.empty_cache()
     copy = measure_e2e(sg, torch, dev, stream, w, grp, min(args.steps, 4))
-    mapped = measure_e2e_mapped(sg, torch, dev, stream, w, grp, 20)
+    mapped = measure_e2e_mapped(sg, torch, dev, stream, w, grp, 20, "staged")
+    mapped_fill = measure_e2e_mapped(sg, torch, dev, stream, w, grp, 20, "fill")
+    # the headline end-to-end path reads the grid's inputs and writes the
+    # result over the link, correct for any grid content; the fill path (the
+    # grid 0 off the gasket, as here) reads nothing and is reported beside it
     out["e2e"] = dict(mapped if mapped["value"] >= copy["value"] else copy)
-    out["e2e_paths"] = {"mapped": mapped, "copy": copy}
+    out["e2e_paths"] = {"mapped": mapped, "mapped_fill": mapped_fill, "copy": copy}
     if grp.rank == 0 and grp.world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(w)
         try:
@@ -773,7 +777,7 @@ def fused_stencils(sg, torch, dev, stream, r, single):
     return out
 
 
-def measure_e2e_mapped(sg, torch, dev, stream, w, grp, steps):
+def measure_e2e_mapped(sg, torch, dev, stream, w, grp, steps, store="staged"):
     """The same metric through the public API with the grid kept in pinned
     host memory and written in place (sg_map_write_mapped): the kernel reads
     and writes the touched chunks of the host grid over the host link
@@ -786,7 +790,7 @@ def measure_e2e_mapped(sg, torch, dev, stream, w, grp, steps):
 
     def step():
         sg.map_write_mapped(host, r, m["rho"], m["map"], w["value"], w["seed"], stream,
-                            order=m["order"], store=m["store"])
+                            order=m["order"], store=store)
 
     step()
     torch.cuda.synchronize(dev)
@@ -795,13 +799,16 @@ def measure_e2e_mapped(sg, torch, dev, stream, w, grp, steps):
     ms = grp.max(ms)
     del host
     sector = touched_bytes(r, 1, 32)
+    reads = sector if store == "staged" else 0
+    how = ("the touched 32-byte sectors read and written back" if store == "staged" else
+           "the touched 32-byte sectors written whole, nothing read (the grid is 0 off "
+           "the gasket)")
     return {"value": round(grp.world * 3 ** r * steps / (ms / 1e3) / 1e9, 4), "unit": UNIT,
-            "h2d_bytes_per_step": sector, "d2h_bytes_per_step": sector,
+            "h2d_bytes_per_step": reads, "d2h_bytes_per_step": sector,
             "steps": steps, "ms_per_step": round(ms / steps, 3),
             "path": (f"grid in pinned host memory, written in place by the kernel over the "
-                     f"host link ({m['map']}, rho {m['rho']}, {m['order']}, {m['store']} "
-                     f"stores); bytes per step = the touched 32-byte sectors read and "
-                     f"written back")}
+                     f"host link ({m['map']}, rho {m['rho']}, {m['order']}, {store} "
+                     f"stores); bytes per step = {how}")}
 
 
 def measure_e2e(sg, torch, dev, stream, w, grp, steps):

@@ -210,8 +210,11 @@ SG_API sg_status sg_diffuse_step_ex(int r, int rho, sg_map map, const float *in,
  * staging copy of the whole grid is made.  The pointer is checked with
  * cudaPointerGetAttributes before any launch (other memory: SG_EINVAL).
  * Stores: SG_STORE_AUTO (staged where the tile rows allow it, else scatter),
- * SG_STORE_STAGED or SG_STORE_SCATTER; SG_STORE_TMA and SG_STORE_FILL
- * (bulk tensor copies) are SG_EUNSUPPORTED here.  The allocation must hold
+ * SG_STORE_STAGED, SG_STORE_SCATTER, or SG_STORE_FILL: here the 32-byte
+ * sectors that hold gasket cells are written whole with plain stores (0 at
+ * their off-gasket cells) and nothing is read, so only the writes cross the
+ * link -- equal to the others on a grid that is 0 off the gasket.
+ * SG_STORE_TMA (bulk tensor copies) is SG_EUNSUPPORTED here.  The allocation must hold
  * the whole n*n grid (its size cannot be queried; a shorter one is the
  * caller's error, as for a device grid).  Otherwise as sg_map_write_ex; the
  * result is in host memory once the stream has completed.

@@ -212,8 +212,11 @@ sg_status sg_map_write_mapped(int r, int rho, sg_map map, sg_dtype dtype, void *
     LaunchCfg cfg;
     if (!read_launch_opts(opts, &cfg)) return SG_EINVAL;
     const int elem = dtype == SG_U8 ? 1 : 4;
-    // only the paths that move data with plain loads and stores
-    if (cfg.store == SG_STORE_TMA || cfg.store == SG_STORE_FILL) return SG_EUNSUPPORTED;
+    // only the paths that move data with plain loads and stores: fill runs
+    // as write-only whole chunks of the staged kernel (no bulk tensor copy)
+    if (cfg.store == SG_STORE_TMA) return SG_EUNSUPPORTED;
+    if ((cfg.store == SG_STORE_STAGED || cfg.store == SG_STORE_FILL) && rho * elem < 16)
+        return SG_EUNSUPPORTED;                       // whole chunks need 16-byte tile rows
     // the pointer must be page-locked host memory mapped into the device's
     // address space; anything else is refused before a launch
     cudaPointerAttributes attr;
@@ -230,7 +233,9 @@ sg_status sg_map_write_mapped(int r, int rho, sg_map map, sg_dtype dtype, void *
     void *grid = attr.devicePointer;
     if (!aligned(grid, (uintptr_t)elem)) return SG_EINVAL;
     const bool can_stage = rho * elem >= 16 && aligned(grid, 16);
-    if (cfg.store == SG_STORE_STAGED && !can_stage) return SG_EUNSUPPORTED;
+    if ((cfg.store == SG_STORE_STAGED || cfg.store == SG_STORE_FILL) && !can_stage)
+        return SG_EUNSUPPORTED;
+    if (cfg.store == SG_STORE_FILL) cfg.store = kStoreFillPlain;
     if (cfg.store == SG_STORE_AUTO) cfg.store = can_stage ? kStoreStaged : kStoreScatter;
     if (dtype == SG_U8)
         return finish(launch_write_u8(r, s, (int)map, (int)value_kind, (uint8_t *)grid,

@@ -278,7 +278,8 @@ __device__ __forceinline__ void team_sync()
 
 template <typename T, int VK, int S, int MAP>
 __global__ void __launch_bounds__(kWriteThreads)
-write_staged_kernel(T *__restrict__ grid, int r, int order, uint64_t vs, uint64_t ntiles)
+write_staged_kernel(T *__restrict__ grid, int r, int order, uint64_t vs, uint64_t ntiles,
+                    int read)
 {
     using WS = WriteShape<T, S>;
     static_assert(WS::STAGE_OK, "staged stores need tile rows of at least 16 bytes");
@@ -327,8 +328,11 @@ write_staged_kernel(T *__restrict__ grid, int r, int order, uint64_t vs, uint64_
             const uint32_t xc = x0 + (uint32_t)(cx * WS::CHUNK_ELEMS), y = y0 + (uint32_t)row;
             const uint32_t xg = xc & ~(uint32_t)(WS::GROUP_ELEMS - 1);   // its sector group
             act[k] = (c < WS::CHUNKS) && in_gasket(xg, y);
-            old[k] = act[k] ? *reinterpret_cast<const uint4 *>(grid + ((uint64_t)y << r) + xc)
-                            : make_uint4(0u, 0u, 0u, 0u);
+            // read == 0: the fill contract, nothing read (off-gasket cells of
+            // the chunks written become 0)
+            old[k] = act[k] && read
+                         ? *reinterpret_cast<const uint4 *>(grid + ((uint64_t)y << r) + xc)
+                         : make_uint4(0u, 0u, 0u, 0u);
         }
         // 2. new values into the shared copy of the tile
         team_sync<TEAM>();        // the previous tile's merge has read `my`
@@ -651,7 +655,8 @@ cudaError_t launch_write_t(int r, T *grid, uint64_t vs, cudaStream_t st, const L
     if (cfg.store == kStoreFill) return launch_write_fill<T, VK, S, MAP>(r, grid, vs, ntiles, st, cfg);
     using WS = WriteShape<T, S>;
     bool staged = false;     // the caller resolved kStoreAuto already
-    if constexpr (WS::STAGE_OK) staged = (cfg.store == kStoreStaged);
+    if constexpr (WS::STAGE_OK)
+        staged = (cfg.store == kStoreStaged || cfg.store == kStoreFillPlain);
     unsigned grid_ctas = 1;
     cudaError_t e;
     if constexpr (WS::STAGE_OK) {
@@ -662,11 +667,12 @@ cudaError_t launch_write_t(int r, T *grid, uint64_t vs, cudaStream_t st, const L
             const uint64_t units = (ntiles * TEAM + kWriteThreads - 1) / kWriteThreads;
             e = persistent_grid(kern, kWriteThreads, 0, units, cfg, &grid_ctas, &occ);
             if (e != cudaSuccess) return e;
-            kern<<<grid_ctas, kWriteThreads, 0, st>>>(grid, r, cfg.order, vs, ntiles);
+            kern<<<grid_ctas, kWriteThreads, 0, st>>>(grid, r, cfg.order, vs, ntiles,
+                                                      cfg.store == kStoreStaged ? 1 : 0);
             return cudaGetLastError();
         }
     }
-    if (cfg.store == kStoreStaged) return cudaErrorNotSupported;
+    if (cfg.store == kStoreStaged || cfg.store == kStoreFillPlain) return cudaErrorNotSupported;
     constexpr int TEAM = WriteTeam<T, S, false>::TEAM;
     static std::atomic<int> occ{0};
     auto kern = write_scatter_kernel<T, VK, S, MAP>;

@@ -30,8 +30,8 @@ WRITE_HEADLINE = dict(r=16, dtype="u8", value="hash", seed=1,
 WRITE_PRESERVE = dict(map="lambda_unroll", rho=32, order="rowmajor", store="staged")
 
 # The same pass on a grid kept in pinned host memory, read and written in
-# place over the host link (sg_map_write_mapped): staged (read-merge-write)
-# stores, the fastest measured form there.
+# place over the host link (sg_map_write_mapped), with staged
+# (read-merge-write) stores or write-only fill stores.
 WRITE_MAPPED = dict(map="lambda_unroll", rho=64, order="rowmajor", store="staged")
 
 # Stencils at levels 14 and 15: 256 CA steps from Bernoulli(0.3) seeded with

@@ -218,7 +218,10 @@ def test_mapped_write_refuses_memory_it_cannot_check(L):
     ptr = buf.ctypes.data
     assert sg.sg_map_write_mapped(8, 16, 0, 0, ptr, 2, 1) == sg.SG_EINVAL
     assert sg.sg_map_write_mapped(8, 16, 0, 0, 0, 2, 1) == sg.SG_EINVAL
-    for store in ("tma", "fill"):
-        assert sg.sg_map_write_mapped(8, 16, 0, 0, ptr, 2, 1,
-                                      sg.launch_opts(store=store)) == sg.SG_EUNSUPPORTED
+    assert sg.sg_map_write_mapped(8, 16, 0, 0, ptr, 2, 1,
+                                  sg.launch_opts(store="tma")) == sg.SG_EUNSUPPORTED
+    assert sg.sg_map_write_mapped(8, 16, 0, 0, ptr, 2, 1,
+                                  sg.launch_opts(store="fill")) == sg.SG_EINVAL
+    assert sg.sg_map_write_mapped(8, 8, 0, 0, ptr, 2, 1,           # 8-byte tile rows
+                                  sg.launch_opts(store="fill")) == sg.SG_EUNSUPPORTED
     assert sg.sg_map_write_mapped(17, 16, 0, 0, ptr, 2, 1) == sg.SG_EINVAL

@@ -494,6 +494,40 @@ def test_mapped_write_on_pinned_host_memory(orc, dtype, store):
         assert np.array_equal(got.view(np.uint8), want.view(np.uint8)), (r, mapk, rho, store)
 
 
+@pytest.mark.parametrize("dtype", ["u8", "f32"])
+def test_mapped_fill_writes_whole_groups_and_reads_nothing(orc, dtype):
+    # fill on a host grid: gasket cells get v, the other cells of every
+    # written group (a 32-byte sector, or a 16-byte chunk for 16-byte tile
+    # rows) become 0, everything else keeps its content; on a grid that is 0
+    # off the gasket that is exactly the oracle's pass
+    npdt = np.uint8 if dtype == "u8" else np.float32
+    elem = np.dtype(npdt).itemsize
+    for r, mapk, rho in ((9, "lambda_unroll", 16), (11, "lambda_unroll", 64),
+                         (11, "bbox", 32), (10, "lambda", 16)):
+        if rho * elem < 16:
+            continue
+        n = 1 << r
+        noise = (inputs.uniform_grid(r, 31).astype(np.float32) * 200.0 + 3.0).astype(npdt)
+        ys, xs = np.mgrid[0:n, 0:n]
+        noise[(xs & ys) != 0] = npdt(9)
+        host = torch.from_numpy(noise.ravel().copy()).pin_memory()
+        sg.map_write_mapped(host, r, rho, mapk, "hash", 6, store="fill")
+        torch.cuda.synchronize()
+        want = noise.copy()
+        orc.map_write(r, want, orc.VAL_HASH, 6)
+        ge = (32 if rho * elem >= 32 else 16) // elem
+        written = (((xs & ~(ge - 1)) & ys) == 0) & ((xs & ys) != 0)
+        want[written] = 0
+        got = host.numpy().reshape(n, n)
+        assert np.array_equal(got.view(np.uint8), want.view(np.uint8)), (r, mapk, rho)
+        zero = torch.zeros(n * n, dtype=host.dtype).pin_memory()
+        sg.map_write_mapped(zero, r, rho, mapk, "hash", 6, store="fill")
+        torch.cuda.synchronize()
+        ref = np.zeros((n, n), dtype=npdt)
+        orc.map_write(r, ref, orc.VAL_HASH, 6)
+        assert np.array_equal(zero.numpy().reshape(n, n).view(np.uint8), ref.view(np.uint8))
+
+
 def test_mapped_write_refuses_device_memory():
     g = torch.zeros(1 << 16, dtype=torch.uint8, device=DEV)
     assert sg.sg_map_write_mapped(8, 16, 0, 0, g.data_ptr(), 2, 1) == sg.SG_EINVAL
