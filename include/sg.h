@@ -393,12 +393,30 @@ SG_API sg_status sg_batch_ca_step_noalloc(int count, const int *levels, uint8_t 
 
 /*
  * sg_device_status -- report and clear the device status word of the current
- * device.  Kernels with bounded waits (SG_STORE_TMA) record a wait that gave
- * up there instead of spinning; the call synchronises `stream` and returns
- * SG_ETIMEOUT if any kernel recorded one since the last call, else SG_OK
- * (or SG_ECUDA if the status could not be read).
+ * device.  Kernels with bounded waits (SG_STORE_TMA, sg_wait_selftest) record
+ * a wait that gave up there instead of spinning; the call synchronises
+ * `stream` and returns SG_ETIMEOUT if any kernel recorded one since the last
+ * call, else SG_OK (or SG_ECUDA if the status could not be read).
  */
 SG_API sg_status sg_device_status(void *stream);
+
+/*
+ * sg_wait_selftest -- exercise, without any fault, the bounded device-side
+ * wait that the SG_STORE_TMA kernels use (failure detection; no operation of
+ * the paper).  Launches `blocks` blocks of 128 threads on `stream`
+ * (asynchronous).  Each block initialises a shared-memory mbarrier that
+ * expects one arrival, and all its threads wait on it, bounded by `limit_ns`
+ * nanoseconds of %globaltimer time and by a poll count.
+ *   - arrive != 0: one thread arrives, the wait completes, nothing is recorded.
+ *   - arrive == 0: nothing ever arrives; every wait gives up after about
+ *     limit_ns, the kernel records SG_ETIMEOUT in the device status word
+ *     (read and cleared by sg_device_status) and returns normally.  The CUDA
+ *     context stays usable.
+ * Errors: SG_EINVAL for `blocks` outside [1, 1024] or `limit_ns` outside
+ * [1000, 2000000000] (2 s is the limit of the product kernels' waits);
+ * SG_ECUDA if the launch failed.
+ */
+SG_API sg_status sg_wait_selftest(int blocks, int arrive, uint64_t limit_ns, void *stream);
 
 /* Human-readable name of a status code (static storage). */
 SG_API const char *sg_status_str(sg_status status);

@@ -26,7 +26,7 @@ __all__ = [
     "sg_map_write_ex", "sg_ca_step_ex", "sg_diffuse_step_ex", "LaunchOpts", "launch_opts",
     "sg_ca_steps", "sg_diffuse_steps", "FUSE_MAX",
     "sg_launch_stats", "sg_status_str", "sg_abi_version", "sg_device_status",
-    "device_status",
+    "device_status", "sg_wait_selftest", "wait_selftest",
     "CABatch", "Graph", "BatchPlan",
     "map_write", "map_write_host", "map_write_mapped", "sg_map_write_mapped", "ca_step",
     "diffuse_step", "ca_steps", "diffuse_steps",
@@ -152,6 +152,8 @@ def lib() -> ctypes.CDLL:
         L.sg_batch_ca_autotune_fused.restype = i32
         L.sg_device_status.argtypes = [vp]
         L.sg_device_status.restype = i32
+        L.sg_wait_selftest.argtypes = [i32, i32, u64, vp]
+        L.sg_wait_selftest.restype = i32
         L.sg_abi_version.argtypes = []
         L.sg_abi_version.restype = i32
         _lib = L
@@ -179,6 +181,20 @@ def device_status(stream=None):
     h = torch.cuda.current_stream().cuda_stream if stream is None else (
         stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
     _check("sg_device_status", sg_device_status(h))
+
+
+def sg_wait_selftest(blocks, arrive, limit_ns, stream=0) -> int:
+    return int(lib().sg_wait_selftest(blocks, 1 if arrive else 0, limit_ns, stream))
+
+
+def wait_selftest(blocks=152, arrive=False, limit_ns=50_000_000, stream=None):
+    """Launch the bounded-wait self-test: every block waits on an mbarrier
+    that nothing arrives on (unless `arrive`), gives up after `limit_ns` and
+    records SG_ETIMEOUT for device_status() to report."""
+    import torch
+    h = torch.cuda.current_stream().cuda_stream if stream is None else (
+        stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+    _check("sg_wait_selftest", sg_wait_selftest(blocks, arrive, limit_ns, h))
 
 
 def _check(fn: str, status: int) -> None:

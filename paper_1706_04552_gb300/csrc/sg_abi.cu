@@ -344,6 +344,13 @@ sg_status sg_device_status(void *stream)
     return status == kDevOk ? SG_OK : SG_ETIMEOUT;
 }
 
+sg_status sg_wait_selftest(int blocks, int arrive, uint64_t limit_ns, void *stream)
+{
+    if (blocks < 1 || blocks > 1024) return SG_EINVAL;
+    if (limit_ns < 1000 || limit_ns > kWaitLimitNs) return SG_EINVAL;
+    return finish(launch_wait_selftest(blocks, arrive != 0, limit_ns, (cudaStream_t)stream));
+}
+
 sg_status sg_launch_stats(int r, int rho, sg_map map, uint64_t *launched, uint64_t *useful)
 {
     int s = 0;

@@ -66,6 +66,31 @@ cudaError_t device_status_ptr(int **ptr)
     return cudaSuccess;
 }
 
+namespace {
+// Every block waits on an mbarrier of its own that expects one arrival.  With
+// `arrive` thread 0 makes it, so the phase completes; without it nothing ever
+// arrives, each wait gives up after limit_ns and the block records kDevTimeout.
+__global__ void __launch_bounds__(128) wait_selftest_kernel(int *status, int arrive,
+                                                            uint64_t limit_ns)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (arrive && threadIdx.x == 0) mbar_arrive(&bar);
+    if (!mbar_wait_bounded(&bar, 0, limit_ns)) record_device_error(status, kDevTimeout);
+    __syncthreads();
+}
+}  // namespace
+
+cudaError_t launch_wait_selftest(int blocks, int arrive, uint64_t limit_ns, cudaStream_t st)
+{
+    int *status = nullptr;
+    cudaError_t e = device_status_ptr(&status);
+    if (e != cudaSuccess) return e;
+    wait_selftest_kernel<<<blocks, 128, 0, st>>>(status, arrive, limit_ns);
+    return cudaGetLastError();
+}
+
 cudaError_t read_device_status(int *status, cudaStream_t st)
 {
     int zero = 0;

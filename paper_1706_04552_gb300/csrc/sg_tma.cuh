@@ -75,16 +75,23 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
     return done != 0;
 }
 
-// Wait for phase `parity` of `bar` to complete; false after kWaitLimitNs.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity)
+// Wait for phase `parity` of `bar` to complete; false after `limit_ns`.
+// Two bounds: the wall clock, and a count of polls that cannot finish in
+// less than about half the limit (a poll takes at least one issue cycle,
+// under 1 ns at the maximum SM clock), so the loop ends even if the timer
+// were to stall.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity,
+                                                  uint64_t limit_ns = kWaitLimitNs)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = global_timer_ns();
-    for (;;) {
+    const uint64_t max_rounds = limit_ns / 32 + 1;   // 64 polls a round
+    for (uint64_t round = 0; round < max_rounds; ++round) {
         for (int i = 0; i < 64; ++i)
             if (mbar_try_wait(bar, parity)) return true;
-        if (global_timer_ns() - t0 > kWaitLimitNs) return false;
+        if (global_timer_ns() - t0 > limit_ns) return false;
     }
+    return false;
 }
 
 // 2-D tiled bulk copy global -> shared, completing on `bar` (complete_tx).
@@ -136,5 +143,8 @@ cudaError_t device_status_ptr(int **ptr);
 // Host: read the current device's status word into *status and clear it
 // (synchronises `st`).
 cudaError_t read_device_status(int *status, cudaStream_t st);
+
+// Host: launch the bounded-wait self-test (sg_wait_selftest) on `st`.
+cudaError_t launch_wait_selftest(int blocks, int arrive, uint64_t limit_ns, cudaStream_t st);
 
 }  // namespace sg

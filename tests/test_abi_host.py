@@ -225,3 +225,9 @@ def test_mapped_write_refuses_memory_it_cannot_check(L):
     assert sg.sg_map_write_mapped(8, 8, 0, 0, ptr, 2, 1,           # 8-byte tile rows
                                   sg.launch_opts(store="fill")) == sg.SG_EUNSUPPORTED
     assert sg.sg_map_write_mapped(17, 16, 0, 0, ptr, 2, 1) == sg.SG_EINVAL
+
+
+def test_wait_selftest_validates_before_launch(L):
+    # block counts and wait limits out of range are refused on the host
+    for blocks, limit in ((0, 10 ** 6), (1025, 10 ** 6), (1, 999), (1, 2 * 10 ** 9 + 1)):
+        assert sg.sg_wait_selftest(blocks, 0, limit) == sg.SG_EINVAL, (blocks, limit)
