@@ -94,6 +94,8 @@ def _load():
         lib.or_diffuse_step_region.restype = None
         lib.or_write_expected_at.argtypes = [i32, i32, i32, u64, u64, vp, vp, vp, vp]
         lib.or_write_expected_at.restype = None
+        lib.or_compact_cells.argtypes = [i32, i32, i32, vp, vp]
+        lib.or_compact_cells.restype = None
         _lib = lib
         return lib
 
@@ -260,3 +262,53 @@ def diffuse_steps(r: int, u: np.ndarray, steps: int, alpha: float = 0.2,
     for _ in range(steps):
         u = diffuse_step(r, u, alpha, x0, y0)
     return u
+
+
+# --------------------------------------------------------------------------
+# Compact storage: only the 3^r gasket cells, tile by tile in launch order
+# --------------------------------------------------------------------------
+
+def compact_cells(r: int, s: int, order: int = ORDER_INTERLEAVED):
+    """(xs, ys): the cell that each element of a level-r compact array with
+    tile side 2^s holds (3^r entries each, uint64)."""
+    assert 0 <= s <= min(r, 6)
+    total = 3 ** r
+    xs = np.zeros(total, dtype=np.uint64)
+    ys = np.zeros(total, dtype=np.uint64)
+    _load().or_compact_cells(r, s, order, _ptr(xs), _ptr(ys))
+    return xs, ys
+
+
+def compact_pack(r: int, s: int, grid: np.ndarray, order: int = ORDER_INTERLEAVED):
+    """The compact array of an embedded n x n grid: its gasket cells, read in
+    the compact order."""
+    xs, ys = compact_cells(r, s, order)
+    return np.asarray(grid)[ys.astype(np.int64), xs.astype(np.int64)].copy()
+
+
+def compact_unpack(r: int, s: int, compact: np.ndarray, grid: np.ndarray,
+                   order: int = ORDER_INTERLEAVED):
+    """Write a compact array's elements into their cells of ``grid`` (in
+    place); every other cell keeps its content."""
+    xs, ys = compact_cells(r, s, order)
+    grid[ys.astype(np.int64), xs.astype(np.int64)] = compact
+    return grid
+
+
+def compact_ca_step(r: int, s: int, compact: np.ndarray,
+                    order: int = ORDER_INTERLEAVED) -> np.ndarray:
+    """One CA step on a compact state: the embedded step of the state it
+    stands for (off-gasket cells 0), read back in the compact order."""
+    n = 1 << r
+    g = compact_unpack(r, s, compact, np.zeros((n, n), dtype=np.uint8), order)
+    return compact_pack(r, s, ca_step(r, g), order)
+
+
+def compact_diffuse_step(r: int, s: int, compact: np.ndarray, alpha: float = 0.2,
+                         order: int = ORDER_INTERLEAVED) -> np.ndarray:
+    """One diffusion step (double precision) on a compact field, through the
+    embedded step as for compact_ca_step."""
+    n = 1 << r
+    g = compact_unpack(r, s, np.asarray(compact, dtype=np.float64),
+                       np.zeros((n, n), dtype=np.float64), order)
+    return compact_pack(r, s, diffuse_step(r, g, alpha), order)

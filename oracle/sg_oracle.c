@@ -375,3 +375,38 @@ void or_write_expected_at(int r, int dtype, int vk, uint64_t vs, uint64_t count,
                                                 : ((const float *)before)[i];
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Compact storage: the succinct blocked layout (Section II) with the        */
+/* block-space map as its block order                                        */
+/* ------------------------------------------------------------------------ */
+
+/* The cell held by every element of a compact array at level r with tile
+ * side 2^s, written to xs[i], ys[i] for i < 3^r:
+ *   q = i div 3^s and e = i mod 3^s;
+ *   (bx, by) = the block of launch index q (or_block_of_index, level r - s);
+ *   (tx, ty) = the e-th cell of the level-s gasket {(tx & ty) == 0} when its
+ *              2^s x 2^s square is read row by row;
+ *   x = bx * 2^s + tx, y = by * 2^s + ty.
+ * Every non-empty tile holds the same level-s pattern, so the tiles become
+ * runs of 3^s consecutive elements in launch order.  The level-s cells are
+ * listed once by scanning the square (rows top to bottom, each row left to
+ * right) and keeping the members. */
+void or_compact_cells(int r, int s, int order, uint64_t *xs, uint64_t *ys)
+{
+    uint64_t rho = (uint64_t)1 << s, per_tile = ipow3(s);
+    uint64_t tiles = ipow3(r - s);
+    uint64_t ltx[729], lty[729];          /* s <= 6: at most 3^6 cells */
+    uint64_t m = 0;
+    for (uint64_t ty = 0; ty < rho; ++ty)
+        for (uint64_t tx = 0; tx < rho; ++tx)
+            if (or_member(tx, ty)) { ltx[m] = tx; lty[m] = ty; ++m; }
+    for (uint64_t q = 0; q < tiles; ++q) {
+        uint64_t bx, by;
+        or_block_of_index(r - s, order, q, &bx, &by);
+        for (uint64_t e = 0; e < per_tile; ++e) {
+            xs[q * per_tile + e] = bx * rho + ltx[e];
+            ys[q * per_tile + e] = by * rho + lty[e];
+        }
+    }
+}

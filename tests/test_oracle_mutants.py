@@ -38,6 +38,11 @@ MUTANTS = [
      "if (!in_grid(nx, n) || !in_grid(ny, n)) continue;\n                    if (!or_member((uint64_t)nx, (uint64_t)ny)) continue;\n                    ++deg;",
      "if (!or_member((uint64_t)nx, (uint64_t)ny)) continue;\n                    ++deg;\n                    if (!in_grid(nx, n) || !in_grid(ny, n)) continue;"),
     ("launch-bbox-count", "                        ++l;\n", "                        l += 2;\n"),
+    ("compact-scan-by-columns",
+     "if (or_member(tx, ty)) { ltx[m] = tx; lty[m] = ty; ++m; }",
+     "if (or_member(tx, ty)) { ltx[m] = ty; lty[m] = tx; ++m; }"),
+    ("compact-tile-transposed", "xs[q * per_tile + e] = bx * rho + ltx[e];",
+     "xs[q * per_tile + e] = by * rho + ltx[e];"),
 ]
 
 

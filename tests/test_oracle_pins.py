@@ -387,3 +387,100 @@ def test_write_expected_at_matches_full_pass(orc):
     ys, xs = np.divmod(np.arange(n * n), n)
     got = orc.write_expected_at(r, np.uint8, orc.VAL_HASH, 9, xs, ys, before.ravel())
     assert np.array_equal(got, full.ravel())
+
+
+# --------------------------------------------------------------------------
+# Compact storage
+# --------------------------------------------------------------------------
+
+def test_compact_layout_hand_worked(orc):
+    rows = read_golden_rows("compact_hand.txt")
+    cases = {}
+    for r, s, order, i, x, y in rows:
+        cases.setdefault((int(r), int(s), int(order)), []).append((int(i), int(x), int(y)))
+    assert len(rows) == 9 + 9 + 27
+    for (r, s, order), cells in cases.items():
+        xs, ys = orc.compact_cells(r, s, order)
+        assert len(xs) == 3 ** r == len(cells)
+        for i, x, y in cells:
+            assert (int(xs[i]), int(ys[i])) == (x, y), (r, s, order, i)
+
+
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("r", range(0, 10))
+def test_compact_layout_is_a_bijection_onto_the_gasket(orc, r, order):
+    # every element holds a distinct gasket cell and all 3^r cells appear
+    n = 1 << r
+    for s in range(0, min(r, 6) + 1):
+        xs, ys = orc.compact_cells(r, s, order)
+        assert len(xs) == 3 ** r
+        assert not np.any(xs & ys)
+        assert xs.max(initial=0) < n and ys.max(initial=0) < n
+        assert len(np.unique(ys * n + xs)) == 3 ** r
+
+
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("r,s", [(3, 1), (6, 2), (8, 4), (9, 6), (10, 5)])
+def test_compact_tiles_are_runs_in_launch_order(orc, r, s, order):
+    # element block q*3^s .. (q+1)*3^s - 1 lies in tile q of the block map,
+    # and inside it the cells come row by row, left to right
+    xs, ys = orc.compact_cells(r, s, order)
+    bx, by = orc.block_map(r - s, order)
+    c = 3 ** s
+    tx = (xs.reshape(-1, c) & ((1 << s) - 1)).astype(np.int64)
+    ty = (ys.reshape(-1, c) & ((1 << s) - 1)).astype(np.int64)
+    assert np.array_equal(xs.reshape(-1, c) >> np.uint64(s), np.repeat(bx[:, None], c, 1))
+    assert np.array_equal(ys.reshape(-1, c) >> np.uint64(s), np.repeat(by[:, None], c, 1))
+    key = ty * (1 << s) + tx
+    assert np.all(np.diff(key, axis=1) > 0)
+
+
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("r", [0, 1, 3, 6])
+def test_compact_single_tile_is_the_row_major_member_list(orc, r, order):
+    # with one tile (s = r) the compact order is the gasket read row by row,
+    # which numpy's nonzero gives for the membership mask
+    xs, ys = orc.compact_cells(r, r, order)
+    ny, nx = np.nonzero(orc.member_grid(r))
+    assert np.array_equal(xs, nx.astype(np.uint64)) and np.array_equal(ys, ny.astype(np.uint64))
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_compact_unit_tiles_follow_the_block_map(orc, order):
+    # with 1 x 1 tiles (s = 0) element q is block q itself
+    for r in range(0, 8):
+        xs, ys = orc.compact_cells(r, 0, order)
+        bx, by = orc.block_map(r, order)
+        assert np.array_equal(xs, bx.astype(np.uint64)) and np.array_equal(ys, by.astype(np.uint64))
+
+
+def test_compact_pack_unpack_round_trip(orc):
+    r, s, n = 7, 3, 128
+    rng = np.random.default_rng(4)
+    g = rng.integers(0, 256, (n, n), dtype=np.uint8)
+    c = orc.compact_pack(r, s, g)
+    assert c.shape == (3 ** r,)
+    back = orc.compact_unpack(r, s, c, np.zeros_like(g))
+    mask = orc.member_grid(r).astype(bool)
+    assert np.array_equal(back, np.where(mask, g, 0))
+    assert np.array_equal(orc.compact_pack(r, s, back), c)
+
+
+def test_compact_steps_are_the_embedded_steps(orc):
+    # the compact CA and diffusion steps stand for the embedded ones: same
+    # multiset of cell values, placed by the layout
+    r, s, n = 6, 2, 64
+    from paper_1706_04552_gb300 import inputs
+    g = inputs.ca_seed_grid(r, 0.4, 3)
+    c = orc.compact_pack(r, s, g)
+    want = orc.ca_step(r, g)
+    got = orc.compact_unpack(r, s, orc.compact_ca_step(r, s, c), np.zeros_like(g))
+    assert np.array_equal(got, want)
+    u = inputs.uniform_grid(r, 3)
+    cu = orc.compact_pack(r, s, u)
+    want = orc.diffuse_step(r, u, 0.2)
+    got = orc.compact_unpack(r, s, orc.compact_diffuse_step(r, s, cu, 0.2),
+                             np.zeros((n, n)))
+    assert np.array_equal(got, want)
+    # the total over the gasket is conserved in the compact form too
+    assert abs(orc.compact_diffuse_step(r, s, cu).sum() - cu.astype(np.float64).sum()) < 1e-9
