@@ -65,7 +65,8 @@ def parse_args():
                         "lambda (bounding sub-boxes, per-cell stores) vs bounding box, timed "
                         "as 100 sub-averages of 10 consecutive calls; prints one JSON line")
     p.add_argument("--workload", choices=("write", "ca", "diffusion", "ca_fused",
-                                          "diffusion_fused"), default="write",
+                                          "diffusion_fused", "ca_compact",
+                                          "diffusion_compact"), default="write",
                    help="with --quick: time the level-15 CA or diffusion step (or its "
                         "fused form, k steps per launch) instead of the write pass (the "
                         "form used to profile those kernels)")
@@ -380,6 +381,7 @@ def run_stencil_quick(args, sg, torch, dev, stream):
     r = args.level if args.level else max(s["levels"])
     n = 1 << r
     kind, fused = args.workload.split("_")[0], args.workload.endswith("_fused")
+    compact = args.workload.endswith("_compact")
     if kind == "ca":
         idx, vals = inputs.ca_seed_sparse(r, s["ca_p"], s["ca_seed"])
         dt = torch.uint8
@@ -390,10 +392,17 @@ def run_stencil_quick(args, sg, torch, dev, stream):
         rho, k = (s["diff_fuse_rho"], s["diff_fuse"]) if fused else (s["diff_rho"], 1)
     a = torch.zeros(n * n, dtype=dt, device=dev)
     a[torch.from_numpy(idx).to(dev)] = torch.from_numpy(vals).to(dev)
+    if compact:
+        rho = workloads.COMPACT["rho"]
+        a = sg.compact_pack(a, torch.empty(3 ** r, dtype=dt, device=dev), r, rho, stream=stream)
     bufs = [a, torch.zeros_like(a)]
 
     def step():
-        if kind == "ca":
+        if compact and kind == "ca":
+            sg.compact_ca_step(bufs[0], bufs[1], r, rho, stream=stream)
+        elif compact:
+            sg.compact_diffuse_step(bufs[0], bufs[1], r, rho, s["alpha"], stream=stream)
+        elif kind == "ca":
             sg.ca_steps(bufs[0], bufs[1], r, rho, k, "lambda", stream)
         else:
             sg.diffuse_steps(bufs[0], bufs[1], r, rho, k, s["alpha"], "lambda", stream)
@@ -402,7 +411,7 @@ def run_stencil_quick(args, sg, torch, dev, stream):
         step()
     total_ms, per = time_launches(step, args.steps, stream)
     return {"workload": f"{args.workload}, level {r}, rho {rho}, {k} step(s) per launch, "
-                        f"lambda",
+                        + ("compact layout" if compact else "lambda"),
             "unit": UNIT, "value": round(3 ** r * k / (total_ms / args.steps / 1e3) / 1e9, 3),
             "launch_ms_mean": round(statistics.mean(per), 5), "steps": args.steps}
 
@@ -730,6 +739,8 @@ def compare_workloads(sg, torch, dev, stream, w, grid_u8, headline_launch_ms):
     torch.cuda.empty_cache()
     # the same step sequences with k steps fused per launch
     res.update(fused_stencils(sg, torch, dev, stream, rs, res))
+    # the write pass and the step sequences on compact arrays
+    res["compact"] = compact_layout(sg, torch, dev, stream, r, rs, res, headline_launch_ms)
     return res
 
 
@@ -772,6 +783,67 @@ def fused_stencils(sg, torch, dev, stream, r, single):
             "rho": rho, "steps": total, "steps_per_launch": k, "launches": len(chunks),
             "us_per_step": round(ms * 1e3 / total, 2), "GCells_s": round(rate, 3),
             "speedup_vs_single_step": round(rate / base, 3) if base else None}
+        del a, bufs
+        torch.cuda.empty_cache()
+    return out
+
+
+def compact_layout(sg, torch, dev, stream, rw, rs, single, headline_launch_ms):
+    """The level-rw write pass and the level-rs stencil sequences on compact
+    arrays (only the 3^r gasket cells, tiles in launch order): rates, the
+    bytes each form keeps on the device, and the ratio to the embedded runs.
+    The compact stencil states start from the embedded seeds, packed."""
+    from paper_1706_04552_gb300 import inputs, workloads
+    c = workloads.COMPACT
+    s = workloads.STENCILS
+    rho, order = c["rho"], c["order"]
+    out = {"rho": rho, "order": order}
+    cw = 3 ** rw
+    buf = torch.empty(cw, dtype=torch.uint8, device=dev)
+    f = lambda: sg.compact_map_write(buf, rw, rho, "hash", 1, order=order, stream=stream)
+    for _ in range(3):
+        f()
+    ms, per = time_launches(f, 200, stream)
+    out[f"write_u8_r{rw}"] = {
+        "GCells_s": _rate(cw, ms / 200), "launch_ms": round(statistics.mean(per), 5),
+        "bytes_on_device": cw, "embedded_bytes_on_device": 1 << (2 * rw),
+        "speedup_vs_embedded_fill": round(headline_launch_ms / statistics.mean(per), 3)}
+    del buf
+    n, cs = 1 << rs, 3 ** rs
+    for kind in ("ca", "diffusion"):
+        if kind == "ca":
+            idx, vals = inputs.ca_seed_sparse(rs, s["ca_p"], s["ca_seed"])
+            dt, total, elem = torch.uint8, s["ca_steps"], 1
+        else:
+            idx, vals = inputs.uniform_sparse(rs, s["diff_seed"])
+            dt, total, elem = torch.float32, s["diff_steps"], 4
+        g = torch.zeros(n * n, dtype=dt, device=dev)
+        g[torch.from_numpy(idx).to(dev)] = torch.from_numpy(vals).to(dev)
+        a = sg.compact_pack(g, torch.empty(cs, dtype=dt, device=dev), rs, rho, order=order,
+                            stream=stream)
+        del g
+        bufs = [a, torch.empty_like(a)]
+
+        def step():
+            if kind == "ca":
+                sg.compact_ca_step(bufs[0], bufs[1], rs, rho, order=order, stream=stream)
+            else:
+                sg.compact_diffuse_step(bufs[0], bufs[1], rs, rho, s["alpha"], order=order,
+                                        stream=stream)
+            bufs.reverse()
+        for _ in range(4):
+            step()
+        ms, per = time_launches(step, total, stream)
+        rate = cs * total / (ms / 1e3) / 1e9
+        one = single.get(f"{kind}_r{rs}_lambda", {}).get("GCells_s")
+        fused = single.get(f"{kind}_r{rs}_fused", {}).get("GCells_s")
+        out[f"{kind}_r{rs}"] = {
+            "steps": total, "us_per_step": round(ms * 1e3 / total, 2),
+            "GCells_s": round(rate, 3),
+            # read + write of every element: both buffers fit in L2 for the CA
+            "state_bytes": 2 * cs * elem, "embedded_state_bytes": 2 * n * n * elem,
+            "speedup_vs_single_step": round(rate / one, 3) if one else None,
+            "speedup_vs_fused": round(rate / fused, 3) if fused else None}
         del a, bufs
         torch.cuda.empty_cache()
     return out

@@ -392,6 +392,60 @@ SG_API sg_status sg_batch_ca_step_noalloc(int count, const int *levels, uint8_t 
                                           const sg_launch_opts *opts, void *stream);
 
 /*
+ * Compact layout (the succinct blocked layout of Section II, with the
+ * block-space map of Theorem 1 as the order of its blocks).  A compact array
+ * at level r and tile side rho = 2^s holds only the 3^r gasket cells:
+ * element i holds cell (bx*rho + tx, by*rho + ty), where (bx, by) is the
+ * lambda block of launch index q = i div 3^s in the walking order
+ * opts->order (the same block sg_block_map lists at position q), and
+ * (tx, ty) is the (i mod 3^s)-th cell of the level-s gasket read row by row
+ * (rows top to bottom, each row left to right).  Every non-empty tile holds
+ * that same pattern (Section III), so the tiles are runs of 3^s consecutive
+ * elements.  At r = 16 an 8-bit array takes 43 MB instead of 4.3 GB.
+ *
+ * Common arguments and errors:
+ *   r, rho   as for sg_map_write (rho a power of two in 1..64, rho <= 2^r)
+ *   opts     NULL or launch options: order and ctas_per_sm are used; store
+ *            must be SG_STORE_AUTO (other values: SG_EUNSUPPORTED)
+ *   compact arrays: device pointers to 3^r elements, aligned to the
+ *            element size; embedded grids: device pointers to n*n elements
+ *            (n = 2^r), aligned to the element size
+ *   stream   cudaStream_t; every call launches one kernel and returns
+ *            without synchronising
+ * SG_EINVAL for out-of-range values, null or misaligned pointers, or an
+ * output that is also the input; SG_ECUDA if the launch failed.
+ */
+
+/* sg_compact_pack -- compact[i] = grid at the cell of element i.  Reads only
+ * gasket cells of `grid`. */
+SG_API sg_status sg_compact_pack(int r, int rho, sg_dtype dtype, const void *grid,
+                                 void *compact, const sg_launch_opts *opts, void *stream);
+
+/* sg_compact_unpack -- grid at the cell of element i = compact[i].  Writes
+ * only gasket cells of `grid`; every other cell keeps its content. */
+SG_API sg_status sg_compact_unpack(int r, int rho, sg_dtype dtype, const void *compact,
+                                   void *grid, const sg_launch_opts *opts, void *stream);
+
+/* sg_compact_map_write -- the map-and-write pass (Section IV) on a compact
+ * array: element i receives v(x, y) of its cell (sg_value_kind, the same
+ * values sg_map_write writes there). */
+SG_API sg_status sg_compact_map_write(int r, int rho, sg_dtype dtype, void *compact,
+                                      sg_value_kind value_kind, uint64_t value_or_seed,
+                                      const sg_launch_opts *opts, void *stream);
+
+/* sg_compact_ca_step -- one gasket-restricted B3/S23 step on compact 0/1
+ * states: out = pack(sg_ca_step(unpack(in))), cell for cell.  in != out. */
+SG_API sg_status sg_compact_ca_step(int r, int rho, const uint8_t *in, uint8_t *out,
+                                    const sg_launch_opts *opts, void *stream);
+
+/* sg_compact_diffuse_step -- one explicit diffusion step on a compact field:
+ * out = pack(sg_diffuse_step(unpack(in))), bit for bit (the same arithmetic
+ * per cell).  in != out; alpha finite. */
+SG_API sg_status sg_compact_diffuse_step(int r, int rho, const float *in, float *out,
+                                         float alpha, const sg_launch_opts *opts,
+                                         void *stream);
+
+/*
  * sg_device_status -- report and clear the device status word of the current
  * device.  Kernels with bounded waits (SG_STORE_TMA, sg_wait_selftest) record
  * a wait that gave up there instead of spinning; the call synchronises

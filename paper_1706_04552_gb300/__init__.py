@@ -27,6 +27,9 @@ __all__ = [
     "sg_ca_steps", "sg_diffuse_steps", "FUSE_MAX",
     "sg_launch_stats", "sg_status_str", "sg_abi_version", "sg_device_status",
     "device_status", "sg_wait_selftest", "wait_selftest",
+    "sg_compact_pack", "sg_compact_unpack", "sg_compact_map_write", "sg_compact_ca_step",
+    "sg_compact_diffuse_step", "compact_size", "compact_pack", "compact_unpack",
+    "compact_map_write", "compact_ca_step", "compact_diffuse_step",
     "CABatch", "Graph", "BatchPlan",
     "map_write", "map_write_host", "map_write_mapped", "sg_map_write_mapped", "ca_step",
     "diffuse_step", "ca_steps", "diffuse_steps",
@@ -154,6 +157,16 @@ def lib() -> ctypes.CDLL:
         L.sg_device_status.restype = i32
         L.sg_wait_selftest.argtypes = [i32, i32, u64, vp]
         L.sg_wait_selftest.restype = i32
+        L.sg_compact_pack.argtypes = [i32, i32, i32, vp, vp, p_opts, vp]
+        L.sg_compact_pack.restype = i32
+        L.sg_compact_unpack.argtypes = [i32, i32, i32, vp, vp, p_opts, vp]
+        L.sg_compact_unpack.restype = i32
+        L.sg_compact_map_write.argtypes = [i32, i32, i32, vp, i32, u64, p_opts, vp]
+        L.sg_compact_map_write.restype = i32
+        L.sg_compact_ca_step.argtypes = [i32, i32, vp, vp, p_opts, vp]
+        L.sg_compact_ca_step.restype = i32
+        L.sg_compact_diffuse_step.argtypes = [i32, i32, vp, vp, ctypes.c_float, p_opts, vp]
+        L.sg_compact_diffuse_step.restype = i32
         L.sg_abi_version.argtypes = []
         L.sg_abi_version.restype = i32
         _lib = L
@@ -548,3 +561,113 @@ def launch_stats(r: int, rho: int, map="lambda"):
     st, launched, useful = sg_launch_stats(r, rho, _map_id(map))
     _check("sg_launch_stats", st)
     return launched, useful
+
+
+# ---------------------------------------------------------------- compact layout
+# Arrays of the 3^r gasket cells only, tile by tile in launch order (layout in
+# include/sg.h).  Raw C layer, then tensor functions.
+
+def sg_compact_pack(r, rho, dtype, grid_ptr, compact_ptr, opts=None, stream=0) -> int:
+    return int(lib().sg_compact_pack(r, rho, dtype, grid_ptr, compact_ptr,
+                                     _opts_ref(opts), stream))
+
+
+def sg_compact_unpack(r, rho, dtype, compact_ptr, grid_ptr, opts=None, stream=0) -> int:
+    return int(lib().sg_compact_unpack(r, rho, dtype, compact_ptr, grid_ptr,
+                                       _opts_ref(opts), stream))
+
+
+def sg_compact_map_write(r, rho, dtype, compact_ptr, value_kind, value_or_seed, opts=None,
+                         stream=0) -> int:
+    return int(lib().sg_compact_map_write(r, rho, dtype, compact_ptr, value_kind,
+                                          value_or_seed & (2**64 - 1), _opts_ref(opts),
+                                          stream))
+
+
+def sg_compact_ca_step(r, rho, in_ptr, out_ptr, opts=None, stream=0) -> int:
+    return int(lib().sg_compact_ca_step(r, rho, in_ptr, out_ptr, _opts_ref(opts), stream))
+
+
+def sg_compact_diffuse_step(r, rho, in_ptr, out_ptr, alpha, opts=None, stream=0) -> int:
+    return int(lib().sg_compact_diffuse_step(r, rho, in_ptr, out_ptr, alpha,
+                                             _opts_ref(opts), stream))
+
+
+def compact_size(r: int) -> int:
+    """Elements of a level-r compact array: the 3^r gasket cells."""
+    return 3 ** r
+
+
+def _compact_check(t, r, dtypes, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name}: expected a CUDA tensor (there is no CPU path)")
+    if t.dtype not in dtypes:
+        raise TypeError(f"{name}: dtype {t.dtype} not in {dtypes}")
+    if not t.is_contiguous() or t.numel() != 3 ** r:
+        raise ValueError(f"{name}: expected a contiguous tensor of 3^{r} elements")
+
+
+def _dtype_id(t):
+    import torch
+    return DTYPES["u8"] if t.dtype == torch.uint8 else DTYPES["f32"]
+
+
+def compact_pack(grid, compact, r: int, rho: int, order=None, stream=None, ctas_per_sm=None):
+    """compact <- the gasket cells of the embedded ``grid`` (same dtype)."""
+    import torch
+    _grid_check(grid, r, (torch.uint8, torch.float32), "grid")
+    _compact_check(compact, r, (grid.dtype,), "compact")
+    with _on_device(grid):
+        _check("sg_compact_pack", sg_compact_pack(
+            r, rho, _dtype_id(grid), grid.data_ptr(), compact.data_ptr(),
+            launch_opts(order, None, ctas_per_sm), _stream_handle(grid, stream)))
+    return compact
+
+
+def compact_unpack(compact, grid, r: int, rho: int, order=None, stream=None, ctas_per_sm=None):
+    """The gasket cells of the embedded ``grid`` <- compact (others unchanged)."""
+    import torch
+    _grid_check(grid, r, (torch.uint8, torch.float32), "grid")
+    _compact_check(compact, r, (grid.dtype,), "compact")
+    with _on_device(grid):
+        _check("sg_compact_unpack", sg_compact_unpack(
+            r, rho, _dtype_id(grid), compact.data_ptr(), grid.data_ptr(),
+            launch_opts(order, None, ctas_per_sm), _stream_handle(grid, stream)))
+    return grid
+
+
+def compact_map_write(compact, r: int, rho: int, value="hash", value_or_seed=1, order=None,
+                      stream=None, ctas_per_sm=None):
+    """Map-and-write pass on a compact array (uint8 or float32, 3^r elements)."""
+    import torch
+    _compact_check(compact, r, (torch.uint8, torch.float32), "compact")
+    vk = VALUES[value] if isinstance(value, str) else int(value)
+    with _on_device(compact):
+        _check("sg_compact_map_write", sg_compact_map_write(
+            r, rho, _dtype_id(compact), compact.data_ptr(), vk, value_or_seed,
+            launch_opts(order, None, ctas_per_sm), _stream_handle(compact, stream)))
+    return compact
+
+
+def compact_ca_step(inp, out, r: int, rho: int, order=None, stream=None, ctas_per_sm=None):
+    import torch
+    _compact_check(inp, r, (torch.uint8,), "in")
+    _compact_check(out, r, (torch.uint8,), "out")
+    with _on_device(inp):
+        _check("sg_compact_ca_step", sg_compact_ca_step(
+            r, rho, inp.data_ptr(), out.data_ptr(), launch_opts(order, None, ctas_per_sm),
+            _stream_handle(inp, stream)))
+    return out
+
+
+def compact_diffuse_step(inp, out, r: int, rho: int, alpha: float = 0.2, order=None,
+                         stream=None, ctas_per_sm=None):
+    import torch
+    _compact_check(inp, r, (torch.float32,), "in")
+    _compact_check(out, r, (torch.float32,), "out")
+    with _on_device(inp):
+        _check("sg_compact_diffuse_step", sg_compact_diffuse_step(
+            r, rho, inp.data_ptr(), out.data_ptr(), float(alpha),
+            launch_opts(order, None, ctas_per_sm), _stream_handle(inp, stream)))
+    return out

@@ -8,6 +8,7 @@
 #include "sg.h"
 #include "sg_device.cuh"
 #include "sg_internal.h"
+#include "sg_compact.cuh"
 #include "sg_tma.cuh"
 
 namespace sg {
@@ -334,6 +335,88 @@ sg_status sg_block_map(int rb, sg_order order, uint32_t *bx, uint32_t *by, void 
     if (bx == nullptr || by == nullptr || bx == by) return SG_EINVAL;
     if (!aligned(bx, 4) || !aligned(by, 4)) return SG_EINVAL;
     return finish(launch_block_map(rb, (int)order, bx, by, (cudaStream_t)stream));
+}
+
+namespace {
+// Checks shared by the compact entries; on success *s = log2(rho).
+sg_status compact_args(int r, int rho, const sg_launch_opts *opts, LaunchCfg *cfg, int *s)
+{
+    if (!valid_level_tile(r, rho, s)) return SG_EINVAL;
+    if (!read_launch_opts(opts, cfg)) return SG_EINVAL;
+    if (cfg->store != kStoreAuto) return SG_EUNSUPPORTED;
+    return SG_OK;
+}
+}  // namespace
+
+sg_status sg_compact_pack(int r, int rho, sg_dtype dtype, const void *grid, void *compact,
+                          const sg_launch_opts *opts, void *stream)
+{
+    int s = 0;
+    LaunchCfg cfg;
+    if (dtype != SG_U8 && dtype != SG_F32) return SG_EINVAL;
+    const int elem = dtype == SG_U8 ? 1 : 4;
+    if (grid == nullptr || compact == nullptr || grid == compact) return SG_EINVAL;
+    if (!aligned(grid, (uintptr_t)elem) || !aligned(compact, (uintptr_t)elem)) return SG_EINVAL;
+    const sg_status st = compact_args(r, rho, opts, &cfg, &s);
+    if (st != SG_OK) return st;
+    return finish(launch_compact_pack(r, s, cfg.order, elem, grid, compact,
+                                      (cudaStream_t)stream, cfg));
+}
+
+sg_status sg_compact_unpack(int r, int rho, sg_dtype dtype, const void *compact, void *grid,
+                            const sg_launch_opts *opts, void *stream)
+{
+    int s = 0;
+    LaunchCfg cfg;
+    if (dtype != SG_U8 && dtype != SG_F32) return SG_EINVAL;
+    const int elem = dtype == SG_U8 ? 1 : 4;
+    if (grid == nullptr || compact == nullptr || grid == compact) return SG_EINVAL;
+    if (!aligned(grid, (uintptr_t)elem) || !aligned(compact, (uintptr_t)elem)) return SG_EINVAL;
+    const sg_status st = compact_args(r, rho, opts, &cfg, &s);
+    if (st != SG_OK) return st;
+    return finish(launch_compact_unpack(r, s, cfg.order, elem, compact, grid,
+                                        (cudaStream_t)stream, cfg));
+}
+
+sg_status sg_compact_map_write(int r, int rho, sg_dtype dtype, void *compact,
+                               sg_value_kind value_kind, uint64_t value_or_seed,
+                               const sg_launch_opts *opts, void *stream)
+{
+    int s = 0;
+    LaunchCfg cfg;
+    if (dtype != SG_U8 && dtype != SG_F32) return SG_EINVAL;
+    if (value_kind < SG_VAL_CONST || value_kind > SG_VAL_HASH) return SG_EINVAL;
+    const int elem = dtype == SG_U8 ? 1 : 4;
+    if (compact == nullptr || !aligned(compact, (uintptr_t)elem)) return SG_EINVAL;
+    const sg_status st = compact_args(r, rho, opts, &cfg, &s);
+    if (st != SG_OK) return st;
+    return finish(launch_compact_write(r, s, cfg.order, elem, (int)value_kind, compact,
+                                       value_or_seed, (cudaStream_t)stream, cfg));
+}
+
+sg_status sg_compact_ca_step(int r, int rho, const uint8_t *in, uint8_t *out,
+                             const sg_launch_opts *opts, void *stream)
+{
+    int s = 0;
+    LaunchCfg cfg;
+    if (in == nullptr || out == nullptr || in == out) return SG_EINVAL;
+    const sg_status st = compact_args(r, rho, opts, &cfg, &s);
+    if (st != SG_OK) return st;
+    return finish(launch_compact_ca(r, s, cfg.order, in, out, (cudaStream_t)stream, cfg));
+}
+
+sg_status sg_compact_diffuse_step(int r, int rho, const float *in, float *out, float alpha,
+                                  const sg_launch_opts *opts, void *stream)
+{
+    int s = 0;
+    LaunchCfg cfg;
+    if (in == nullptr || out == nullptr || in == out) return SG_EINVAL;
+    if (!aligned(in, 4) || !aligned(out, 4)) return SG_EINVAL;
+    if (!(alpha == alpha) || alpha > 3.0e38f || alpha < -3.0e38f) return SG_EINVAL;
+    const sg_status st = compact_args(r, rho, opts, &cfg, &s);
+    if (st != SG_OK) return st;
+    return finish(launch_compact_diffuse(r, s, cfg.order, in, out, alpha, (cudaStream_t)stream,
+                                         cfg));
 }
 
 sg_status sg_device_status(void *stream)

@@ -42,6 +42,11 @@ STENCILS = dict(levels=(14, 15), ca_p=0.3, ca_seed=0, ca_steps=256,
                 # the same sequences with k steps fused per launch
                 ca_fuse=16, ca_fuse_rho=64, diff_fuse=8, diff_fuse_rho=64)
 
+# The same write pass and stencil sequences on compact arrays (the 3^r
+# gasket cells only, tiles in launch order): 43 MB instead of 4.3 GB for the
+# level-16 uint8 grid.
+COMPACT = dict(rho=64, order="interleaved")
+
 # Batched: 64 gaskets with levels drawn uniformly from 8..14 (seed 2), each
 # with its own uint8 CA state (Bernoulli(0.3), seed 2 + i * 2^32), 64 CA
 # steps each: one launch per step over the prefix-summed work list (captured

@@ -231,3 +231,29 @@ def test_wait_selftest_validates_before_launch(L):
     # block counts and wait limits out of range are refused on the host
     for blocks, limit in ((0, 10 ** 6), (1025, 10 ** 6), (1, 999), (1, 2 * 10 ** 9 + 1)):
         assert sg.sg_wait_selftest(blocks, 0, limit) == sg.SG_EINVAL, (blocks, limit)
+
+
+def test_compact_entries_validate_before_launch(L):
+    u8, f32 = sg.DTYPES["u8"], sg.DTYPES["f32"]
+    # level, tile side, dtype, pointers, alignment, aliasing
+    assert sg.sg_compact_pack(17, 16, u8, FAKE, FAKE + 4096) == sg.SG_EINVAL
+    assert sg.sg_compact_pack(8, 128, u8, FAKE, FAKE + 4096) == sg.SG_EINVAL
+    assert sg.sg_compact_pack(3, 16, u8, FAKE, FAKE + 4096) == sg.SG_EINVAL   # rho > n
+    assert sg.sg_compact_pack(8, 16, 2, FAKE, FAKE + 4096) == sg.SG_EINVAL
+    assert sg.sg_compact_pack(8, 16, u8, 0, FAKE) == sg.SG_EINVAL
+    assert sg.sg_compact_pack(8, 16, u8, FAKE, FAKE) == sg.SG_EINVAL
+    assert sg.sg_compact_pack(8, 16, f32, FAKE + 2, FAKE + 4096) == sg.SG_EINVAL
+    assert sg.sg_compact_unpack(8, 16, f32, FAKE, FAKE + 4098) == sg.SG_EINVAL
+    assert sg.sg_compact_unpack(8, 12, u8, FAKE, FAKE + 4096) == sg.SG_EINVAL
+    # value kinds, stencil aliasing, alpha, store options
+    assert sg.sg_compact_map_write(8, 16, u8, FAKE, 3, 1) == sg.SG_EINVAL
+    assert sg.sg_compact_map_write(8, 16, u8, 0, 2, 1) == sg.SG_EINVAL
+    assert sg.sg_compact_ca_step(8, 16, FAKE, FAKE) == sg.SG_EINVAL
+    assert sg.sg_compact_ca_step(8, 16, 0, FAKE) == sg.SG_EINVAL
+    assert sg.sg_compact_diffuse_step(8, 16, FAKE, FAKE + 4096, float("nan")) == sg.SG_EINVAL
+    assert sg.sg_compact_diffuse_step(8, 16, FAKE + 1, FAKE + 4096, 0.2) == sg.SG_EINVAL
+    opts = sg.launch_opts(store="staged")
+    assert sg.sg_compact_ca_step(8, 16, FAKE, FAKE + 4096, opts) == sg.SG_EUNSUPPORTED
+    assert sg.sg_compact_map_write(8, 16, u8, FAKE, 2, 1, opts) == sg.SG_EUNSUPPORTED
+    assert sg.sg_compact_ca_step(8, 16, FAKE, FAKE + 4096, sg.launch_opts(order=2)) == sg.SG_EINVAL
+    assert sg.compact_size(16) == 43046721
