@@ -41,6 +41,7 @@ METRIC = ("gasket GCells/s and % of HBM peak at n=2^16, λ vs bounding-box; "
           "served p50/p99 latency")
 UNIT = "GCells/s"
 FALLBACK_HBM_GBS = 6800.0
+NOMINAL_HBM_GBS = 8000.0
 
 
 def parse_args():
@@ -317,6 +318,8 @@ def run_ours(args, grp: Group):
     roofline = {
         "bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
         "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+        # the same against the nominal HBM3e figure (about 8 TB/s)
+        "peak_nominal": NOMINAL_HBM_GBS, "frac_nominal": round(achieved / NOMINAL_HBM_GBS, 4),
         "traffic": recorded_traffic(kernel_key, "sg_write_u8.cu"),
         "algorithmic_bytes_per_launch": line_bytes,
         "algorithmic_bytes": "touched 128-byte lines: 2^7 * 3^9 lines of 128 B",

@@ -20,6 +20,10 @@
 // cells exist here: nothing is spent on the off-gasket 82 % of a 64-tile, and
 // the state of a level-15 CA (14.3 MB) stays in L2.
 //
+// The CA on 64-tiles runs bit-sliced instead (compact_ca_bits_kernel below):
+// the gather above spends 9 shared loads per cell and is bound by the L1 /
+// shared-memory pipe, while rows of bits take the rule 64 cells at a time.
+//
 // The cell arithmetic is the embedded kernels' own (life rule on (count |
 // self) == 3; diffusion through diffuse_update with the same grouping of the
 // neighbour sum), so a compact step equals the embedded step cell for cell.
@@ -155,6 +159,258 @@ compact_ca_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int
     }
 }
 
+// ---------------------------------------------------------------------------
+// CA, rho = 64: bit-sliced rows.
+//
+// Row y of a 64-tile holds its gasket cells at the columns x with
+// x & y == 0.  Split x = 8*hi + lo: they sit in the bytes hi with
+// hi & (y >> 3) == 0 and, inside each, at the bits lo with lo & (y & 7) == 0.
+// In compact order the row is one run of 2^(6 - popc(y)) elements, made of
+// one block of 2^(3 - popc(y & 7)) elements per such byte.  A warp takes one
+// tile (729 elements) at a time:
+//   1. ballots turn the 729 states (0 / 1) into 23 words of compact bits;
+//   2. each lane deposits rows 2*lane and 2*lane + 1 into 64-bit row words,
+//      a block at a time through dep[y & 7][block];
+//   3. the B3/S23 rule runs on whole rows: horizontal 3-sums and 2-sums by
+//      bitwise full adders, the rows above and below through shuffles, the
+//      halo cells of the neighbouring tiles as edge bits;
+//   4. the next rows are gathered back (cmp[y & 7][byte]) into compact bits
+//      and stored as bytes.
+// Non-member columns hold 0 in every row word and are dropped by the gather,
+// so the rule can run on them freely.
+// ---------------------------------------------------------------------------
+struct RowCodec {
+    uint8_t dep[8][256];       // block v of a row with y & 7 = yl -> the byte
+    uint8_t cmp[8][256];       // byte of such a row -> its block
+    uint16_t row_start[64];    // compact index (within the tile) of row y's first cell
+};
+
+constexpr int popcount6(int v) { int n = 0; for (int i = 0; i < 6; ++i) n += (v >> i) & 1; return n; }
+
+constexpr RowCodec make_row_codec()
+{
+    RowCodec t{};
+    for (int yl = 0; yl < 8; ++yl)
+        for (int v = 0; v < 256; ++v) {
+            int d = 0, c = 0, k = 0;
+            for (int lo = 0; lo < 8; ++lo)
+                if ((lo & yl) == 0) {
+                    if ((v >> k) & 1) d |= 1 << lo;    // bit k of the block -> column lo
+                    if ((v >> lo) & 1) c |= 1 << k;    // column lo -> bit k of the block
+                    ++k;
+                }
+            t.dep[yl][v] = (uint8_t)d;
+            t.cmp[yl][v] = (uint8_t)c;
+        }
+    int e = 0;
+    for (int y = 0; y < 64; ++y) {
+        t.row_start[y] = (uint16_t)e;
+        e += 1 << (6 - popcount6(y));
+    }
+    return t;
+}
+
+__device__ const RowCodec kRowCodec = make_row_codec();
+static_assert(make_row_codec().row_start[63] == kUnit - 1, "the last row holds one cell");
+
+// The 64 bits of `cb` from bit o on (cb holds two zero guard words).
+__device__ __forceinline__ uint64_t bits_at(const uint32_t *cb, uint32_t o)
+{
+    const uint32_t k = o >> 5, sh = o & 31u;
+    const uint32_t w0 = cb[k], w1 = cb[k + 1], w2 = cb[k + 2];
+    return (uint64_t)__funnelshift_r(w0, w1, sh) | ((uint64_t)__funnelshift_r(w1, w2, sh) << 32);
+}
+
+__device__ __forceinline__ uint64_t deposit_row(const RowCodec &tc, uint64_t c, uint32_t y)
+{
+    const uint32_t yh = y >> 3, yl = y & 7u, nl = 8u >> __popc(yl);
+    const uint32_t lmask = (1u << nl) - 1u;
+    uint64_t row = 0;
+    uint32_t sh = 0;
+#pragma unroll
+    for (uint32_t hi = 0; hi < 8; ++hi)
+        if ((hi & yh) == 0u) {
+            row |= (uint64_t)tc.dep[yl][(uint32_t)(c >> sh) & lmask] << (8 * hi);
+            sh += nl;
+        }
+    return row;
+}
+
+__device__ __forceinline__ uint64_t gather_row(const RowCodec &tc, uint64_t row, uint32_t y)
+{
+    const uint32_t yh = y >> 3, yl = y & 7u, nl = 8u >> __popc(yl);
+    uint64_t c = 0;
+    uint32_t sh = 0;
+#pragma unroll
+    for (uint32_t hi = 0; hi < 8; ++hi)
+        if ((hi & yh) == 0u) {
+            c |= (uint64_t)tc.cmp[yl][(uint32_t)(row >> (8 * hi)) & 0xFFu] << sh;
+            sh += nl;
+        }
+    return c;
+}
+
+// OR the bits of c (those of one row: its other bits are 0) into `ob` at bit o.
+__device__ __forceinline__ void or_bits_at(uint32_t *ob, uint32_t o, uint64_t c)
+{
+    const uint32_t k = o >> 5, sh = o & 31u;
+    const uint32_t lo = (uint32_t)c, hi = (uint32_t)(c >> 32);
+    if (lo << sh) atomicOr(&ob[k], lo << sh);
+    const uint32_t mid = sh ? (lo >> (32 - sh)) | (hi << sh) : hi;
+    if (mid) atomicOr(&ob[k + 1], mid);
+    if (sh && (hi >> (32 - sh))) atomicOr(&ob[k + 2], hi >> (32 - sh));
+}
+
+__device__ __forceinline__ uint64_t maj3(uint64_t a, uint64_t b, uint64_t c)
+{
+    return (a & b) | (c & (a ^ b));
+}
+
+// Horizontal sums of a row (bit x: cells x-1, x, x+1), with the cells left
+// of column 0 and right of column 63 given as edge bits.
+struct RowSums {
+    uint64_t t0, t1;    // 3-sum L + v + R, bit planes
+    uint64_t d0, d1;    // 2-sum L + R
+};
+
+__device__ __forceinline__ RowSums row_sums(uint64_t v, uint32_t left, uint32_t right)
+{
+    const uint64_t L = (v << 1) | (uint64_t)left, R = (v >> 1) | ((uint64_t)right << 63);
+    RowSums s;
+    s.t0 = L ^ v ^ R;
+    s.t1 = maj3(L, v, R);
+    s.d0 = L ^ R;
+    s.d1 = L & R;
+    return s;
+}
+
+// B3/S23 on a row from the 3-sums above and below and its own 2-sum.
+__device__ __forceinline__ uint64_t life_row(uint64_t u0, uint64_t u1, uint64_t m0, uint64_t m1,
+                                             uint64_t b0, uint64_t b1, uint64_t self)
+{
+    const uint64_t s0 = u0 ^ m0 ^ b0, k0 = maj3(u0, m0, b0);
+    const uint64_t t = u1 ^ m1 ^ b1, k1 = maj3(u1, m1, b1);
+    const uint64_t s1 = t ^ k0, k2 = t & k0;
+    // count = s0 + 2*s1 + 4*(k1 + k2): 2 or 3 iff s1 and no carry out of bit 1
+    return s1 & ~(k1 | k2) & (s0 | self);
+}
+
+__device__ __forceinline__ uint64_t shfl_up64(uint64_t v)
+{
+    const uint32_t lo = __shfl_up_sync(0xffffffffu, (uint32_t)v, 1);
+    const uint32_t hi = __shfl_up_sync(0xffffffffu, (uint32_t)(v >> 32), 1);
+    return (uint64_t)lo | ((uint64_t)hi << 32);
+}
+
+__device__ __forceinline__ uint64_t shfl_down64(uint64_t v)
+{
+    const uint32_t lo = __shfl_down_sync(0xffffffffu, (uint32_t)v, 1);
+    const uint32_t hi = __shfl_down_sync(0xffffffffu, (uint32_t)(v >> 32), 1);
+    return (uint64_t)lo | ((uint64_t)hi << 32);
+}
+
+__global__ void __launch_bounds__(kUnitThreads, 4)
+compact_ca_bits_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int r, int order,
+                       uint32_t total)
+{
+    constexpr int S = 6, WORDS = (kUnit + 31) / 32;           // 23 words of compact bits
+    __shared__ RowCodec tc;
+    __shared__ uint32_t cbits[kUnitWarps][WORDS + 3], obits[kUnitWarps][WORDS + 3];
+    {
+        const uint32_t *src = reinterpret_cast<const uint32_t *>(&kRowCodec);
+        uint32_t *dst = reinterpret_cast<uint32_t *>(&tc);
+        for (int i = threadIdx.x; i < (int)(sizeof(RowCodec) / 4); i += kUnitThreads)
+            dst[i] = src[i];
+    }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    uint32_t *cb = cbits[warp], *ob = obits[warp];
+    if (lane >= WORDS && lane < WORDS + 3) cb[lane] = 0u;     // guard words
+    __syncthreads();
+    static_assert(sizeof(RowCodec) % 4 == 0, "copied as words");
+
+    const CompactPattern<S> &pat = compact_pattern<S>();
+    const int rb = r - S;
+    const uint32_t units = total / kUnit;                     // whole tiles: r >= 6
+    LambdaLane ll;
+    ll.init(lane, rb, order);
+    const uint32_t W = pi_word(order, rb);
+    const uint32_t y0 = 2u * lane, y1 = y0 + 1u;
+    const uint32_t o0 = tc.row_start[y0], o1 = tc.row_start[y1];
+    // halo cell k of lane k: its place around the tile, (ex, ey) in [-1, 64]
+    int ex = 0, ey = 0;
+    if (lane < kCaHalo) {
+        ex = pat.ca_halo[lane][0] * 64 + pat.ca_halo[lane][2];
+        ey = pat.ca_halo[lane][1] * 64 + pat.ca_halo[lane][3];
+    }
+    const uint32_t nwarps = gridDim.x * kUnitWarps;
+    for (uint32_t u = blockIdx.x * kUnitWarps + warp; u < units; u += nwarps) {
+        const uint32_t bq = u / W, aq = u - bq * W;
+        const uint2 b = ll.decode(aq, bq);
+        const uint32_t base = u * kUnit;
+        // halo cells (lanes 0..7): their loads are issued first
+        uint32_t hv = 0;
+        if (lane < kCaHalo) {
+            bool p;
+            hv = halo_value<uint8_t, S>(in, b, pat.ca_halo[lane][0], pat.ca_halo[lane][1],
+                                        pat.ca_halo_rank[lane], rb, order, &p);
+        }
+        // 1. compact bits: lane `it` keeps word `it`
+        uint32_t mine = 0;
+#pragma unroll
+        for (int it = 0; it < WORDS; ++it) {
+            const int c = 32 * it + lane;
+            const uint8_t v = c < kUnit ? in[base + c] : 0;
+            const uint32_t w = __ballot_sync(0xffffffffu, v != 0);
+            if (lane == it) mine = w;
+        }
+        const bool alive = hv != 0;
+        __syncwarp();                  // the previous tile's reads of cb are done
+        if (lane < WORDS) cb[lane] = mine;
+        if (lane < WORDS + 3) ob[lane] = 0u;
+        // edge bits and the rows above row 0 and below row 63
+        const uint32_t up_body = __ballot_sync(0xffffffffu, alive && ey == -1 && ex == 0);
+        const uint32_t up_right = __ballot_sync(0xffffffffu, alive && ey == -1 && ex == 64);
+        const uint32_t dn_body0 = __ballot_sync(0xffffffffu, alive && ey == 64 && ex == 0);
+        const uint32_t dn_body1 = __ballot_sync(0xffffffffu, alive && ey == 64 && ex == 1);
+        const uint32_t dn_left = __ballot_sync(0xffffffffu, alive && ey == 64 && ex == -1);
+        const uint32_t l0 = __ballot_sync(0xffffffffu, alive && ey == 0 && ex == -1);
+        const uint32_t r0 = __ballot_sync(0xffffffffu, alive && ey == 0 && ex == 64);
+        const uint32_t r1 = __ballot_sync(0xffffffffu, alive && ey == 1 && ex == 64);
+        __syncwarp();
+        // 2. rows
+        const uint64_t v0 = deposit_row(tc, bits_at(cb, o0), y0);
+        const uint64_t v1 = deposit_row(tc, bits_at(cb, o1), y1);
+        // 3. the rule; only lane 0 has cells beside the left and right edges
+        const bool first = lane == 0, last = lane == 31;
+        const RowSums a = row_sums(v0, first && l0, first && r0);
+        const RowSums c = row_sums(v1, 0u, first && r1);
+        uint64_t u0 = shfl_up64(c.t0), u1 = shfl_up64(c.t1);       // row y0 - 1
+        uint64_t b0 = shfl_down64(a.t0), b1 = shfl_down64(a.t1);   // row y1 + 1
+        if (first) {
+            const RowSums h = row_sums(up_body ? 1ull : 0ull, 0u, up_right != 0u);
+            u0 = h.t0;
+            u1 = h.t1;
+        }
+        if (last) {
+            const RowSums h = row_sums((dn_body0 ? 1ull : 0ull) | (dn_body1 ? 2ull : 0ull),
+                                       dn_left != 0u, 0u);
+            b0 = h.t0;
+            b1 = h.t1;
+        }
+        const uint64_t n0 = life_row(u0, u1, a.d0, a.d1, c.t0, c.t1, v0);
+        const uint64_t n1 = life_row(a.t0, a.t1, c.d0, c.d1, b0, b1, v1);
+        // 4. back to compact bits, then bytes
+        or_bits_at(ob, o0, gather_row(tc, n0, y0));
+        or_bits_at(ob, o1, gather_row(tc, n1, y1));
+        __syncwarp();
+#pragma unroll
+        for (int it = 0; it < WORDS; ++it) {
+            const int cc = 32 * it + lane;
+            if (cc < kUnit) out[base + cc] = (uint8_t)((ob[it] >> lane) & 1u);
+        }
+    }
+}
+
 template <int S>
 __global__ void __launch_bounds__(kUnitThreads)
 compact_diffuse_kernel(const float *__restrict__ in, float *__restrict__ out, int r, int order,
@@ -221,6 +477,14 @@ cudaError_t launch_ca_t(int r, int order, const uint8_t *in, uint8_t *out, cudaS
     const uint32_t total = (uint32_t)pow3i(r);
     const uint64_t units = (total + kUnit - 1) / kUnit;
     unsigned grid = 1;
+    if constexpr (S == 6) {
+        auto k = compact_ca_bits_kernel;
+        cudaError_t e = persistent_grid(k, kUnitThreads, 0, (units + kUnitWarps - 1) / kUnitWarps,
+                                        cfg, &grid, &occ);
+        if (e != cudaSuccess) return e;
+        k<<<grid, kUnitThreads, 0, st>>>(in, out, r, order, total);
+        return cudaGetLastError();
+    }
     auto k = compact_ca_kernel<S>;
     constexpr int smem = StencilSmem<uint8_t, S, kCaHalo, kUnit * 16>::BYTES;
     cudaError_t e = dyn_smem_grid(k, smem, (units + kUnitWarps - 1) / kUnitWarps, cfg, &grid,

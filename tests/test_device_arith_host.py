@@ -376,3 +376,165 @@ def test_tile_base_and_offset_bits_are_disjoint(r, S):
     koff = (ty << rs) | tx
     assert np.array_equal(base + koff, base ^ koff)
     assert np.all(base + koff < np.uint64(1 << (2 * r)))
+
+
+# --------------------------------------------------------------------------
+# Compact layout: the bit-sliced CA step on 64-tiles (compact_ca_bits_kernel)
+# --------------------------------------------------------------------------
+M64 = (1 << 64) - 1
+
+
+def _row_codec():
+    """dep / cmp / row_start as make_row_codec builds them."""
+    dep = [[0] * 256 for _ in range(8)]
+    cmp_ = [[0] * 256 for _ in range(8)]
+    for yl in range(8):
+        for v in range(256):
+            d = c = k = 0
+            for lo in range(8):
+                if lo & yl == 0:
+                    if (v >> k) & 1:
+                        d |= 1 << lo
+                    if (v >> lo) & 1:
+                        c |= 1 << k
+                    k += 1
+            dep[yl][v], cmp_[yl][v] = d, c
+    starts, e = [], 0
+    for y in range(64):
+        starts.append(e)
+        e += 1 << (6 - bin(y).count("1"))
+    return dep, cmp_, starts
+
+
+def _halo_list64():
+    """The CA halo cells of a 64-tile in the order make_compact_pattern
+    discovers them: cells row by row, neighbours by (dy, dx)."""
+    R, halo = 64, []
+    for y in range(R):
+        for x in range(R):
+            if x & y:
+                continue
+            for dy in (-1, 0, 1):
+                for dx in (-1, 0, 1):
+                    if dx == 0 and dy == 0:
+                        continue
+                    nx, ny = x + dx, y + dy
+                    if 0 <= nx < R and 0 <= ny < R:
+                        continue
+                    dbx = -1 if nx < 0 else (1 if nx >= R else 0)
+                    dby = -1 if ny < 0 else (1 if ny >= R else 0)
+                    lx, ly = nx - dbx * R, ny - dby * R
+                    if lx & ly == 0 and (dbx, dby, lx, ly) not in halo:
+                        halo.append((dbx, dby, lx, ly))
+    return halo
+
+
+def _lambda_index(bx, by, rb, order):
+    """Launch index of a block: the inverse of the decode, as lambda_index."""
+    ly = ((1 << rb) - 1) - by
+    q = wx = wy = 0
+    for mu in range(rb, 0, -1):
+        beta = ((bx >> (mu - 1)) & 1) + ((ly >> (mu - 1)) & 1)
+        if order == 1:
+            q = q * 3 + beta
+        elif mu & 1:
+            wy = wy * 3 + beta
+        else:
+            wx = wx * 3 + beta
+    return q if order == 1 else wy * 3 ** (rb // 2) + wx
+
+
+def _compact_bits_ca_tile(state, u, bx, by, rb, order, tabs, halo):
+    """One tile of compact_ca_bits_kernel, word operation by word operation."""
+    dep, cmp_, starts = tabs
+    base = u * 729
+    words = [0] * 26
+    for c in range(729):
+        if state[base + c]:
+            words[c >> 5] |= 1 << (c & 31)
+    alive = {}
+    for k, (dbx, dby, lx, ly) in enumerate(halo):
+        nbx, nby = bx + dbx, by + dby
+        ok = 0 <= nbx < (1 << rb) and 0 <= nby < (1 << rb) and (nbx & nby) == 0
+        v = state[_lambda_index(nbx, nby, rb, order) * 729 + starts[ly] +
+                  _rank_in_row(lx, ly)] if ok else 0
+        alive[(dbx * 64 + lx, dby * 64 + ly)] = bool(v)
+
+    def bits_at(o):
+        k, sh = o >> 5, o & 31
+        w0, w1, w2 = words[k], words[k + 1], words[k + 2]
+        lo = ((w0 | (w1 << 32)) >> sh) & 0xFFFFFFFF
+        hi = ((w1 | (w2 << 32)) >> sh) & 0xFFFFFFFF
+        return lo | (hi << 32)
+
+    def deposit(c, y):
+        yh, yl = y >> 3, y & 7
+        nl = 8 >> bin(yl).count("1")
+        row, sh = 0, 0
+        for hi in range(8):
+            if hi & yh == 0:
+                row |= dep[yl][(c >> sh) & ((1 << nl) - 1)] << (8 * hi)
+                sh += nl
+        return row
+
+    def gather(row, y):
+        yh, yl = y >> 3, y & 7
+        nl = 8 >> bin(yl).count("1")
+        c, sh = 0, 0
+        for hi in range(8):
+            if hi & yh == 0:
+                c |= cmp_[yl][(row >> (8 * hi)) & 0xFF] << sh
+                sh += nl
+        return c
+
+    def maj(a, b, c):
+        return (a & b) | (c & (a ^ b))
+
+    def sums(v, left, right):
+        L = ((v << 1) | left) & M64
+        R = (v >> 1) | (right << 63)
+        return (L ^ v ^ R, maj(L, v, R), L ^ R, L & R)
+
+    rows = [deposit(bits_at(starts[y]), y) for y in range(64)]
+    edge_l = {y: int(alive.get((-1, y), False)) for y in range(-1, 65)}
+    edge_r = {y: int(alive.get((64, y), False)) for y in range(-1, 65)}
+    above = sum(1 << x for x in range(64) if alive.get((x, -1), False))
+    below = sum(1 << x for x in range(64) if alive.get((x, 64), False))
+    ext = {-1: above, 64: below}
+    ext.update(enumerate(rows))
+    s = {y: sums(ext[y], edge_l[y], edge_r[y]) for y in range(-1, 65)}
+    out = [0] * 729
+    for y in range(64):
+        u0, u1 = s[y - 1][0], s[y - 1][1]
+        m0, m1 = s[y][2], s[y][3]
+        b0, b1 = s[y + 1][0], s[y + 1][1]
+        s0, k0 = u0 ^ m0 ^ b0, maj(u0, m0, b0)
+        t, k1 = u1 ^ m1 ^ b1, maj(u1, m1, b1)
+        s1, k2 = t ^ k0, t & k0
+        nxt = s1 & ~(k1 | k2) & (s0 | rows[y]) & M64
+        c = gather(nxt, y)
+        for i in range(1 << (6 - bin(y).count("1"))):
+            out[starts[y] + i] = (c >> i) & 1
+    return out
+
+
+def _rank_in_row(lx, ly):
+    """Rank of member lx among the members of row ly of a 64-tile."""
+    return sum(1 for x in range(lx) if x & ly == 0)
+
+
+@pytest.mark.parametrize("order", [0, 1])
+@pytest.mark.parametrize("r", [6, 7, 8])
+def test_compact_bit_sliced_ca_restated_matches_oracle(r, order):
+    from paper_1706_04552_gb300 import inputs
+    s0 = inputs.ca_seed_grid(r, 0.45, 30 + r)
+    packed = oracle.compact_pack(r, 6, s0, order)
+    want = oracle.compact_ca_step(r, 6, packed, order)
+    rb = r - 6
+    bx, by = oracle.block_map(rb, order)
+    tabs, halo = _row_codec(), _halo_list64()
+    assert len(halo) == 8 and tabs[2][63] == 728
+    got = []
+    for u in range(3 ** rb):
+        got += _compact_bits_ca_tile(packed, u, int(bx[u]), int(by[u]), rb, order, tabs, halo)
+    assert np.array_equal(np.array(got, dtype=np.uint8), want)
