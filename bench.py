@@ -67,7 +67,8 @@ def parse_args():
                         "as 100 sub-averages of 10 consecutive calls; prints one JSON line")
     p.add_argument("--workload", choices=("write", "ca", "diffusion", "ca_fused",
                                           "diffusion_fused", "ca_compact",
-                                          "diffusion_compact"), default="write",
+                                          "diffusion_compact", "ca_compact_fused"),
+                   default="write",
                    help="with --quick: time the level-15 CA or diffusion step (or its "
                         "fused form, k steps per launch) instead of the write pass (the "
                         "form used to profile those kernels)")
@@ -384,7 +385,7 @@ def run_stencil_quick(args, sg, torch, dev, stream):
     r = args.level if args.level else max(s["levels"])
     n = 1 << r
     kind, fused = args.workload.split("_")[0], args.workload.endswith("_fused")
-    compact = args.workload.endswith("_compact")
+    compact = "_compact" in args.workload
     if kind == "ca":
         idx, vals = inputs.ca_seed_sparse(r, s["ca_p"], s["ca_seed"])
         dt = torch.uint8
@@ -401,7 +402,9 @@ def run_stencil_quick(args, sg, torch, dev, stream):
     bufs = [a, torch.zeros_like(a)]
 
     def step():
-        if compact and kind == "ca":
+        if compact and kind == "ca" and fused:
+            sg.compact_ca_steps(bufs[0], bufs[1], r, rho, k, stream=stream)
+        elif compact and kind == "ca":
             sg.compact_ca_step(bufs[0], bufs[1], r, rho, stream=stream)
         elif compact:
             sg.compact_diffuse_step(bufs[0], bufs[1], r, rho, s["alpha"], stream=stream)
@@ -840,6 +843,26 @@ def compact_layout(sg, torch, dev, stream, rw, rs, single, headline_launch_ms):
         rate = cs * total / (ms / 1e3) / 1e9
         one = single.get(f"{kind}_r{rs}_lambda", {}).get("GCells_s")
         fused = single.get(f"{kind}_r{rs}_fused", {}).get("GCells_s")
+        if kind == "ca":
+            # the same sequence as launches of k fused steps
+            k = s["ca_fuse"]
+            chunks = [k] * (total // k) + ([total % k] if total % k else [])
+            pos = [0]
+
+            def launch():
+                sg.compact_ca_steps(bufs[0], bufs[1], rs, rho, chunks[pos[0] % len(chunks)],
+                                    order=order, stream=stream)
+                pos[0] += 1
+                bufs.reverse()
+            for _ in range(len(chunks)):
+                launch()
+            pos[0] = 0
+            fms, _ = time_launches(launch, len(chunks), stream)
+            frate = cs * total / (fms / 1e3) / 1e9
+            out[f"ca_r{rs}_fused"] = {
+                "steps": total, "steps_per_launch": k, "launches": len(chunks),
+                "us_per_step": round(fms * 1e3 / total, 2), "GCells_s": round(frate, 3),
+                "speedup_vs_embedded_fused": round(frate / fused, 3) if fused else None}
         out[f"{kind}_r{rs}"] = {
             "steps": total, "us_per_step": round(ms * 1e3 / total, 2),
             "GCells_s": round(rate, 3),

@@ -438,6 +438,15 @@ SG_API sg_status sg_compact_map_write(int r, int rho, sg_dtype dtype, void *comp
 SG_API sg_status sg_compact_ca_step(int r, int rho, const uint8_t *in, uint8_t *out,
                                     const sg_launch_opts *opts, void *stream);
 
+/* sg_compact_ca_steps -- k CA steps in one launch on compact 0/1 states
+ * (temporal blocking): out = the state after k sg_compact_ca_step calls, bit
+ * for bit.  Each 64-tile is stepped k times in shared memory with the cells
+ * of its neighbouring tiles that k steps can reach.  k in 1 ..
+ * SG_FUSE_MAX (k = 1 is sg_compact_ca_step); rho must be 64 for k > 1
+ * (SG_EUNSUPPORTED otherwise).  in != out. */
+SG_API sg_status sg_compact_ca_steps(int r, int rho, int k, const uint8_t *in, uint8_t *out,
+                                     const sg_launch_opts *opts, void *stream);
+
 /* sg_compact_diffuse_step -- one explicit diffusion step on a compact field:
  * out = pack(sg_diffuse_step(unpack(in))), bit for bit (the same arithmetic
  * per cell).  in != out; alpha finite. */

@@ -28,8 +28,9 @@ __all__ = [
     "sg_launch_stats", "sg_status_str", "sg_abi_version", "sg_device_status",
     "device_status", "sg_wait_selftest", "wait_selftest",
     "sg_compact_pack", "sg_compact_unpack", "sg_compact_map_write", "sg_compact_ca_step",
-    "sg_compact_diffuse_step", "compact_size", "compact_pack", "compact_unpack",
-    "compact_map_write", "compact_ca_step", "compact_diffuse_step",
+    "sg_compact_diffuse_step", "sg_compact_ca_steps", "compact_size", "compact_pack",
+    "compact_unpack", "compact_map_write", "compact_ca_step", "compact_ca_steps",
+    "compact_diffuse_step",
     "CABatch", "Graph", "BatchPlan",
     "map_write", "map_write_host", "map_write_mapped", "sg_map_write_mapped", "ca_step",
     "diffuse_step", "ca_steps", "diffuse_steps",
@@ -165,6 +166,8 @@ def lib() -> ctypes.CDLL:
         L.sg_compact_map_write.restype = i32
         L.sg_compact_ca_step.argtypes = [i32, i32, vp, vp, p_opts, vp]
         L.sg_compact_ca_step.restype = i32
+        L.sg_compact_ca_steps.argtypes = [i32, i32, i32, vp, vp, p_opts, vp]
+        L.sg_compact_ca_steps.restype = i32
         L.sg_compact_diffuse_step.argtypes = [i32, i32, vp, vp, ctypes.c_float, p_opts, vp]
         L.sg_compact_diffuse_step.restype = i32
         L.sg_abi_version.argtypes = []
@@ -588,6 +591,10 @@ def sg_compact_ca_step(r, rho, in_ptr, out_ptr, opts=None, stream=0) -> int:
     return int(lib().sg_compact_ca_step(r, rho, in_ptr, out_ptr, _opts_ref(opts), stream))
 
 
+def sg_compact_ca_steps(r, rho, k, in_ptr, out_ptr, opts=None, stream=0) -> int:
+    return int(lib().sg_compact_ca_steps(r, rho, k, in_ptr, out_ptr, _opts_ref(opts), stream))
+
+
 def sg_compact_diffuse_step(r, rho, in_ptr, out_ptr, alpha, opts=None, stream=0) -> int:
     return int(lib().sg_compact_diffuse_step(r, rho, in_ptr, out_ptr, alpha,
                                              _opts_ref(opts), stream))
@@ -657,6 +664,19 @@ def compact_ca_step(inp, out, r: int, rho: int, order=None, stream=None, ctas_pe
     with _on_device(inp):
         _check("sg_compact_ca_step", sg_compact_ca_step(
             r, rho, inp.data_ptr(), out.data_ptr(), launch_opts(order, None, ctas_per_sm),
+            _stream_handle(inp, stream)))
+    return out
+
+
+def compact_ca_steps(inp, out, r: int, rho: int, k: int, order=None, stream=None,
+                     ctas_per_sm=None):
+    """k CA steps in one launch on compact states (rho = 64 for k > 1)."""
+    import torch
+    _compact_check(inp, r, (torch.uint8,), "in")
+    _compact_check(out, r, (torch.uint8,), "out")
+    with _on_device(inp):
+        _check("sg_compact_ca_steps", sg_compact_ca_steps(
+            r, rho, k, inp.data_ptr(), out.data_ptr(), launch_opts(order, None, ctas_per_sm),
             _stream_handle(inp, stream)))
     return out
 

@@ -405,6 +405,20 @@ sg_status sg_compact_ca_step(int r, int rho, const uint8_t *in, uint8_t *out,
     return finish(launch_compact_ca(r, s, cfg.order, in, out, (cudaStream_t)stream, cfg));
 }
 
+sg_status sg_compact_ca_steps(int r, int rho, int k, const uint8_t *in, uint8_t *out,
+                              const sg_launch_opts *opts, void *stream)
+{
+    int s = 0;
+    LaunchCfg cfg;
+    if (in == nullptr || out == nullptr || in == out) return SG_EINVAL;
+    if (k < 1 || k > SG_FUSE_MAX) return SG_EINVAL;
+    const sg_status st = compact_args(r, rho, opts, &cfg, &s);
+    if (st != SG_OK) return st;
+    if (k == 1) return finish(launch_compact_ca(r, s, cfg.order, in, out, (cudaStream_t)stream, cfg));
+    if (rho != 64) return SG_EUNSUPPORTED;
+    return finish(launch_compact_ca_fused(r, cfg.order, in, out, k, (cudaStream_t)stream, cfg));
+}
+
 sg_status sg_compact_diffuse_step(int r, int rho, const float *in, float *out, float alpha,
                                   const sg_launch_opts *opts, void *stream)
 {

@@ -179,88 +179,6 @@ compact_ca_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int
 // Non-member columns hold 0 in every row word and are dropped by the gather,
 // so the rule can run on them freely.
 // ---------------------------------------------------------------------------
-struct RowCodec {
-    uint8_t dep[8][256];       // block v of a row with y & 7 = yl -> the byte
-    uint8_t cmp[8][256];       // byte of such a row -> its block
-    uint16_t row_start[64];    // compact index (within the tile) of row y's first cell
-};
-
-constexpr int popcount6(int v) { int n = 0; for (int i = 0; i < 6; ++i) n += (v >> i) & 1; return n; }
-
-constexpr RowCodec make_row_codec()
-{
-    RowCodec t{};
-    for (int yl = 0; yl < 8; ++yl)
-        for (int v = 0; v < 256; ++v) {
-            int d = 0, c = 0, k = 0;
-            for (int lo = 0; lo < 8; ++lo)
-                if ((lo & yl) == 0) {
-                    if ((v >> k) & 1) d |= 1 << lo;    // bit k of the block -> column lo
-                    if ((v >> lo) & 1) c |= 1 << k;    // column lo -> bit k of the block
-                    ++k;
-                }
-            t.dep[yl][v] = (uint8_t)d;
-            t.cmp[yl][v] = (uint8_t)c;
-        }
-    int e = 0;
-    for (int y = 0; y < 64; ++y) {
-        t.row_start[y] = (uint16_t)e;
-        e += 1 << (6 - popcount6(y));
-    }
-    return t;
-}
-
-__device__ const RowCodec kRowCodec = make_row_codec();
-static_assert(make_row_codec().row_start[63] == kUnit - 1, "the last row holds one cell");
-
-// The 64 bits of `cb` from bit o on (cb holds two zero guard words).
-__device__ __forceinline__ uint64_t bits_at(const uint32_t *cb, uint32_t o)
-{
-    const uint32_t k = o >> 5, sh = o & 31u;
-    const uint32_t w0 = cb[k], w1 = cb[k + 1], w2 = cb[k + 2];
-    return (uint64_t)__funnelshift_r(w0, w1, sh) | ((uint64_t)__funnelshift_r(w1, w2, sh) << 32);
-}
-
-__device__ __forceinline__ uint64_t deposit_row(const RowCodec &tc, uint64_t c, uint32_t y)
-{
-    const uint32_t yh = y >> 3, yl = y & 7u, nl = 8u >> __popc(yl);
-    const uint32_t lmask = (1u << nl) - 1u;
-    uint64_t row = 0;
-    uint32_t sh = 0;
-#pragma unroll
-    for (uint32_t hi = 0; hi < 8; ++hi)
-        if ((hi & yh) == 0u) {
-            row |= (uint64_t)tc.dep[yl][(uint32_t)(c >> sh) & lmask] << (8 * hi);
-            sh += nl;
-        }
-    return row;
-}
-
-__device__ __forceinline__ uint64_t gather_row(const RowCodec &tc, uint64_t row, uint32_t y)
-{
-    const uint32_t yh = y >> 3, yl = y & 7u, nl = 8u >> __popc(yl);
-    uint64_t c = 0;
-    uint32_t sh = 0;
-#pragma unroll
-    for (uint32_t hi = 0; hi < 8; ++hi)
-        if ((hi & yh) == 0u) {
-            c |= (uint64_t)tc.cmp[yl][(uint32_t)(row >> (8 * hi)) & 0xFFu] << sh;
-            sh += nl;
-        }
-    return c;
-}
-
-// OR the bits of c (those of one row: its other bits are 0) into `ob` at bit o.
-__device__ __forceinline__ void or_bits_at(uint32_t *ob, uint32_t o, uint64_t c)
-{
-    const uint32_t k = o >> 5, sh = o & 31u;
-    const uint32_t lo = (uint32_t)c, hi = (uint32_t)(c >> 32);
-    if (lo << sh) atomicOr(&ob[k], lo << sh);
-    const uint32_t mid = sh ? (lo >> (32 - sh)) | (hi << sh) : hi;
-    if (mid) atomicOr(&ob[k + 1], mid);
-    if (sh && (hi >> (32 - sh))) atomicOr(&ob[k + 2], hi >> (32 - sh));
-}
-
 __device__ __forceinline__ uint64_t maj3(uint64_t a, uint64_t b, uint64_t c)
 {
     return (a & b) | (c & (a ^ b));
@@ -473,7 +391,6 @@ cudaError_t launch_ca_t(int r, int order, const uint8_t *in, uint8_t *out, cudaS
                         const LaunchCfg &cfg)
 {
     static std::atomic<int> occ{0};
-    static std::atomic<uint64_t> attr{0};
     const uint32_t total = (uint32_t)pow3i(r);
     const uint64_t units = (total + kUnit - 1) / kUnit;
     unsigned grid = 1;
@@ -483,14 +400,15 @@ cudaError_t launch_ca_t(int r, int order, const uint8_t *in, uint8_t *out, cudaS
                                         cfg, &grid, &occ);
         if (e != cudaSuccess) return e;
         k<<<grid, kUnitThreads, 0, st>>>(in, out, r, order, total);
-        return cudaGetLastError();
+    } else {
+        static std::atomic<uint64_t> attr{0};
+        auto k = compact_ca_kernel<S>;
+        constexpr int smem = StencilSmem<uint8_t, S, kCaHalo, kUnit * 16>::BYTES;
+        cudaError_t e = dyn_smem_grid(k, smem, (units + kUnitWarps - 1) / kUnitWarps, cfg, &grid,
+                                      &occ, &attr);
+        if (e != cudaSuccess) return e;
+        k<<<grid, kUnitThreads, smem, st>>>(in, out, r, order, total);
     }
-    auto k = compact_ca_kernel<S>;
-    constexpr int smem = StencilSmem<uint8_t, S, kCaHalo, kUnit * 16>::BYTES;
-    cudaError_t e = dyn_smem_grid(k, smem, (units + kUnitWarps - 1) / kUnitWarps, cfg, &grid,
-                                  &occ, &attr);
-    if (e != cudaSuccess) return e;
-    k<<<grid, kUnitThreads, smem, st>>>(in, out, r, order, total);
     return cudaGetLastError();
 }
 

@@ -257,3 +257,11 @@ def test_compact_entries_validate_before_launch(L):
     assert sg.sg_compact_map_write(8, 16, u8, FAKE, 2, 1, opts) == sg.SG_EUNSUPPORTED
     assert sg.sg_compact_ca_step(8, 16, FAKE, FAKE + 4096, sg.launch_opts(order=2)) == sg.SG_EINVAL
     assert sg.compact_size(16) == 43046721
+
+
+def test_compact_fused_steps_validate_before_launch(L):
+    assert sg.sg_compact_ca_steps(8, 64, 0, FAKE, FAKE + 4096) == sg.SG_EINVAL
+    assert sg.sg_compact_ca_steps(8, 64, sg.FUSE_MAX + 1, FAKE, FAKE + 4096) == sg.SG_EINVAL
+    assert sg.sg_compact_ca_steps(8, 64, 4, FAKE, FAKE) == sg.SG_EINVAL
+    assert sg.sg_compact_ca_steps(8, 32, 4, FAKE, FAKE + 4096) == sg.SG_EUNSUPPORTED
+    assert sg.sg_compact_ca_steps(5, 64, 4, FAKE, FAKE + 4096) == sg.SG_EINVAL      # rho > n

@@ -194,3 +194,57 @@ def test_compact_full_size_matches_embedded():
     c = torch.empty(3 ** rw, dtype=torch.uint8, device=DEV)
     sg.compact_map_write(c, rw, 64, "hash", 1)
     assert torch.equal(c, sg.compact_pack(g, torch.empty_like(c), rw, 64))
+
+
+FUSED_KS = (2, 3, 4, 5, 8, 9, 15, 16)
+
+
+@pytest.mark.parametrize("order", ORDERS)
+@pytest.mark.parametrize("r,p", [(6, 0.5), (7, 0.45), (8, 0.4), (10, 0.3)])
+def test_compact_fused_ca_matches_oracle(orc, r, p, order):
+    oid = sg.ORDERS[order]
+    s0 = inputs.ca_seed_grid(r, p, 50 + r)
+    ref = [orc.compact_pack(r, 6, s0, oid)]
+    for _ in range(max(FUSED_KS)):
+        ref.append(orc.compact_ca_step(r, 6, ref[-1], oid))
+    a = dev1(ref[0])
+    for k in FUSED_KS:
+        b = torch.zeros_like(a)
+        sg.compact_ca_steps(a, b, r, 64, k, order=order)
+        assert np.array_equal(host1(b), ref[k]), k
+    assert np.array_equal(host1(a), ref[0])             # the input is left as it was
+
+
+def test_compact_fused_ca_equals_single_steps():
+    r = 11
+    s0 = sg.compact_pack(to_dev(inputs.ca_seed_grid(r, 0.35, 8)),
+                         torch.empty(3 ** r, dtype=torch.uint8, device=DEV), r, 64)
+    for k in (2, 7, 16):
+        a, b = s0.clone(), torch.zeros_like(s0)
+        for _ in range(k):
+            sg.compact_ca_step(a, b, r, 64)
+            a, b = b, a
+        f = torch.zeros_like(s0)
+        sg.compact_ca_steps(s0, f, r, 64, k)
+        assert torch.equal(a, f), k
+
+
+@pytest.mark.slow
+def test_compact_fused_ca_full_size_matches_embedded_fused():
+    # the stencil workload's CA sequence (256 steps from the seeded state) as
+    # 16 launches of 16 fused compact steps equals the embedded fused run, packed
+    w = workloads.STENCILS
+    r = max(w["levels"])
+    n = 1 << r
+    idx, vals = inputs.ca_seed_sparse(r, w["ca_p"], w["ca_seed"])
+    a = torch.zeros(n * n, dtype=torch.uint8, device=DEV)
+    a[torch.from_numpy(idx).to(DEV)] = torch.from_numpy(vals).to(DEV)
+    ca = sg.compact_pack(a, torch.empty(3 ** r, dtype=torch.uint8, device=DEV), r, 64)
+    cb = torch.empty_like(ca)
+    b = torch.zeros_like(a)
+    for _ in range(w["ca_steps"] // 16):
+        sg.ca_steps(a, b, r, 64, 16)
+        a, b = b, a
+        sg.compact_ca_steps(ca, cb, r, 64, 16)
+        ca, cb = cb, ca
+    assert torch.equal(ca, sg.compact_pack(a, torch.empty_like(ca), r, 64))
