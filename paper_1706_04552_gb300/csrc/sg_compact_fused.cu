@@ -65,7 +65,7 @@ template <int KH> __device__ __forceinline__ const HaloRuns<KH> &halo_runs()
 }
 
 template <int KH>
-__global__ void __launch_bounds__(kUnitThreads, 4)
+__global__ void __launch_bounds__(kUnitThreads, 6)
 compact_ca_fused_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int r,
                         int order, uint32_t total, int k)
 {
