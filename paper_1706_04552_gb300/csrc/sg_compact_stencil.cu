@@ -227,7 +227,7 @@ __device__ __forceinline__ uint64_t shfl_down64(uint64_t v)
     return (uint64_t)lo | ((uint64_t)hi << 32);
 }
 
-__global__ void __launch_bounds__(kUnitThreads, 4)
+__global__ void __launch_bounds__(kUnitThreads, 5)
 compact_ca_bits_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int r, int order,
                        uint32_t total)
 {
