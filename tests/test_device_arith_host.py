@@ -538,3 +538,83 @@ def test_compact_bit_sliced_ca_restated_matches_oracle(r, order):
     for u in range(3 ** rb):
         got += _compact_bits_ca_tile(packed, u, int(bx[u]), int(by[u]), rb, order, tabs, halo)
     assert np.array_equal(np.array(got, dtype=np.uint8), want)
+
+
+def _halo_runs(KH):
+    """make_halo_runs: the runs of the 9 neighbour tiles a KH-step light cone
+    reaches, and their word offsets."""
+    _, _, starts = _row_codec()
+
+    def start(y):
+        return 729 if y >= 64 else starts[y]
+    lo, hi, word, w = [], [], [], 0
+    for s in range(9):
+        dtx, dty = s % 3 - 1, s // 3 - 1
+        y0 = 64 - KH if dty < 0 else 0
+        y1 = KH if dty > 0 else 64
+        if dtx < 0 and y1 > 16:
+            y1 = 16
+        y1 = max(y1, y0)
+        lo.append(start(y0))
+        hi.append(start(y1))
+        word.append(w)
+        w += (hi[-1] - lo[-1] + 31) // 32
+    return lo, hi, word, w
+
+
+def _member_bits4(y):
+    return (0x135F >> (4 * (y & 3))) & 0xF
+
+
+@pytest.mark.parametrize("KH", [4, 8, 16])
+@pytest.mark.parametrize("order", [0, 1])
+def test_compact_fused_staging_restated_matches_the_grid(KH, order):
+    # compact_ca_fused_kernel's staging: runs of the neighbour tiles packed to
+    # bits, then every staged 16-column chunk deposited through the row codec,
+    # must give the chunk's bits read straight off the embedded grid
+    from paper_1706_04552_gb300 import inputs
+    r = 8
+    n = 1 << r
+    grid = inputs.ca_seed_grid(r, 0.5, 70 + KH)
+    packed = oracle.compact_pack(r, 6, grid, order)
+    rb = r - 6
+    bx_all, by_all = oracle.block_map(rb, order)
+    dep, _, starts = _row_codec()
+    lo, hi, word, nwords = _halo_runs(KH)
+    for u in range(3 ** rb):
+        bx, by = int(bx_all[u]), int(by_all[u])
+        cb = [0] * (nwords + 2)
+        for s in range(9):
+            nbx, nby = bx + s % 3 - 1, by + s // 3 - 1
+            ok = 0 <= nbx < (1 << rb) and 0 <= nby < (1 << rb) and (nbx & nby) == 0
+            q = _lambda_index(nbx, nby, rb, order) if ok else None
+            for e in range(lo[s], hi[s]):
+                if q is not None and packed[q * 729 + e]:
+                    bit = (e - lo[s])
+                    cb[word[s] + bit // 32] |= 1 << (bit % 32)
+        x0, y0 = bx * 64, by * 64
+        for row in range(64 + 2 * KH):
+            for h in range(6):
+                x, y = x0 - 16 + 16 * h, y0 - KH + row
+                want = 0
+                if 0 <= x < n and 0 <= y < n and (x & y) == 0:
+                    for lo16 in range(16):
+                        if grid[y, x + lo16]:
+                            want |= 1 << lo16
+                    s = ((y >> 6) - by + 1) * 3 + ((x >> 6) - bx + 1)
+                    lx, ly = x & 63, y & 63
+                    cx, n16 = lx >> 4, 16 >> bin(ly & 15).count("1")
+                    rank = bin(_member_bits4(ly >> 4) & ((1 << cx) - 1)).count("1")
+                    e = starts[ly] + rank * n16
+                    assert lo[s] <= e and e + n16 <= hi[s], (u, row, h)
+                    o = word[s] * 32 + (e - lo[s])
+                    bits = ((cb[o >> 5] | (cb[(o >> 5) + 1] << 32)) >> (o & 31)) & 0xFFFFFFFF
+                    yl = ly & 7
+                    n8 = 8 >> bin(yl).count("1")
+                    m8 = (1 << n8) - 1
+                    got = dep[yl][bits & m8]
+                    if (ly & 8) == 0:
+                        got |= dep[yl][(bits >> n8) & m8] << 8
+                    assert got == want, (u, row, h, got, want)
+                elif 0 <= x < n and 0 <= y < n:
+                    assert not grid[y, x:x + 16].any()
