@@ -248,3 +248,39 @@ def test_compact_fused_ca_full_size_matches_embedded_fused():
         sg.compact_ca_steps(ca, cb, r, 64, 16)
         ca, cb = cb, ca
     assert torch.equal(ca, sg.compact_pack(a, torch.empty_like(ca), r, 64))
+
+
+@pytest.mark.slow
+def test_compact_steps_at_the_largest_level():
+    # level 16 (43 M cells; the embedded buffers are 4.3 GB u8 / 17.2 GB f32):
+    # the compact CA (single and fused) and diffusion steps equal the packed
+    # embedded steps bit for bit
+    r, rho = 16, 64
+    n = 1 << r
+    idx, vals = inputs.ca_seed_sparse(r, 0.3, 5)
+    a = torch.zeros(n * n, dtype=torch.uint8, device=DEV)
+    a[torch.from_numpy(idx).to(DEV)] = torch.from_numpy(vals).to(DEV)
+    ca = sg.compact_pack(a, torch.empty(3 ** r, dtype=torch.uint8, device=DEV), r, rho)
+    b = torch.zeros_like(a)
+    sg.ca_steps(a, b, r, rho, 4)
+    want = sg.compact_pack(b, torch.empty_like(ca), r, rho)
+    got = torch.empty_like(ca)
+    sg.compact_ca_steps(ca, got, r, rho, 4)
+    assert torch.equal(got, want)
+    c1, c2 = ca.clone(), torch.empty_like(ca)
+    for _ in range(4):
+        sg.compact_ca_step(c1, c2, r, rho)
+        c1, c2 = c2, c1
+    assert torch.equal(c1, want)
+    del a, b, ca, want, got, c1, c2
+    torch.cuda.empty_cache()
+    idx, vals = inputs.uniform_sparse(r, 5)
+    u = torch.zeros(n * n, dtype=torch.float32, device=DEV)
+    u[torch.from_numpy(idx).to(DEV)] = torch.from_numpy(vals).to(DEV)
+    cu = sg.compact_pack(u, torch.empty(3 ** r, dtype=torch.float32, device=DEV), r, rho)
+    v = torch.zeros_like(u)
+    sg.diffuse_step(u, v, r, rho, 0.2, "lambda")
+    want = sg.compact_pack(v, torch.empty_like(cu), r, rho)
+    got = torch.empty_like(cu)
+    sg.compact_diffuse_step(cu, got, r, rho, 0.2)
+    assert torch.equal(got, want)
