@@ -60,6 +60,10 @@ def parse_args():
     p.add_argument("--quick", action="store_true",
                    help="headline launches only (no clock soak, extras, e2e or CPU "
                         "baseline): the form used under ncu")
+    p.add_argument("--write-sweep", action="store_true",
+                   help="the map-and-write sweep instead of the headline: levels 8..16, "
+                        "uint8 and float32, rho 8..64, lambda vs bounding box; prints one "
+                        "JSON line")
     p.add_argument("--paper-sweep", action="store_true",
                    help="the paper's experiment instead of the headline: write a constant "
                         "into the gasket of a zero uint8 matrix for r = 0..16, rho = 1..32, "
@@ -632,6 +636,83 @@ def paper_sweep(args):
             "points": rows, "best_per_level": best}
 
 
+def write_sweep(args):
+    """The map-and-write sweep over levels 8..16, uint8 and float32 grids,
+    rho = 8, 16, 32, 64, lambda (the headline's intra-tile map and walking
+    order) against the bounding box, hash values seed 1, both with whole-tile
+    fill stores where a tile row holds at least 16 bytes and per-cell stores
+    otherwise.  Each point: GPU time per launch from CUDA-graph replays of 10
+    launches (the L2 flushed before each timed replay), GCells/s, launched
+    against useful cell slots, and touched 128-byte lines per second."""
+    import torch
+    import paper_1706_04552_gb300 as sg
+    from paper_1706_04552_gb300 import workloads
+    sg.lib()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    sw, hw = workloads.WRITE_SWEEP, workloads.WRITE_HEADLINE
+    l2 = int(getattr(torch.cuda.get_device_properties(dev), "L2_cache_size", 0)) or (129 << 20)
+    flush = torch.empty(2 * l2, dtype=torch.uint8, device=dev)
+    peak, peak_kind = measured_peak()
+    rows = []
+    for dtype, elem, tdt in (("u8", 1, torch.uint8), ("f32", 4, torch.float32)):
+        for r in sw["levels"]:
+            n = 1 << r
+            g = torch.zeros(n * n, dtype=tdt, device=dev)
+            lines = touched_bytes(r, elem, 128)
+            for rho in sw["rhos"]:
+                if rho > n:
+                    continue
+                store = "fill" if rho * elem >= 16 else "scatter"
+                for name, mapk in (("lambda", hw["map"]), ("bbox", "bbox")):
+                    cap = torch.cuda.Stream(dev)
+                    call = lambda st: sg.map_write(g, r, rho, mapk, "hash", hw["seed"], st,
+                                                   order=hw["order"], store=store)
+                    call(torch.cuda.current_stream(dev))
+                    torch.cuda.synchronize(dev)
+                    graph = torch.cuda.CUDAGraph()
+                    with torch.cuda.graph(graph, stream=cap):
+                        for _ in range(10):
+                            call(torch.cuda.current_stream(dev))
+                    graph.replay()
+                    torch.cuda.synchronize(dev)
+                    st = torch.cuda.current_stream(dev)
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    vals = []
+                    for k in range(5):
+                        flush.fill_(k & 0xFF)
+                        e0.record(st)
+                        graph.replay()
+                        e1.record(st)
+                        e1.synchronize()
+                        vals.append(e0.elapsed_time(e1) * 1e3 / 10)
+                    us = statistics.median(vals)
+                    launched, useful = sg.launch_stats(r, rho, mapk)
+                    rows.append({"dtype": dtype, "r": r, "rho": rho, "map": mapk, "store": store,
+                                 "us": round(us, 2), "GCells_s": round(3 ** r / us / 1e3, 2),
+                                 "launched_slots": launched, "useful_cells": useful,
+                                 "line_GBps": round(lines / us / 1e3, 1),
+                                 "frac": round(lines / us / 1e3 / peak, 3)})
+                    del graph
+            del g
+            torch.cuda.empty_cache()
+    best = {}
+    for dtype in ("u8", "f32"):
+        for r in sw["levels"]:
+            pts = [p for p in rows if p["dtype"] == dtype and p["r"] == r]
+            bl = min((p for p in pts if p["map"] != "bbox"), key=lambda p: p["us"])
+            bb = min((p for p in pts if p["map"] == "bbox"), key=lambda p: p["us"])
+            best[f"{dtype}_r{r}"] = {"lambda_rho": bl["rho"], "lambda_us": bl["us"],
+                                     "lambda_GCells_s": bl["GCells_s"], "lambda_frac": bl["frac"],
+                                     "bbox_rho": bb["rho"], "bbox_us": bb["us"],
+                                     "speedup_best_vs_best": round(bb["us"] / bl["us"], 3)}
+    return {"experiment": "map-and-write sweep: levels 8..16, uint8 and float32, rho 8..64, "
+                          "lambda vs bounding box, hash values seed 1",
+            "protocol": "median of 5 CUDA-graph replays of 10 launches, L2 flushed before each",
+            "peak_GBps": peak, "peak_kind": peak_kind, "points": rows, "best_per_level": best}
+
+
 def serving_workload():
     """Continuous batching of CA-step requests (Poisson arrivals, 500 resident
     gaskets of levels 6..15) with batched launches and, on the same trace,
@@ -1062,6 +1143,9 @@ def main():
         return 0
     if args.paper_sweep:
         print(json.dumps(paper_sweep(args)))
+        return 0
+    if args.write_sweep:
+        print(json.dumps(write_sweep(args)))
         return 0
     grp = Group()
     try:
