@@ -160,13 +160,8 @@ compact_ca_kernel(const uint8_t *__restrict__ in, uint8_t *__restrict__ out, int
 }
 
 // ---------------------------------------------------------------------------
-// CA, rho = 64: bit-sliced rows.
-//
-// Row y of a 64-tile holds its gasket cells at the columns x with
-// x & y == 0.  Split x = 8*hi + lo: they sit in the bytes hi with
-// hi & (y >> 3) == 0 and, inside each, at the bits lo with lo & (y & 7) == 0.
-// In compact order the row is one run of 2^(6 - popc(y)) elements, made of
-// one block of 2^(3 - popc(y & 7)) elements per such byte.  A warp takes one
+// CA, rho = 64: bit-sliced rows (the row codec of sg_compact.cuh moves a
+// tile row between its compact run and a 64-bit word).  A warp takes one
 // tile (729 elements) at a time:
 //   1. ballots turn the 729 states (0 / 1) into 23 words of compact bits;
 //   2. each lane deposits rows 2*lane and 2*lane + 1 into 64-bit row words,
