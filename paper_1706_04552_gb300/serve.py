@@ -25,6 +25,14 @@ request, so every result is still the plain per-gasket step sequence.
 mode="per_gasket" runs the same scheduler with one single-gasket launch per
 active gasket per iteration instead of the batched launch, for comparison.
 
+Failures are contained on the host.  A launch that the library refuses
+(an SGError from its C ABI) fails the head requests of the gaskets it was
+for: nothing ran, their states stay as they were, and the rest of the
+iteration and of the trace go on.  A gasket that cannot be brought onto the
+device fails the requests queued for it and stays in host memory.  Each
+failure is recorded with its error and the steps of the request that had
+already run; a failed request's steps that ran stay applied.
+
 Every gasket's state follows the plain per-gasket sequence of CA steps in
 arrival order of its requests, so each result equals stepping the gasket
 alone; tests check that against single-gasket runs and the CPU oracle.
@@ -132,6 +140,7 @@ class Server:
         self.used = 0
         self.evictions = 0
         self.loads = 0
+        self.failures = []                # per failed request: (request, gasket, steps run, error)
         cnt = len(self.gaskets)
         if cfg.fuse < 1 or cfg.fuse > sg.FUSE_MAX:
             raise ValueError(f"fuse must be 1..{sg.FUSE_MAX}")
@@ -214,44 +223,59 @@ class Server:
     def _steps_for(self, g):
         return steps_this_iteration(g.queue[0][1], self.ks)
 
-    def _step(self, active):
-        """Advance every active gasket; returns the number of launches."""
+    def _launch(self, group, k):
+        """One launch of k steps for `group` (one gasket in per-gasket mode).
+        Raises SGError when the library refuses it; nothing has run then."""
         sg = self.sg
         if self.cfg.mode == "per_gasket":
-            for g in active:
-                sg.ca_step(g.cur, g.nxt, g.level, min(self.cfg.rho, 1 << g.level), "lambda",
-                           self.stream)
-            return len(active)
+            g = group[0]
+            sg.ca_step(g.cur, g.nxt, g.level, min(self.cfg.rho, 1 << g.level), "lambda",
+                       self.stream)
+            return
         L = sg.lib()
+        for j, g in enumerate(group):
+            self._lv[j] = g.level
+            self._pa[j] = g.cur.data_ptr()
+            self._pb[j] = g.nxt.data_ptr()
+        ws = self.ws[self.ks.index(k)]
+        st = L.sg_batch_ca_plan(len(group), self._lv.ctypes.data, self._pa.ctypes.data,
+                                self._pb.ctypes.data, self.cfg.rho, ws.data_ptr(), ws.numel(),
+                                ctypes.byref(self._plan), self.stream.cuda_stream)
+        sg._check("sg_batch_ca_plan", int(st))
+        sg._check("sg_batch_ca_steps", int(L.sg_batch_ca_steps(
+            ctypes.byref(self._plan), 0, k, None, self.stream.cuda_stream)))
+
+    def _step(self, active):
+        """Advance every active gasket.  Returns (launches, gaskets whose
+        launch was refused, with the error)."""
+        failed = {}
+        if self.cfg.mode == "per_gasket":
+            groups = [([g], 1) for g in active]
+        else:
+            groups = [([g for g in active if g.advance == k], k) for k in self.ks]
         launches = 0
-        for slot, k in enumerate(self.ks):
-            group = [g for g in active if g.advance == k]
+        for group, k in groups:
             if not group:
                 continue
-            for j, g in enumerate(group):
-                self._lv[j] = g.level
-                self._pa[j] = g.cur.data_ptr()
-                self._pb[j] = g.nxt.data_ptr()
-            ws = self.ws[slot]
-            st = L.sg_batch_ca_plan(len(group), self._lv.ctypes.data, self._pa.ctypes.data,
-                                    self._pb.ctypes.data, self.cfg.rho, ws.data_ptr(),
-                                    ws.numel(), ctypes.byref(self._plan),
-                                    self.stream.cuda_stream)
-            sg._check("sg_batch_ca_plan", int(st))
-            sg._check("sg_batch_ca_steps", int(L.sg_batch_ca_steps(
-                ctypes.byref(self._plan), 0, k, None, self.stream.cuda_stream)))
-            launches += 1
-        return launches
+            try:
+                self._launch(group, k)
+                launches += 1
+            except self.sg.SGError as e:
+                for g in group:
+                    failed[g.gid] = str(e)
+        return launches, failed
 
     # ----------------------------------------------------------------- loop
     def run(self, trace, on_complete=None):
         """Serve a trace (arrival s, gasket, steps).  on_complete(req, gasket)
         is called right after a request's last step (state in gasket.cur).
-        Returns per-request arrival/completion times and counters."""
+        Returns per-request arrival/completion times, which requests failed,
+        and counters."""
         t_arr, g_id, k_steps = trace
         nreq = len(t_arr)
         done_at = np.full(nreq, np.nan)
         start_at = np.full(nreq, np.nan)
+        failed = np.zeros(nreq, dtype=bool)
         busy = 0.0
         iters = 0
         launches = 0
@@ -275,20 +299,48 @@ class Server:
                 continue
             waiting = list(pending.values())
             protect = set(pending)
-            active = [g for g in waiting if self._make_resident(g, protect)]
+            active = []
+            for g in waiting:
+                try:
+                    ok = self._make_resident(g, protect)
+                except Exception as e:          # the copy in failed: its requests fail
+                    now = time.perf_counter() - t0
+                    while g.queue:
+                        req, left = g.queue.pop(0)
+                        self.failures.append((req, g.gid, int(k_steps[req]) - left, str(e)))
+                        failed[req] = True
+                        done_at[req] = now
+                        remaining -= 1
+                    del pending[g.gid]
+                    continue
+                if ok:
+                    active.append(g)
             if not active:
-                raise RuntimeError("a requested gasket does not fit the device budget")
+                if pending:
+                    raise RuntimeError("a requested gasket does not fit the device budget")
+                continue
             self.tick += 1
             for g in active:
                 g.advance = self._steps_for(g) if self.cfg.mode == "batched" else 1
             tb = time.perf_counter()
-            launches += self._step(active)
+            n_launch, refused = self._step(active)
+            launches += n_launch
             self.stream.synchronize()
             te = time.perf_counter()
             busy += te - tb
             iters += 1
             tdone = te - t0
             for g in active:
+                if g.gid in refused:           # nothing ran: its head request fails
+                    req, left = g.queue.pop(0)
+                    self.failures.append((req, g.gid, int(k_steps[req]) - left, refused[g.gid]))
+                    failed[req] = True
+                    done_at[req] = tdone
+                    remaining -= 1
+                    g.last_use = self.tick
+                    if not g.queue:
+                        del pending[g.gid]
+                    continue
                 g.cur, g.nxt = g.nxt, g.cur
                 g.last_use = self.tick
                 g.steps_done += g.advance
@@ -309,7 +361,7 @@ class Server:
         lat = done_at - t_arr
         return {"requests": nreq, "wall_s": wall, "iterations": iters, "launches": launches,
                 "busy_s": busy, "cell_steps": cells, "latency_s": lat, "arrival_s": t_arr,
-                "evictions": self.evictions, "loads": self.loads}
+                "failed": failed, "evictions": self.evictions, "loads": self.loads}
 
     def state_of(self, gid):
         """Current state of gasket gid (host numpy copy)."""
@@ -325,6 +377,7 @@ def summarize(res, cfg: ServeConfig):
     return {
         "mode": cfg.mode if cfg.fuse == 1 else f"{cfg.mode}, up to {cfg.fuse} fused steps",
         "requests": int(res["requests"]),
+        "failed": int(res["failed"].sum()),
         "offered_rate_rps": cfg.rate,
         "throughput_rps": round(res["requests"] / res["wall_s"], 1),
         "cell_steps_per_s_G": round(res["cell_steps"] / res["wall_s"] / 1e9, 4),

@@ -83,3 +83,66 @@ def test_serve_fused_with_evictions_to_host(orc):
     cfg = ServeConfig(gaskets=32, level_max=10, rate=3000.0, duration=0.2, seed=10,
                       budget_bytes=3 << 20, fuse=8)
     _serve_and_check(orc, cfg, expect_evictions=True)
+
+
+def test_serve_contains_host_side_failures(orc):
+    # failures injected on the host: one batched launch is refused (an SGError
+    # from the C ABI, as a bad plan would give) and one gasket's copy onto the
+    # device fails.  The affected requests are reported failed; every other
+    # request still equals stepping its gasket alone through the steps that
+    # actually ran, and the trace is served to the end.
+    cfg = ServeConfig(gaskets=24, level_max=9, rate=3000.0, duration=0.15, seed=13,
+                      budget_bytes=1 << 20, fuse=4)
+    server = Server(cfg)
+    initial = [g.host.clone() for g in server.gaskets]
+    trace = make_trace(cfg)
+    t, gid, k = trace
+    with_reqs = sorted(set(int(x) for x in gid))
+    launch_victim = with_reqs[0]
+    load_victim = next(i for i in reversed(with_reqs)
+                       if not server.gaskets[i].resident and i != launch_victim)
+    fired = {"launch": 0, "load": 0}
+    launch, make_resident = server._launch, server._make_resident
+
+    def failing_launch(group, kk):
+        if fired["launch"] == 0 and any(g.gid == launch_victim and g.steps_done > 0
+                                        for g in group):
+            fired["launch"] += 1
+            raise sg.SGError("sg_batch_ca_steps", sg.SG_ECUDA, "injected")
+        return launch(group, kk)
+
+    def failing_resident(g, protect):
+        if fired["load"] == 0 and g.gid == load_victim and not g.resident:
+            fired["load"] += 1
+            raise RuntimeError("injected copy failure")
+        return make_resident(g, protect)
+
+    server._launch = failing_launch
+    server._make_resident = failing_resident
+    snap = {}
+
+    def on_complete(req, g):
+        snap[req] = g.cur.clone()
+
+    res = server.run(trace, on_complete)
+    torch.cuda.synchronize()
+    assert fired == {"launch": 1, "load": 1}
+    failed = res["failed"]
+    ran = {req: steps for req, _, steps, _ in server.failures}
+    assert failed.sum() == len(server.failures) >= 2
+    assert set(np.nonzero(failed)[0]) == set(ran)
+    assert all("injected" in err for _, _, _, err in server.failures)
+    assert len(snap) + failed.sum() == len(t)
+    assert not np.isnan(res["latency_s"]).any()
+    for i, g in enumerate(server.gaskets):
+        reqs = [j for j in range(len(t)) if gid[j] == i]
+        a = initial[i].cuda()
+        b = torch.zeros_like(a)
+        rho = min(cfg.rho, 1 << g.level)
+        for j in reqs:
+            for _ in range(ran.get(j, int(k[j]))):
+                sg.ca_step(a, b, g.level, rho, "lambda")
+                a, b = b, a
+            if not failed[j]:
+                torch.cuda.synchronize()
+                assert torch.equal(a, snap[j]), (i, j)
