@@ -26,9 +26,11 @@
  *   SG_MAP_BBOX           bounding box: the identity map over all n_b^2
  *                         tiles, every cell tests membership (Section I).
  *   SG_MAP_LAMBDA_LUT     lambda for tiles; inside a tile only the 3^s member
- *                         slots are visited, in row-major order, through an
- *                         offset table shared by the block (Section III-D,
- *                         Shared Lookup Table).  Write pass only.
+ *                         slots are visited, in the row-major order of the
+ *                         paper's shared lookup table (Section III-D, Shared
+ *                         Lookup Table); each thread computes the entries it
+ *                         visits once and keeps them in registers.  Write
+ *                         pass only.
  *   SG_MAP_LAMBDA_UNROLL  lambda for tiles; inside a tile each thread applies
  *                         lambda again to its own index (Section III-D,
  *                         Further Unrolling).  Write pass only.
