@@ -371,7 +371,9 @@ def run_ours(args, grp: Group):
     # result over the link, correct for any grid content; the fill path (the
     # grid 0 off the gasket, as here) reads nothing and is reported beside it
     out["e2e"] = dict(mapped if mapped["value"] >= copy["value"] else copy)
-    out["e2e_paths"] = {"mapped": mapped, "mapped_fill": mapped_fill, "copy": copy}
+    compact_mapped = measure_e2e_compact_mapped(sg, torch, dev, stream, w, grp, 20)
+    out["e2e_paths"] = {"mapped": mapped, "mapped_fill": mapped_fill, "copy": copy,
+                        "compact_mapped": compact_mapped}
     if grp.rank == 0 and grp.world == 1 and not args.no_cpu:
         out["cpu_baseline"] = cpu_baseline(w)
         try:
@@ -988,6 +990,35 @@ def measure_e2e_mapped(sg, torch, dev, stream, w, grp, steps, store="staged"):
             "path": (f"grid in pinned host memory, written in place by the kernel over the "
                      f"host link ({m['map']}, rho {m['rho']}, {m['order']}, {store} "
                      f"stores); bytes per step = {how}")}
+
+
+def measure_e2e_compact_mapped(sg, torch, dev, stream, w, grp, steps):
+    """The write pass in the compact layout (the 3^r gasket cells, tiles in
+    launch order) written straight into pinned host memory over the host link
+    (sg_compact_map_write_mapped): one contiguous run of whole sectors per
+    pass, nothing read.  A different storage of the same cells and values as
+    the embedded grid."""
+    from paper_1706_04552_gb300 import workloads
+    r = w["r"]
+    rho = workloads.COMPACT["rho"]
+    host = torch.zeros(3 ** r, dtype=torch.uint8, pin_memory=True)
+
+    def step():
+        sg.compact_map_write_mapped(host, r, rho, w["value"], w["seed"],
+                                    order=workloads.COMPACT["order"], stream=stream)
+
+    step()
+    torch.cuda.synchronize(dev)
+    grp.barrier()
+    ms, _ = time_launches(step, steps, stream)
+    ms = grp.max(ms)
+    del host
+    return {"value": round(grp.world * 3 ** r * steps / (ms / 1e3) / 1e9, 4), "unit": UNIT,
+            "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 3 ** r,
+            "steps": steps, "ms_per_step": round(ms / steps, 3),
+            "path": (f"compact layout (gasket cells only, rho {rho}) written by the kernel "
+                     f"straight into pinned host memory over the host link; bytes per step "
+                     f"= the 3^{r} cells, one contiguous run")}
 
 
 def measure_e2e(sg, torch, dev, stream, w, grp, steps):

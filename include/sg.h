@@ -435,6 +435,16 @@ SG_API sg_status sg_compact_map_write(int r, int rho, sg_dtype dtype, void *comp
                                       sg_value_kind value_kind, uint64_t value_or_seed,
                                       const sg_launch_opts *opts, void *stream);
 
+/* sg_compact_map_write_mapped -- sg_compact_map_write on a compact array
+ * in page-locked host memory mapped into the device's address space
+ * (cudaHostAlloc / cudaHostRegister with mapping; on Grace-Blackwell the
+ * kernel writes it over NVLink-C2C).  The array is written once, as whole
+ * consecutive sectors; nothing is read.  Other memory: SG_EINVAL before any
+ * launch.  The values are in host memory once `stream` has completed. */
+SG_API sg_status sg_compact_map_write_mapped(int r, int rho, sg_dtype dtype, void *host_compact,
+                                             sg_value_kind value_kind, uint64_t value_or_seed,
+                                             const sg_launch_opts *opts, void *stream);
+
 /* sg_compact_ca_step -- one gasket-restricted B3/S23 step on compact 0/1
  * states: out = pack(sg_ca_step(unpack(in))), cell for cell.  in != out. */
 SG_API sg_status sg_compact_ca_step(int r, int rho, const uint8_t *in, uint8_t *out,

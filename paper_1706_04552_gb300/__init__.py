@@ -30,7 +30,7 @@ __all__ = [
     "sg_compact_pack", "sg_compact_unpack", "sg_compact_map_write", "sg_compact_ca_step",
     "sg_compact_diffuse_step", "sg_compact_ca_steps", "compact_size", "compact_pack",
     "compact_unpack", "compact_map_write", "compact_ca_step", "compact_ca_steps",
-    "compact_diffuse_step",
+    "compact_diffuse_step", "sg_compact_map_write_mapped", "compact_map_write_mapped",
     "CABatch", "Graph", "BatchPlan",
     "map_write", "map_write_host", "map_write_mapped", "sg_map_write_mapped", "ca_step",
     "diffuse_step", "ca_steps", "diffuse_steps",
@@ -166,6 +166,8 @@ def lib() -> ctypes.CDLL:
         L.sg_compact_map_write.restype = i32
         L.sg_compact_ca_step.argtypes = [i32, i32, vp, vp, p_opts, vp]
         L.sg_compact_ca_step.restype = i32
+        L.sg_compact_map_write_mapped.argtypes = [i32, i32, i32, vp, i32, u64, p_opts, vp]
+        L.sg_compact_map_write_mapped.restype = i32
         L.sg_compact_ca_steps.argtypes = [i32, i32, i32, vp, vp, p_opts, vp]
         L.sg_compact_ca_steps.restype = i32
         L.sg_compact_diffuse_step.argtypes = [i32, i32, vp, vp, ctypes.c_float, p_opts, vp]
@@ -591,6 +593,13 @@ def sg_compact_ca_step(r, rho, in_ptr, out_ptr, opts=None, stream=0) -> int:
     return int(lib().sg_compact_ca_step(r, rho, in_ptr, out_ptr, _opts_ref(opts), stream))
 
 
+def sg_compact_map_write_mapped(r, rho, dtype, host_ptr, value_kind, value_or_seed, opts=None,
+                                stream=0) -> int:
+    return int(lib().sg_compact_map_write_mapped(r, rho, dtype, host_ptr, value_kind,
+                                                 value_or_seed & (2**64 - 1), _opts_ref(opts),
+                                                 stream))
+
+
 def sg_compact_ca_steps(r, rho, k, in_ptr, out_ptr, opts=None, stream=0) -> int:
     return int(lib().sg_compact_ca_steps(r, rho, k, in_ptr, out_ptr, _opts_ref(opts), stream))
 
@@ -655,6 +664,30 @@ def compact_map_write(compact, r: int, rho: int, value="hash", value_or_seed=1, 
             r, rho, _dtype_id(compact), compact.data_ptr(), vk, value_or_seed,
             launch_opts(order, None, ctas_per_sm), _stream_handle(compact, stream)))
     return compact
+
+
+def compact_map_write_mapped(host_compact, r: int, rho: int, value="hash", value_or_seed=1,
+                             order=None, stream=None, device=None):
+    """Compact write pass straight into a pinned CPU tensor of 3^r elements
+    (sg_compact_map_write_mapped).  Returns without synchronising."""
+    import torch
+    if host_compact.is_cuda or not host_compact.is_contiguous() or not host_compact.is_pinned():
+        raise TypeError("host_compact: expected a contiguous pinned CPU tensor")
+    if host_compact.dtype not in (torch.uint8, torch.float32):
+        raise TypeError("host_compact: expected uint8 or float32")
+    if host_compact.numel() != 3 ** r:
+        raise ValueError(f"host_compact: expected 3^{r} elements")
+    vk = VALUES[value] if isinstance(value, str) else int(value)
+    dev = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+    if stream is None:
+        st = torch.cuda.current_stream(dev).cuda_stream
+    else:
+        st = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    with torch.cuda.device(dev):
+        _check("sg_compact_map_write_mapped", sg_compact_map_write_mapped(
+            r, rho, _dtype_id(host_compact), host_compact.data_ptr(), vk, value_or_seed,
+            launch_opts(order, None, None), st))
+    return host_compact
 
 
 def compact_ca_step(inp, out, r: int, rho: int, order=None, stream=None, ctas_per_sm=None):

@@ -394,6 +394,36 @@ sg_status sg_compact_map_write(int r, int rho, sg_dtype dtype, void *compact,
                                        value_or_seed, (cudaStream_t)stream, cfg));
 }
 
+sg_status sg_compact_map_write_mapped(int r, int rho, sg_dtype dtype, void *host_compact,
+                                      sg_value_kind value_kind, uint64_t value_or_seed,
+                                      const sg_launch_opts *opts, void *stream)
+{
+    int s = 0;
+    LaunchCfg cfg;
+    if (dtype != SG_U8 && dtype != SG_F32) return SG_EINVAL;
+    if (value_kind < SG_VAL_CONST || value_kind > SG_VAL_HASH) return SG_EINVAL;
+    if (host_compact == nullptr) return SG_EINVAL;
+    const sg_status st = compact_args(r, rho, opts, &cfg, &s);
+    if (st != SG_OK) return st;
+    // page-locked host memory mapped into the device's address space only
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, host_compact) != cudaSuccess) {
+        cudaGetLastError();                           // reset the runtime's last error
+        set_last_error_message("sg_compact_map_write_mapped: pointer attributes unavailable");
+        return SG_EINVAL;
+    }
+    if (attr.type != cudaMemoryTypeHost || attr.devicePointer == nullptr) {
+        set_last_error_message("sg_compact_map_write_mapped: not page-locked host memory "
+                               "mapped into the device");
+        return SG_EINVAL;
+    }
+    const int elem = dtype == SG_U8 ? 1 : 4;
+    if (!aligned(attr.devicePointer, (uintptr_t)elem)) return SG_EINVAL;
+    return finish(launch_compact_write(r, s, cfg.order, elem, (int)value_kind,
+                                       attr.devicePointer, value_or_seed, (cudaStream_t)stream,
+                                       cfg));
+}
+
 sg_status sg_compact_ca_step(int r, int rho, const uint8_t *in, uint8_t *out,
                              const sg_launch_opts *opts, void *stream)
 {

@@ -265,3 +265,15 @@ def test_compact_fused_steps_validate_before_launch(L):
     assert sg.sg_compact_ca_steps(8, 64, 4, FAKE, FAKE) == sg.SG_EINVAL
     assert sg.sg_compact_ca_steps(8, 32, 4, FAKE, FAKE + 4096) == sg.SG_EUNSUPPORTED
     assert sg.sg_compact_ca_steps(5, 64, 4, FAKE, FAKE + 4096) == sg.SG_EINVAL      # rho > n
+
+
+def test_compact_mapped_write_refuses_memory_it_cannot_check(L):
+    import numpy as np
+    buf = np.zeros(3 ** 8, dtype=np.uint8)
+    u8 = sg.DTYPES["u8"]
+    assert sg.sg_compact_map_write_mapped(8, 16, u8, 0, 2, 1) == sg.SG_EINVAL
+    assert sg.sg_compact_map_write_mapped(8, 16, u8, buf.ctypes.data, 2, 1) == sg.SG_EINVAL
+    assert sg.sg_compact_map_write_mapped(8, 16, u8, buf.ctypes.data, 3, 1) == sg.SG_EINVAL
+    assert sg.sg_compact_map_write_mapped(17, 16, u8, buf.ctypes.data, 2, 1) == sg.SG_EINVAL
+    assert sg.sg_compact_map_write_mapped(8, 16, u8, buf.ctypes.data, 2, 1,
+                                          sg.launch_opts(store="fill")) == sg.SG_EUNSUPPORTED

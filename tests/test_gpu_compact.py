@@ -284,3 +284,18 @@ def test_compact_steps_at_the_largest_level():
     got = torch.empty_like(cu)
     sg.compact_diffuse_step(cu, got, r, rho, 0.2)
     assert torch.equal(got, want)
+
+
+@pytest.mark.parametrize("dtype", ["u8", "f32"])
+@pytest.mark.parametrize("r", [6, 9, 12])
+def test_compact_write_into_pinned_host_memory(orc, r, dtype):
+    np_dt = np.uint8 if dtype == "u8" else np.float32
+    grid = np.zeros((1 << r, 1 << r), dtype=np_dt)
+    orc.map_write(r, grid, orc.VAL_HASH, 4)
+    for rho in (16, 64):
+        h = torch.full((3 ** r,), 7, dtype=torch.uint8 if dtype == "u8" else torch.float32
+                       ).pin_memory()
+        sg.compact_map_write_mapped(h, r, rho, "hash", 4)
+        torch.cuda.synchronize()
+        want = orc.compact_pack(r, rho.bit_length() - 1, grid)
+        assert np.array_equal(h.numpy().view(np.uint8), want.view(np.uint8)), rho
