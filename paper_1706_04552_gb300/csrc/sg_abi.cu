@@ -421,7 +421,7 @@ sg_status sg_compact_map_write_mapped(int r, int rho, sg_dtype dtype, void *host
     if (!aligned(attr.devicePointer, (uintptr_t)elem)) return SG_EINVAL;
     return finish(launch_compact_write(r, s, cfg.order, elem, (int)value_kind,
                                        attr.devicePointer, value_or_seed, (cudaStream_t)stream,
-                                       cfg));
+                                       cfg, /*wide=*/true));
 }
 
 sg_status sg_compact_ca_step(int r, int rho, const uint8_t *in, uint8_t *out,

@@ -280,8 +280,10 @@ cudaError_t launch_compact_pack(int r, int s, int order, int elem, const void *g
                                 void *compact, cudaStream_t st, const LaunchCfg &cfg);
 cudaError_t launch_compact_unpack(int r, int s, int order, int elem, const void *compact,
                                   void *grid, cudaStream_t st, const LaunchCfg &cfg);
+// wide: whole aligned 16-byte stores (a destination in host memory)
 cudaError_t launch_compact_write(int r, int s, int order, int elem, int vk, void *compact,
-                                 uint64_t vs, cudaStream_t st, const LaunchCfg &cfg);
+                                 uint64_t vs, cudaStream_t st, const LaunchCfg &cfg,
+                                 bool wide = false);
 cudaError_t launch_compact_ca(int r, int s, int order, const uint8_t *in, uint8_t *out,
                               cudaStream_t st, const LaunchCfg &cfg);
 cudaError_t launch_compact_diffuse(int r, int s, int order, const float *in, float *out,

@@ -74,12 +74,28 @@ compact_move_kernel(const T *__restrict__ src, T *__restrict__ dst, int r, int o
     }
 }
 
-template <typename T, int VK, int S>
+// Byte offset of the per-warp staging buffers of the write kernel, and their
+// size: a unit's values plus room to align them like their destination.
+template <int S> __host__ __device__ constexpr int write_stage_offset()
+{
+    return IoSmem<S>::BYTES + ((kUnit * 2 + 15) / 16) * 16;
+}
+template <typename T> __host__ __device__ constexpr int write_stage_bytes()
+{
+    return (kUnit * (int)sizeof(T) + 16 + 15) / 16 * 16;
+}
+
+// WIDE: stage each unit in shared memory and store it in whole aligned
+// 16-byte chunks (for a destination in host memory, across the host link);
+// otherwise every lane stores its values directly (device memory, where the
+// staging's extra registers cost more than the wide stores save).
+template <typename T, int VK, int S, bool WIDE>
 __global__ void __launch_bounds__(kUnitThreads)
 compact_write_kernel(T *__restrict__ compact, int r, int order, uint32_t total, uint64_t vs)
 {
     using M = IoSmem<S>;
     constexpr int G = M::G;
+    constexpr int STAGE = write_stage_bytes<T>();
     extern __shared__ __align__(16) unsigned char smem[];
     // per position: the value-key offset of the cell within its tile (the
     // same in every tile), and the tile within the unit
@@ -94,6 +110,7 @@ compact_write_kernel(T *__restrict__ compact, int r, int order, uint32_t total, 
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     uint32_t *vbase = reinterpret_cast<uint32_t *>(smem + M::TABLE + warp * M::WARP);
+    unsigned char *stage = smem + write_stage_offset<S>() + warp * STAGE;
     const int rb = r - S;
     const uint32_t ntiles = total / CompactPattern<S>::C, units = (total + kUnit - 1) / kUnit;
     const CellValue<T, VK> cv{vs * kGoldenGamma, (uint32_t)vs};
@@ -114,18 +131,41 @@ compact_write_kernel(T *__restrict__ compact, int r, int order, uint32_t total, 
         __syncwarp();
         const uint32_t base = u * kUnit;
         const uint32_t cnt = min((uint32_t)kUnit, total - base);
-        T *out = compact + base;
+        if constexpr (!WIDE) {
+            T *dst = compact + base;
+#pragma unroll 4
+            for (uint32_t c = lane; c < cnt; c += 32) {
+                const uint32_t vb = G == 1 ? vbase[0] : vbase[tile_of[c]];
+                dst[c] = cv(vb, koff[c]);
+            }
+            continue;
+        }
+        // the values go to shared memory at the destination's offset within
+        // 16 bytes, then out as whole aligned 16-byte chunks (byte stores
+        // only for the unit's ragged ends)
+        unsigned char *out = reinterpret_cast<unsigned char *>(compact + base);
+        const uint32_t lead = (uint32_t)(reinterpret_cast<uintptr_t>(out) & 15u);
+        T *sv = reinterpret_cast<T *>(stage + lead);
 #pragma unroll 4
         for (uint32_t c = lane; c < cnt; c += 32) {
             const uint32_t vb = G == 1 ? vbase[0] : vbase[tile_of[c]];
-            out[c] = cv(vb, koff[c]);
+            sv[c] = cv(vb, koff[c]);
         }
+        __syncwarp();
+        const uint32_t nb = cnt * (uint32_t)sizeof(T);
+        const uint32_t head = min((16u - lead) & 15u, nb);
+        const uint32_t chunks = (nb - head) / 16u, body_end = head + 16u * chunks;
+        for (uint32_t i = lane; i < head; i += 32) out[i] = stage[lead + i];
+        for (uint32_t k = lane; k < chunks; k += 32)
+            *reinterpret_cast<uint4 *>(out + head + 16u * k) =
+                *reinterpret_cast<const uint4 *>(stage + lead + head + 16u * k);
+        for (uint32_t i = body_end + lane; i < nb; i += 32) out[i] = stage[lead + i];
     }
 }
 
-template <int S> constexpr int write_smem_bytes()
+template <typename T, int S, bool WIDE> constexpr int write_smem_bytes()
 {
-    return IoSmem<S>::BYTES + ((kUnit * 2 + 15) / 16) * 16;
+    return write_stage_offset<S>() + (WIDE ? kUnitWarps * write_stage_bytes<T>() : 0);
 }
 
 template <typename T, int S, int MODE>
@@ -146,7 +186,7 @@ cudaError_t launch_move_t(int r, int order, const T *src, T *dst, cudaStream_t s
     return cudaGetLastError();
 }
 
-template <typename T, int VK, int S>
+template <typename T, int VK, int S, bool WIDE>
 cudaError_t launch_write_t(int r, int order, T *compact, uint64_t vs, cudaStream_t st,
                            const LaunchCfg &cfg)
 {
@@ -155,8 +195,8 @@ cudaError_t launch_write_t(int r, int order, T *compact, uint64_t vs, cudaStream
     const uint32_t total = (uint32_t)pow3i(r);
     const uint64_t units = (total + kUnit - 1) / kUnit;
     unsigned grid = 1;
-    auto k = compact_write_kernel<T, VK, S>;
-    constexpr int smem = write_smem_bytes<S>();
+    auto k = compact_write_kernel<T, VK, S, WIDE>;
+    constexpr int smem = write_smem_bytes<T, S, WIDE>();
     cudaError_t e = dyn_smem_grid(k, smem, (units + kUnitWarps - 1) / kUnitWarps, cfg, &grid,
                                   &occ, &attr);
     if (e != cudaSuccess) return e;
@@ -185,23 +225,24 @@ cudaError_t launch_move(int r, int s, int order, const T *src, T *dst, cudaStrea
 #undef CALL
 }
 
-template <typename T, int VK>
+template <typename T, int VK, bool WIDE>
 cudaError_t launch_write_vk(int r, int s, int order, T *compact, uint64_t vs, cudaStream_t st,
                             const LaunchCfg &cfg)
 {
-#define CALL(S) launch_write_t<T, VK, S>(r, order, compact, vs, st, cfg)
+#define CALL(S) launch_write_t<T, VK, S, WIDE>(r, order, compact, vs, st, cfg)
     SG_COMPACT_S_SWITCH(s, CALL)
 #undef CALL
 }
 
-template <typename T>
+template <typename T, bool WIDE>
 cudaError_t launch_write_dt(int r, int s, int order, int vk, T *compact, uint64_t vs,
                             cudaStream_t st, const LaunchCfg &cfg)
 {
     switch (vk) {
-    case kValConst: return launch_write_vk<T, kValConst>(r, s, order, compact, vs, st, cfg);
-    case kValLinear31: return launch_write_vk<T, kValLinear31>(r, s, order, compact, vs, st, cfg);
-    case kValHash: return launch_write_vk<T, kValHash>(r, s, order, compact, vs, st, cfg);
+    case kValConst: return launch_write_vk<T, kValConst, WIDE>(r, s, order, compact, vs, st, cfg);
+    case kValLinear31:
+        return launch_write_vk<T, kValLinear31, WIDE>(r, s, order, compact, vs, st, cfg);
+    case kValHash: return launch_write_vk<T, kValHash, WIDE>(r, s, order, compact, vs, st, cfg);
     default: return cudaErrorInvalidValue;
     }
 }
@@ -227,11 +268,14 @@ cudaError_t launch_compact_unpack(int r, int s, int order, int elem, const void 
 }
 
 cudaError_t launch_compact_write(int r, int s, int order, int elem, int vk, void *compact,
-                                 uint64_t vs, cudaStream_t st, const LaunchCfg &cfg)
+                                 uint64_t vs, cudaStream_t st, const LaunchCfg &cfg, bool wide)
 {
     if (elem == 1)
-        return launch_write_dt<uint8_t>(r, s, order, vk, (uint8_t *)compact, vs, st, cfg);
-    return launch_write_dt<float>(r, s, order, vk, (float *)compact, vs, st, cfg);
+        return wide ? launch_write_dt<uint8_t, true>(r, s, order, vk, (uint8_t *)compact, vs, st, cfg)
+                    : launch_write_dt<uint8_t, false>(r, s, order, vk, (uint8_t *)compact, vs, st,
+                                                      cfg);
+    return wide ? launch_write_dt<float, true>(r, s, order, vk, (float *)compact, vs, st, cfg)
+                : launch_write_dt<float, false>(r, s, order, vk, (float *)compact, vs, st, cfg);
 }
 
 }  // namespace sg
