@@ -618,3 +618,80 @@ def test_compact_fused_staging_restated_matches_the_grid(KH, order):
                     assert got == want, (u, row, h, got, want)
                 elif 0 <= x < n and 0 <= y < n:
                     assert not grid[y, x:x + 16].any()
+
+
+# --------------------------------------------------------------------------
+# Compact layout: the compile-time neighbour tables (make_compact_pattern)
+# --------------------------------------------------------------------------
+HOST_SRC = os.path.join(os.path.dirname(__file__), "host_src", "dump_compact_tables.cu")
+
+
+@pytest.fixture(scope="module")
+def compact_tables(tmp_path_factory):
+    """The tables as the library's header computes them, printed by a host
+    program built with nvcc from that header (skipped without nvcc)."""
+    import shutil
+    import subprocess
+    nvcc = shutil.which("nvcc") or ("/usr/local/cuda/bin/nvcc"
+                                    if os.path.exists("/usr/local/cuda/bin/nvcc") else None)
+    if nvcc is None:
+        pytest.skip("nvcc not available")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    exe = str(tmp_path_factory.mktemp("ct") / "dump_ct")
+    subprocess.run([nvcc, "-gencode=arch=compute_103a,code=sm_103a", "-std=c++17", "-O1",
+                    "-I", os.path.join(root, "include"),
+                    "-I", os.path.join(root, "paper_1706_04552_gb300", "csrc"),
+                    HOST_SRC, "-o", exe], check=True)
+    out = subprocess.run([exe], check=True, capture_output=True, text=True).stdout
+    t = {}
+    for line in out.splitlines():
+        kind, *vals = line.split()
+        t.setdefault(kind, []).append(tuple(int(v) for v in vals))
+    return t
+
+
+@pytest.mark.parametrize("S", range(0, 7))
+def test_compact_neighbour_tables_match_brute_force(compact_tables, S):
+    R = 1 << S
+    members = [(x, y) for y in range(R) for x in range(R) if x & y == 0]
+    rank = {c: i for i, c in enumerate(members)}
+    pos = {e: (x, y) for s, e, x, y in compact_tables["pos"] if s == S}
+    assert [pos[e] for e in range(len(members))] == members
+    ca_halo = {h: v for s, h, *v in compact_tables["cahalo"] if s == S}
+    df_halo = {h: v for s, h, *v in compact_tables["dfhalo"] if s == S}
+    assert len(ca_halo) == 8 and len(df_halo) == 4
+
+    def expect(x, y, dx, dy, halo):
+        nx, ny = x + dx, y + dy
+        if 0 <= nx < R and 0 <= ny < R:
+            return rank[(nx, ny)] if nx & ny == 0 else 0xFFFF
+        dbx = -1 if nx < 0 else (1 if nx >= R else 0)
+        dby = -1 if ny < 0 else (1 if ny >= R else 0)
+        lx, ly = nx - dbx * R, ny - dby * R
+        if lx & ly:
+            return 0xFFFF
+        hs = [h for h, v in halo.items() if v[:4] == [dbx, dby, lx, ly]]
+        assert len(hs) == 1 and halo[hs[0]][4] == rank[(lx, ly)]
+        return 0x8000 | hs[0]
+
+    ca = {(e, k): v for s, e, k, v in compact_tables["ca"] if s == S}
+    df = {(e, k): v for s, e, k, v in compact_tables["df"] if s == S}
+    deg = {e: v for s, e, v in compact_tables["deg"] if s == S}
+    d8 = [(dx, dy) for dy in (-1, 0, 1) for dx in (-1, 0, 1) if (dx, dy) != (0, 0)]
+    d4 = [(-1, 0), (1, 0), (0, -1), (0, 1)]
+    used_ca, used_df = set(), set()
+    for e, (x, y) in enumerate(members):
+        for k, (dx, dy) in enumerate(d8):
+            v = expect(x, y, dx, dy, ca_halo)
+            assert ca[(e, k)] == v, (S, e, k)
+            if v != 0xFFFF and v & 0x8000:
+                used_ca.add(v & 0x7FFF)
+        inside = 0
+        for k, (dx, dy) in enumerate(d4):
+            v = expect(x, y, dx, dy, df_halo)
+            assert df[(e, k)] == v, (S, e, k)
+            if v != 0xFFFF and v & 0x8000:
+                used_df.add(v & 0x7FFF)
+            inside += v < 0x8000
+        assert deg[e] == inside
+    assert used_ca == set(range(8)) and used_df == set(range(4))
