@@ -695,3 +695,13 @@ def test_compact_neighbour_tables_match_brute_force(compact_tables, S):
             inside += v < 0x8000
         assert deg[e] == inside
     assert used_ca == set(range(8)) and used_df == set(range(4))
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_inverse_lambda_restated_inverts_the_block_map(order):
+    # lambda_index (the compact kernels' halo lookup) read back into base-3
+    # digits gives every block's launch index, at every level up to 11
+    for rb in range(0, 12):
+        bx, by = oracle.block_map(rb, order)
+        for q in range(3 ** rb):
+            assert _lambda_index(int(bx[q]), int(by[q]), rb, order) == q, (rb, q)
