@@ -11,9 +11,10 @@ no L2 flush is needed between passes.
 Beside the headline the line carries: the roofline of the write kernel
 (touched 128-byte lines per launch / CUDA-event launch time, against the
 measured HBM copy bandwidth), the bounding-box map on the same workload, the
-float32 grid, the level-15 CA and diffusion steps, the end-to-end rate through
-host buffers, SM clocks sampled during the run, and the CPU oracle timed on
-the host cores.
+float32 grid, the level-15 CA and diffusion steps (single and fused), the
+compact layout's write pass and steps, the level sweep, the batched CA and
+the continuous-batching server, the end-to-end rate through host buffers,
+SM clocks sampled during the run, and the CPU oracle timed on the host cores.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
