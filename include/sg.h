@@ -382,7 +382,11 @@ SG_API sg_status sg_batch_ca_autotune_fused(int count, const int *levels, uint8_
  *   - More than SG_NOALLOC_MAX_GASKETS gaskets: SG_EINVAL, with the reason in
  *     sg_last_error_string().
  *   - The first call on a device looks up the array's device address (with
- *     that device current); make that first call before any stream capture.
+ *     that device current) and keeps it for the life of the process; calls
+ *     after a cudaDeviceReset of that device are not supported.
+ *   - Each call copies the work list from a host buffer inside libsg that the
+ *     next call overwrites, so it returns SG_EUNSUPPORTED while `stream` is
+ *     being captured, before it copies or launches anything.
  *   - Every call shares the one array, and it keeps the last call's contents.
  *     Calls whose copies and kernels can overlap on the GPU (for example on
  *     two streams without ordering between them) race on it: order them on

@@ -627,8 +627,20 @@ extern "C" sg_status sg_batch_ca_step_noalloc(int count, const int *levels,
     }
     prefix[count] = (uint32_t)total;
 
+    // The copy below reads `img`, a host buffer that the next call on this
+    // thread overwrites, so a graph captured around it would replay whatever
+    // that buffer holds then: refuse while `stream` is capturing.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing((cudaStream_t)stream, &cap);
+    if (e != cudaSuccess) return cuda_fail(e);
+    if (cap != cudaStreamCaptureStatusNone) {
+        set_last_error_message("sg_batch_ca_step_noalloc: the stream is being captured; the "
+                               "work list is copied from a host buffer that the next call "
+                               "reuses");
+        return SG_EUNSUPPORTED;
+    }
     void *scratch = nullptr;
-    cudaError_t e = noalloc_scratch(&scratch);
+    e = noalloc_scratch(&scratch);
     if (e != cudaSuccess) return cuda_fail(e);
     // The whole work list the step reads is rewritten on `stream` first, so
     // nothing in the array has to start at zero.  (Pageable source: the copy

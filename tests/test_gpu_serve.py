@@ -146,3 +146,66 @@ def test_serve_contains_host_side_failures(orc):
             if not failed[j]:
                 torch.cuda.synchronize()
                 assert torch.equal(a, snap[j]), (i, j)
+
+
+def _full_size_sample(levels):
+    """Gaskets whose every request is checked at the full serving size: every
+    gasket of level >= 11 (the seeded draw of 500 gaskets holds one each at
+    levels 12, 13 and 15, five at 11 and none at 14), and the first three of
+    each level 6..10."""
+    pick = [i for i, r in enumerate(levels) if r >= 11]
+    for r in range(6, 11):
+        pick += [i for i, lr in enumerate(levels) if lr == r][:3]
+    return sorted(pick)
+
+
+@pytest.mark.parametrize("mode,fuse", [("batched", 1), ("batched", 16), ("per_gasket", 1)])
+def test_serve_full_size_config_bit_exact(orc, mode, fuse):
+    # The serving configuration itself: 500 resident gaskets of levels 6..15
+    # drawn toward small levels (seed 3), Poisson arrivals at 2000 req/s for
+    # 2 s (seed 4), 1-32 CA steps per request, 40 GB device budget.  For a
+    # sample spread over every level present, every completed request's state
+    # is kept and compared bit for bit with the gasket stepped alone through
+    # the same requests; sampled gaskets of level <= 10 are also compared
+    # with the CPU oracle after their last request.
+    cfg = ServeConfig(mode=mode, fuse=fuse)
+    assert (cfg.gaskets, cfg.level_min, cfg.level_max, cfg.rate, cfg.duration,
+            cfg.budget_bytes) == (500, 6, 15, 2000.0, 2.0, 40 << 30)
+    server = Server(cfg)
+    levels = [g.level for g in server.gaskets]
+    sample = set(_full_size_sample(levels))
+    assert len(sample) >= 20 and {15, 13, 12, 11} <= {levels[i] for i in sample}
+    initial = {i: server.gaskets[i].host.clone() for i in sample}
+    trace = make_trace(cfg)
+    t, gid, k = trace
+    snap = {}
+
+    def on_complete(req, g):
+        if g.gid in sample:
+            snap[req] = g.cur.clone()
+
+    res = server.run(trace, on_complete)
+    torch.cuda.synchronize()
+    assert not res["failed"].any()
+    s = summarize(res, cfg)
+    assert s["requests"] == len(t) > 3000
+    checked = 0
+    for i in sorted(sample):
+        g = server.gaskets[i]
+        reqs = [j for j in range(len(t)) if gid[j] == i]
+        a = initial[i].cuda()
+        b = torch.zeros_like(a)
+        rho = min(cfg.rho, 1 << g.level)
+        for j in reqs:
+            for _ in range(int(k[j])):
+                sg.ca_step(a, b, g.level, rho, "lambda")
+                a, b = b, a
+            torch.cuda.synchronize()
+            assert torch.equal(a, snap.pop(j)), (i, g.level, j)
+            checked += 1
+        if g.level <= 10 and reqs:
+            n = 1 << g.level
+            want = orc.ca_steps(g.level, initial[i].numpy().reshape(n, n),
+                                int(sum(k[j] for j in reqs)))
+            assert np.array_equal(server.state_of(i), want), (i, g.level)
+    assert checked >= 100 and not snap

@@ -74,3 +74,41 @@ def test_noalloc_rejects_more_gaskets_than_its_array(L):
     st = L.sg_batch_ca_step_noalloc(n, lv, pa, pb, 16, 0, None, None)
     assert st == sg.SG_EINVAL
     assert b"SG_NOALLOC_MAX_GASKETS" in L.sg_last_error_string()
+
+
+def test_noalloc_full_array_then_a_smaller_call(L):
+    # 1024 gaskets of level 4 (one 16 x 16 tile each) fill the array exactly;
+    # the next call, with fewer gaskets of other levels, must not read what
+    # the first call left behind it.  Both are compared with the regular step.
+    rho = 16
+    stream = torch.cuda.current_stream().cuda_stream
+    for levels, seed in (([4] * MAX_GASKETS, 31), ([7, 5, 9, 4, 6], 32)):
+        a1, b1 = _batch(levels, seed)
+        a2, b2 = _batch(levels, seed)
+        regular = sg.CABatch(levels, a1, b1, rho=rho)
+        lv = (ctypes.c_int * len(levels))(*levels)
+        pa, pb = _ptrs(a2), _ptrs(b2)
+        for parity in (0, 1):
+            regular.step(parity)
+            st = L.sg_batch_ca_step_noalloc(len(levels), lv, pa, pb, rho, parity, None, stream)
+            assert st == sg.SG_OK, sg.sg_status_str(st)
+        torch.cuda.synchronize()
+        for i in range(len(levels)):
+            assert torch.equal(a1[i], a2[i]) and torch.equal(b1[i], b2[i]), (len(levels), i)
+
+
+def test_noalloc_refuses_while_the_stream_is_captured(L):
+    levels = [6, 7]
+    a, b = _batch(levels, 33)
+    lv = (ctypes.c_int * 2)(*levels)
+    pa, pb = _ptrs(a), _ptrs(b)
+    before = [t.clone() for t in b]
+    side = torch.cuda.Stream()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=side):
+        st = L.sg_batch_ca_step_noalloc(2, lv, pa, pb, 16, 0, None,
+                                        torch.cuda.current_stream().cuda_stream)
+    assert st == sg.SG_EUNSUPPORTED
+    assert b"captured" in L.sg_last_error_string()
+    torch.cuda.synchronize()
+    assert all(torch.equal(x, y) for x, y in zip(b, before))
