@@ -475,7 +475,10 @@ SG_API sg_status sg_compact_diffuse_step(int r, int rho, const float *in, float 
  * device.  Kernels with bounded waits (SG_STORE_TMA, sg_wait_selftest) record
  * a wait that gave up there instead of spinning; the call synchronises
  * `stream` and returns SG_ETIMEOUT if any kernel recorded one since the last
- * call, else SG_OK (or SG_ECUDA if the status could not be read).
+ * call, else SG_OK (or SG_ECUDA if the status could not be read).  The fused
+ * diffusion kernel for rho = 32, 64 records a unit whose live chunks exceed
+ * the bound its registers are sized for (proved on the host never to happen);
+ * that is reported as SG_EUNSUPPORTED.
  */
 SG_API sg_status sg_device_status(void *stream);
 

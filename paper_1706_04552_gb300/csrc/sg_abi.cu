@@ -468,7 +468,13 @@ sg_status sg_device_status(void *stream)
     int status = 0;
     cudaError_t e = read_device_status(&status, (cudaStream_t)stream);
     if (e != cudaSuccess) return fail_cuda(e);
-    return status == kDevOk ? SG_OK : SG_ETIMEOUT;
+    if (status == kDevOk) return SG_OK;
+    if (status == kDevOverflow) {
+        set_last_error_message("sg_device_status: a fused diffusion unit had more live chunks "
+                               "than its bound; that unit was not written");
+        return SG_EUNSUPPORTED;
+    }
+    return SG_ETIMEOUT;
 }
 
 sg_status sg_wait_selftest(int blocks, int arrive, uint64_t limit_ns, void *stream)

@@ -17,7 +17,11 @@ constexpr uint64_t kWaitLimitNs = 2000000000ull;   // 2 s
 // Device status word (one per device, defined in sg_tma.cu): 0 = fine,
 // otherwise the first error a kernel recorded.  Kernels receive its address;
 // sg_device_status() reads and clears it.
-enum : int { kDevOk = 0, kDevTimeout = 1 };
+enum : int { kDevOk = 0, kDevTimeout = 1,
+              // a fused diffusion unit listed more live chunks than its
+              // register slots hold (a bound checked on the host; the unit is
+              // skipped rather than run wrong)
+              kDevOverflow = 2 };
 
 __device__ __forceinline__ void record_device_error(int *status, int code)
 {

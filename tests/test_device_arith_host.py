@@ -705,3 +705,105 @@ def test_inverse_lambda_restated_inverts_the_block_map(order):
         bx, by = oracle.block_map(rb, order)
         for q in range(3 ** rb):
             assert _lambda_index(int(bx[q]), int(by[q]), rb, order) == q, (rb, q)
+
+
+# ---------------------------------------------------------------------------
+# The warp-per-unit fused diffusion kernel (csrc/sg_fused.cu): its closed form
+# for a region row's live chunks, and the bound on live chunks per region that
+# sizes its register slots.
+# ---------------------------------------------------------------------------
+FUSED_SRC = os.path.join(os.path.dirname(__file__), os.pardir, "paper_1706_04552_gb300", "csrc",
+                         "sg_fused.cu")
+
+
+def _region_row_mask(x0, y, n, hc):
+    """region_row_mask<HC> as the kernel computes it."""
+    if y < 0 or y >= n:
+        return 0
+    m3 = (y >> 2) & 7
+    s8 = 0xFF
+    if m3 & 1:
+        s8 &= 0x55
+    if m3 & 2:
+        s8 &= 0x33
+    if m3 & 4:
+        s8 &= 0x0F
+    lt = (s8 >> (8 - hc)) if (x0 >= 32 and ((x0 - 32) & y) == 0) else 0
+    tt = s8 if (x0 & y) == 0 else 0
+    rt = (s8 & ((1 << hc) - 1)) if (x0 + 32 < n and ((x0 + 32) & y) == 0) else 0
+    return lt | (tt << hc) | (rt << (hc + 8))
+
+
+@pytest.mark.parametrize("kh", [4, 8, 16])
+def test_region_row_mask_is_the_chunk_membership_test(kh):
+    # bit cc of the mask: the chunk at column x0 - HX + 4 cc on row y lies in
+    # the grid and holds a gasket cell, i.e. (x & y) == 0 -- brute force over
+    # every 32-unit column and every region row of levels 5..8
+    hx = (kh + 3) // 4 * 4
+    hc, pc = hx // 4, 8 + 2 * hx // 4
+    for r in range(5, 9):
+        n = 1 << r
+        for x0 in range(0, n, 32):
+            for y in range(-kh, n + kh):
+                want = 0
+                for cc in range(pc):
+                    x = x0 - hx + 4 * cc
+                    if 0 <= x < n and 0 <= y < n and (x & y) == 0:
+                        want |= 1 << cc
+                assert _region_row_mask(x0, y, n, hc) == want, (r, x0, y)
+
+
+def _neighbourhoods(rb):
+    """Which of the 3 x 3 tiles around each non-empty tile of a level-rb block
+    gasket are non-empty (tiles off the grid count as empty)."""
+    nb = 1 << rb
+    out = set()
+    for by in range(nb):
+        for bx in range(nb):
+            if bx & by:
+                continue
+            out.add(tuple(0 <= bx + i < nb and 0 <= by + j < nb and ((bx + i) & (by + j)) == 0
+                          for j in (-1, 0, 1) for i in (-1, 0, 1)))
+    return out
+
+
+def _live_in_region(pattern, kh):
+    hx = (kh + 3) // 4 * 4
+    pc, rows = 8 + 2 * hx // 4, 32 + 2 * kh
+    c = 0
+    for row in range(rows):
+        for cc in range(pc):
+            x, y = 4 * cc - hx, row - kh
+            if pattern[((y + 32) // 32) * 3 + (x + 32) // 32] and ((x % 32) & (y % 32)) == 0:
+                c += 1
+    return c
+
+
+def test_fused_diffusion_live_block_bound():
+    # the rows of a group of 4 (starting at a multiple of 4) share their live
+    # chunks, so the region's live 4 x 4 blocks are its live chunks / 4.  The
+    # set of neighbourhoods is the same at every block level from 3 to 9, and
+    # over it the most live blocks in a unit's region are the kernel's MAXB
+    # for each halo depth; the levels' own units agree (brute force)
+    sets = [_neighbourhoods(rb) for rb in range(3, 10)]
+    assert all(s == sets[0] for s in sets) and len(sets[0]) == 13
+    with open(FUSED_SRC) as f:
+        m = re.search(r"MAXB = KH == 4 \? (\d+) : KH == 8 \? (\d+) : (\d+);", f.read())
+    maxb = dict(zip((4, 8, 16), map(int, m.groups())))
+    for kh in (4, 8, 16):
+        live = [_live_in_region(p, kh) for p in sets[0]]
+        assert all(c % 4 == 0 for c in live)
+        assert max(live) == 4 * maxb[kh], kh
+    # direct count over every unit of a level-11 gasket, KH = 8: blocks from
+    # the first row of each group, chunks from every row
+    r, kh = 11, 8
+    n = 1 << r
+    best = 0
+    for by in range(n // 32):
+        for bx in range(n // 32):
+            if bx & by:
+                continue
+            rows = [_region_row_mask(32 * bx, 32 * by - kh + row, n, 2) for row in range(32 + 2 * kh)]
+            assert all(rows[4 * (i // 4)] == rows[i] for i in range(len(rows)))
+            best = max(best, sum(bin(rows[4 * g]).count("1") for g in range(len(rows) // 4)))
+    assert best == maxb[8]

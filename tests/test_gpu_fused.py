@@ -62,6 +62,7 @@ def test_diffusion_fused_matches_fp64_oracle(orc, r, mapk, order):
             assert not got[~mask].any(), (rho, k)
             assert max_rel_err(got[mask], want[k][mask]) <= DIFF_TOL, (rho, k)
     assert np.array_equal(to_host(a, n), u0)
+    sg.device_status()          # no unit exceeded its live-chunk bound (raises otherwise)
 
 
 @pytest.mark.parametrize("rho", FUSED_RHOS)
