@@ -55,7 +55,11 @@ def parse_args():
     p.add_argument("--rho", type=int, default=None)
     p.add_argument("--map", default=None)
     p.add_argument("--order", default=None, choices=("rowmajor", "interleaved"))
-    p.add_argument("--store", default=None, choices=("auto", "scatter", "staged", "tma", "fill"))
+    p.add_argument("--store", default=None, choices=("auto", "scatter", "staged", "tma", "fill",
+                                                     "sector", "merge", "masked"))
+    p.add_argument("--value", default=None, choices=("hash", "linear31", "const"),
+                   help="with --quick: the written value (a constant times the store path "
+                        "alone)")
     p.add_argument("--no-extras", action="store_true",
                    help="skip the comparison workloads (bbox, f32, stencils)")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -79,7 +83,9 @@ def parse_args():
                         "fused form, k steps per launch) instead of the write pass (the "
                         "form used to profile those kernels)")
     p.add_argument("--level", type=int, default=None,
-                   help="with --quick and a stencil workload: the gasket level (default 15)")
+                   help="with --quick: the gasket level (stencils: default 15; write: 16)")
+    p.add_argument("--dtype", default="u8", choices=("u8", "f32"),
+                   help="with --quick and the write workload: the grid's element type")
     return p.parse_args()
 
 
@@ -289,9 +295,16 @@ def run_ours(args, grp: Group):
         w["order"] = args.order
     if args.store:
         w["store"] = args.store
+    if args.value:
+        w["value"] = args.value
+    if args.quick and args.level:
+        w["r"] = args.level
+    if args.quick and args.dtype == "f32" and not args.rho:
+        w["rho"] = w["f32_rho"]
     r, n = w["r"], 1 << w["r"]
     cells = 3 ** r
-    grid = torch.zeros(n * n, dtype=torch.uint8, device=dev)
+    grid = torch.zeros(n * n, dtype=torch.uint8 if args.dtype == "u8" or not args.quick
+                       else torch.float32, device=dev)
 
     def step():
         sg.map_write(grid, r, w["rho"], w["map"], w["value"], w["seed"], stream,
@@ -317,8 +330,9 @@ def run_ours(args, grp: Group):
     value = grp.world * cells * args.steps / (total_ms / 1e3) / 1e9
     launch_ms = statistics.mean(per_launch)
     peak, peak_kind = measured_peak()
-    line_bytes = touched_bytes(r, 1, 128)
-    sector_bytes = touched_bytes(r, 1, 32)
+    elem = 4 if grid.dtype == torch.float32 else 1
+    line_bytes = touched_bytes(r, elem, 128)
+    sector_bytes = touched_bytes(r, elem, 32)
     achieved = line_bytes / (launch_ms / 1e3) / 1e9
     launched, useful = sg.launch_stats(r, w["rho"], w["map"])
     kernel_key = f"write_{w['map']}_{w['store']}_{w['order']}_r{r}_u8_rho{w['rho']}"
@@ -332,6 +346,8 @@ def run_ours(args, grp: Group):
         "algorithmic_bytes": "touched 128-byte lines: 2^7 * 3^9 lines of 128 B",
         "sector_bytes_per_launch": sector_bytes,
         "achieved_sector_gbs": round(sector_bytes / (launch_ms / 1e3) / 1e9, 1),
+        # the same against the 32-byte sectors the pass must write (stricter)
+        "frac_sector": round(sector_bytes / (launch_ms / 1e3) / 1e9 / peak, 4),
         "launch_ms_mean": round(launch_ms, 5),
         "launch_ms_min": round(min(per_launch), 5),
         "kernel": kernel_key,
@@ -357,6 +373,10 @@ def run_ours(args, grp: Group):
         "gpu_launches": args.steps,
     }
 
+    if roofline["traffic"]:
+        # ncu DRAM bytes against the touched sectors: above 1 means bytes the
+        # method does not need (here whole 64-byte tile rows)
+        roofline["traffic_ratio"] = round(roofline["traffic"] / sector_bytes, 3)
     if args.quick:
         return out
     if grp.rank == 0 and not args.no_extras:
@@ -640,14 +660,19 @@ def paper_sweep(args):
             "points": rows, "best_per_level": best}
 
 
+SWEEP_LAUNCHES = 50
+
+
 def write_sweep(args):
     """The map-and-write sweep over levels 8..16, uint8 and float32 grids,
     rho = 8, 16, 32, 64, lambda (the headline's intra-tile map and walking
-    order) against the bounding box, hash values seed 1, both with whole-tile
-    fill stores where a tile row holds at least 16 bytes and per-cell stores
-    otherwise.  Each point: GPU time per launch from CUDA-graph replays of 10
-    launches (the L2 flushed before each timed replay), GCells/s, launched
-    against useful cell slots, and touched 128-byte lines per second."""
+    order) against the bounding box, hash values seed 1, each with every
+    store path the tile rows allow (per-cell stores; whole-tile fill stores
+    where a tile row holds at least 16 bytes; whole-sector stores where it
+    holds at least 32).  Each point: GPU time per launch from CUDA-graph
+    replays of 50 launches (the L2 flushed before each timed replay),
+    GCells/s, launched against useful cell slots, and touched 128-byte lines
+    per second; each map's best point per level is compared."""
     import torch
     import paper_1706_04552_gb300 as sg
     from paper_1706_04552_gb300 import workloads
@@ -667,8 +692,12 @@ def write_sweep(args):
             for rho in sw["rhos"]:
                 if rho > n:
                     continue
-                store = "fill" if rho * elem >= 16 else "scatter"
-                for name, mapk in (("lambda", hw["map"]), ("bbox", "bbox")):
+                # every store path the tile rows allow, for both maps: each
+                # map is then compared at its best (rho, store)
+                stores = ["scatter"] + (["fill"] if rho * elem >= 16 else []) + \
+                         (["sector"] if rho * elem >= 32 else [])
+                for store, (name, mapk) in ((st_, m_) for st_ in stores for m_ in (
+                        ("lambda", hw["map"]), ("bbox", "bbox"))):
                     cap = torch.cuda.Stream(dev)
                     call = lambda st: sg.map_write(g, r, rho, mapk, "hash", hw["seed"], st,
                                                    order=hw["order"], store=store)
@@ -676,7 +705,7 @@ def write_sweep(args):
                     torch.cuda.synchronize(dev)
                     graph = torch.cuda.CUDAGraph()
                     with torch.cuda.graph(graph, stream=cap):
-                        for _ in range(10):
+                        for _ in range(SWEEP_LAUNCHES):
                             call(torch.cuda.current_stream(dev))
                     graph.replay()
                     torch.cuda.synchronize(dev)
@@ -690,7 +719,7 @@ def write_sweep(args):
                         graph.replay()
                         e1.record(st)
                         e1.synchronize()
-                        vals.append(e0.elapsed_time(e1) * 1e3 / 10)
+                        vals.append(e0.elapsed_time(e1) * 1e3 / SWEEP_LAUNCHES)
                     us = statistics.median(vals)
                     launched, useful = sg.launch_stats(r, rho, mapk)
                     rows.append({"dtype": dtype, "r": r, "rho": rho, "map": mapk, "store": store,
@@ -713,7 +742,7 @@ def write_sweep(args):
                                      "speedup_best_vs_best": round(bb["us"] / bl["us"], 3)}
     return {"experiment": "map-and-write sweep: levels 8..16, uint8 and float32, rho 8..64, "
                           "lambda vs bounding box, hash values seed 1",
-            "protocol": "median of 5 CUDA-graph replays of 10 launches, L2 flushed before each",
+            "protocol": "median of 5 CUDA-graph replays of 50 launches, L2 flushed before each",
             "peak_GBps": peak, "peak_kind": peak_kind, "points": rows, "best_per_level": best}
 
 
@@ -768,6 +797,40 @@ def _rate(cells, ms):
     return round(cells / (ms / 1e3) / 1e9, 3)
 
 
+def _time_leg(sg, grid, r, cfg, seed, stream, cells, sector_b, steps):
+    f = lambda: sg.map_write(grid, r, cfg["rho"], cfg["map"], "hash", seed, stream,
+                             order=cfg["order"], store=cfg["store"])
+    for _ in range(3):
+        f()
+    ms, per = time_launches(f, steps, stream)
+    return {"map": cfg["map"], "rho": cfg["rho"], "order": cfg["order"], "store": cfg["store"],
+            "GCells_s": _rate(cells, ms / steps), "launch_ms": round(statistics.mean(per), 5),
+            "sector_GBps": round(sector_b / (statistics.mean(per) / 1e3) / 1e9, 1)}
+
+
+def _with_l2_fetch_granularity(nbytes, fn):
+    """Run fn() with the current CUDA context's L2 fetch granularity limit
+    (CU_LIMIT_MAX_L2_FETCH_GRANULARITY) set to nbytes, then put the previous
+    value back.  The limit belongs to this process's context only."""
+    import ctypes
+    try:
+        cu = ctypes.CDLL("libcuda.so.1")
+    except OSError as e:
+        return {"unavailable": f"libcuda: {e}"}
+    limit = 0x05                       # CU_LIMIT_MAX_L2_FETCH_GRANULARITY
+    old = ctypes.c_size_t(0)
+    if cu.cuCtxGetLimit(ctypes.byref(old), limit) != 0:
+        return {"unavailable": "cuCtxGetLimit failed"}
+    if cu.cuCtxSetLimit(limit, ctypes.c_size_t(nbytes)) != 0:
+        return {"unavailable": "cuCtxSetLimit failed"}
+    try:
+        out = fn()
+    finally:
+        cu.cuCtxSetLimit(limit, old)
+    out["l2_fetch_granularity"] = {"set": nbytes, "default": old.value}
+    return out
+
+
 def compare_workloads(sg, torch, dev, stream, w, grid_u8, headline_launch_ms):
     """Short timings of the other configurations on the same GPU."""
     from paper_1706_04552_gb300 import inputs, workloads
@@ -779,21 +842,48 @@ def compare_workloads(sg, torch, dev, stream, w, grid_u8, headline_launch_ms):
     # content; the paper's own intra-tile variant (bounding sub-boxes)
     from paper_1706_04552_gb300 import workloads as wl
     pv = wl.WRITE_PRESERVE
-    for name, mapk, rho, order, store, steps in (
-            ("bbox_u8", "bbox", w["bbox_rho"], w["order"], w["store"], 20),
-            ("lambda_preserving_u8", pv["map"], pv["rho"], pv["order"], pv["store"], 200),
-            ("lambda_subbox_u8", "lambda", w["rho"], w["order"], w["store"], 200)):
-        f = lambda: sg.map_write(grid_u8, r, rho, mapk, "hash", w["seed"], stream,
+    sector_b = touched_bytes(r, 1, 32)
+    legs = (("bbox_u8", "bbox", w["bbox_rho"], w["order"], w["store"], 20, "hash"),
+            ("lambda_preserving_u8", pv["map"], pv["rho"], pv["order"], pv["store"], 200, "hash"),
+            ("lambda_staged_u8", pv["map"], 32, "rowmajor", "staged", 200, "hash"),
+            ("lambda_masked_u8", pv["map"], 64, w["order"], "masked", 100, "hash"),
+            ("lambda_sector_u8", w["map"], 64, w["order"], "sector", 200, "hash"),
+            ("lambda_subbox_u8", "lambda", w["rho"], w["order"], w["store"], 200, "hash"),
+            # the store paths alone: a constant instead of the hash
+            ("store_floor_fill_const_u8", w["map"], w["rho"], w["order"], w["store"], 200,
+             "const"),
+            ("store_floor_sector_const_u8", w["map"], 64, w["order"], "sector", 200, "const"))
+    for name, mapk, rho, order, store, steps, vk in legs:
+        f = lambda: sg.map_write(grid_u8, r, rho, mapk, vk, w["seed"], stream,
                                  order=order, store=store)
         for _ in range(3):
             f()
         grid_u8.zero_()
         ms, per = time_launches(f, steps, stream)
-        res[name] = {"map": mapk, "rho": rho, "order": order, "store": store,
+        res[name] = {"map": mapk, "rho": rho, "order": order, "store": store, "value": vk,
                      "GCells_s": _rate(cells, ms / steps),
                      "launch_ms": round(statistics.mean(per), 5),
                      "line_GBps": round(touched_bytes(r, 1, 128) /
-                                        (statistics.mean(per) / 1e3) / 1e9, 1)}
+                                        (statistics.mean(per) / 1e3) / 1e9, 1),
+                     "sector_GBps": round(sector_b / (statistics.mean(per) / 1e3) / 1e9, 1)}
+    # the preserving merge pass with the L2 fetching 32 bytes per read miss
+    # (a per-context limit of the CUDA driver, restored afterwards): DRAM then
+    # reads the touched sectors only, instead of their whole 128-byte lines
+    res["lambda_preserving_u8_l2fetch32"] = _with_l2_fetch_granularity(32, lambda: _time_leg(
+        sg, grid_u8, r, pv, w["seed"], stream, cells, sector_b, 200))
+    # streaming write bandwidth of the same memory: the whole 4.3 GB grid
+    # zeroed by the runtime's fill kernel
+    torch.cuda.synchronize(dev)
+    zl = []
+    for _ in range(4):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        grid_u8.zero_()
+        e1.record(stream)
+        e1.synchronize()
+        zl.append(e0.elapsed_time(e1))
+    res["stream_write_full_grid"] = {"bytes": grid_u8.numel(), "ms": round(min(zl[1:]), 4),
+                                     "GBps": round(grid_u8.numel() / (min(zl[1:]) / 1e3) / 1e9, 1)}
     grid_u8.zero_()
     res["speedup_lambda_over_bbox"] = round(res["bbox_u8"]["launch_ms"] / headline_launch_ms, 3)
     # float32 grid (17.2 GB)

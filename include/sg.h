@@ -102,13 +102,31 @@ typedef enum {
     SG_STORE_TMA = 3,       /* whole tiles moved by 2-D bulk tensor copies (TMA),
                                several tiles in flight per team; same
                                requirement as SG_STORE_STAGED */
-    SG_STORE_FILL = 4       /* write-only: every tile that holds gasket cells is
+    SG_STORE_FILL = 4,      /* write-only: every tile that holds gasket cells is
                                written whole, v(x, y) at gasket cells and 0 at
                                the other cells of the tile; nothing is read.
                                The result equals the other modes' whenever the
                                grid is 0 off the gasket (the zero matrix of the
                                paper's benchmark, the stencils' invariant).
                                Same requirement as SG_STORE_STAGED. */
+    SG_STORE_SECTOR = 5,    /* write-only, one lane per 32-cell-wide unit: every
+                               32-byte sector that holds gasket cells is written
+                               whole with one 32-byte store, v(x, y) at gasket
+                               cells and 0 at its other cells; nothing is read.
+                               Equal to the preserving modes whenever the grid is
+                               0 off the gasket.  Needs rho * element size >= 32
+                               bytes and a 32-byte aligned grid. */
+    SG_STORE_MERGE = 6,     /* as SG_STORE_SECTOR, but each such sector is read
+                               (32-byte load), its gasket cells replaced and
+                               written back; off-gasket cells keep their content
+                               (no other kernel may write the grid meanwhile).
+                               Same requirements. */
+    SG_STORE_MASKED = 7     /* as SG_STORE_SECTOR, but only the gasket cells are
+                               stored (one 4-, 2- or 1-byte store per run of
+                               gasket cells in a 32-bit word, one store per cell
+                               for float32); the L2 completes each sector from
+                               DRAM.  Only gasket cells ever change.  Same
+                               requirements. */
 } sg_store;
 
 /* Launch options of the *_ex calls.  Zero-initialise, then set fields. */
@@ -142,12 +160,16 @@ typedef enum {
  *   stream         cudaStream_t
  * Launches one kernel.  Returns SG_OK, SG_EINVAL or SG_ECUDA.
  *
- * With SG_STORE_STAGED or SG_STORE_TMA (the default is one of them wherever
- * rho * element size >= 16 bytes and `grid` is 16-byte aligned) the off-gasket
- * cells of a touched tile are read and written back unchanged, so no other
- * kernel may write `grid` while the pass runs; with SG_STORE_SCATTER only
- * gasket cells are ever stored.  SG_STORE_FILL (on request only) writes 0 to
- * the off-gasket cells of every tile that holds gasket cells.
+ * The default (SG_STORE_AUTO) is SG_STORE_MERGE where rho * element size >= 32
+ * bytes and `grid` is 32-byte aligned, else SG_STORE_STAGED where rho *
+ * element size >= 16 bytes and `grid` is 16-byte aligned, else
+ * SG_STORE_SCATTER.  With SG_STORE_MERGE, SG_STORE_STAGED or SG_STORE_TMA the
+ * off-gasket cells of a touched sector or tile are read and written back
+ * unchanged, so no other kernel may write `grid` while the pass runs; with
+ * SG_STORE_SCATTER only gasket cells are ever stored.  SG_STORE_FILL (on request only) writes 0 to
+ * the off-gasket cells of every tile that holds gasket cells.  SG_STORE_SECTOR,
+ * SG_STORE_MERGE and SG_STORE_MASKED (on request only) move whole 32-byte
+ * sectors with one lane per unit (see sg_store).
  */
 SG_API sg_status sg_map_write(int r, int rho, sg_map map, sg_dtype dtype, void *grid,
                               sg_value_kind value_kind, uint64_t value_or_seed,
@@ -216,7 +238,8 @@ SG_API sg_status sg_diffuse_step_ex(int r, int rho, sg_map map, const float *in,
  * sectors that hold gasket cells are written whole with plain stores (0 at
  * their off-gasket cells) and nothing is read, so only the writes cross the
  * link -- equal to the others on a grid that is 0 off the gasket.
- * SG_STORE_TMA (bulk tensor copies) is SG_EUNSUPPORTED here.  The allocation must hold
+ * SG_STORE_TMA (bulk tensor copies) and the sector modes (SG_STORE_SECTOR,
+ * SG_STORE_MERGE, SG_STORE_MASKED) are SG_EUNSUPPORTED here.  The allocation must hold
  * the whole n*n grid (its size cannot be queried; a shorter one is the
  * caller's error, as for a device grid).  Otherwise as sg_map_write_ex; the
  * result is in host memory once the stream has completed.

@@ -46,7 +46,8 @@ MAPS = {"lambda": 0, "bbox": 1, "lambda_lut": 2, "lambda_unroll": 3}
 DTYPES = {"u8": 0, "f32": 1}
 VALUES = {"const": 0, "linear31": 1, "hash": 2}
 ORDERS = {"rowmajor": 0, "interleaved": 1}
-STORES = {"auto": 0, "scatter": 1, "staged": 2, "tma": 3, "fill": 4}
+STORES = {"auto": 0, "scatter": 1, "staged": 2, "tma": 3, "fill": 4, "sector": 5, "merge": 6,
+          "masked": 7}
 
 
 class LaunchOpts(ctypes.Structure):

@@ -66,7 +66,7 @@ bool read_launch_opts(const sg_launch_opts *o, LaunchCfg *cfg)
         if (o->order != SG_ORDER_ROWMAJOR && o->order != SG_ORDER_INTERLEAVED) return false;
         cfg->order = o->order;
     }
-    if (o->store < SG_STORE_AUTO || o->store > SG_STORE_FILL) return false;
+    if (o->store < SG_STORE_AUTO || o->store > SG_STORE_MASKED) return false;
     cfg->store = o->store;
     if (o->ctas_per_sm < 0 || o->ctas_per_sm > 64) return false;
     cfg->ctas_per_sm = o->ctas_per_sm;
@@ -190,8 +190,16 @@ sg_status sg_map_write_ex(int r, int rho, sg_map map, sg_dtype dtype, void *grid
         cfg.store == SG_STORE_FILL) {
         if (!can_stage) return SG_EUNSUPPORTED;
         if (!aligned(grid, 16)) return SG_EINVAL;
+    } else if (cfg.store == SG_STORE_SECTOR || cfg.store == SG_STORE_MERGE ||
+               cfg.store == SG_STORE_MASKED) {
+        // one lane per unit of whole 32-byte sectors: tile rows of >= 32 bytes
+        if (rho * elem < 32) return SG_EUNSUPPORTED;
+        if (!aligned(grid, 32)) return SG_EINVAL;
     } else if (cfg.store == SG_STORE_AUTO) {
-        cfg.store = (can_stage && aligned(grid, 16)) ? kDefaultWholeTileStore : kStoreScatter;
+        // the measured best that keeps off-gasket content: whole 32-byte
+        // sectors read, merged and written back where the tile rows allow it
+        if (rho * elem >= 32 && aligned(grid, 32)) cfg.store = kStoreMerge;
+        else cfg.store = (can_stage && aligned(grid, 16)) ? kDefaultWholeTileStore : kStoreScatter;
     }
     if (dtype == SG_U8)
         return finish(launch_write_u8(r, s, (int)map, (int)value_kind, (uint8_t *)grid,
@@ -215,7 +223,9 @@ sg_status sg_map_write_mapped(int r, int rho, sg_map map, sg_dtype dtype, void *
     const int elem = dtype == SG_U8 ? 1 : 4;
     // only the paths that move data with plain loads and stores: fill runs
     // as write-only whole chunks of the staged kernel (no bulk tensor copy)
-    if (cfg.store == SG_STORE_TMA) return SG_EUNSUPPORTED;
+    if (cfg.store == SG_STORE_TMA || cfg.store == SG_STORE_SECTOR ||
+        cfg.store == SG_STORE_MERGE || cfg.store == SG_STORE_MASKED)
+        return SG_EUNSUPPORTED;
     if ((cfg.store == SG_STORE_STAGED || cfg.store == SG_STORE_FILL) && rho * elem < 16)
         return SG_EUNSUPPORTED;                       // whole chunks need 16-byte tile rows
     // the pointer must be page-locked host memory mapped into the device's

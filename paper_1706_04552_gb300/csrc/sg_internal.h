@@ -11,9 +11,10 @@ namespace sg {
 enum : int { kMapLambda = 0, kMapBBox = 1, kMapLut = 2, kMapUnroll = 3 };
 
 enum : int { kStoreAuto = 0, kStoreScatter = 1, kStoreStaged = 2, kStoreTma = 3, kStoreFill = 4,
+              kStoreSector = 5, kStoreMerge = 6, kStoreMasked = 7,
               // internal: the fill contract through the staged kernel's plain
               // stores, reading nothing (grids in host memory)
-              kStoreFillPlain = 5 };
+              kStoreFillPlain = 100 };
 
 // Launch knobs.  ctas_per_sm <= 0 selects the occupancy maximum; order is a
 // traversal order of the block space (kOrderRowMajor / kOrderInterleaved);

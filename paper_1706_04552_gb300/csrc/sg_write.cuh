@@ -49,6 +49,7 @@
 #include "sg_device.cuh"
 #include "sg_internal.h"
 #include "sg_tma.cuh"
+#include "sg_write_sector.cuh"
 
 namespace sg {
 
@@ -652,6 +653,8 @@ cudaError_t launch_write_t(int r, T *grid, uint64_t vs, cudaStream_t st, const L
     const int rb = r - S;
     const uint64_t ntiles = (MAP == kMapBBox) ? (1ull << (2 * rb)) : (uint64_t)pow3i(rb);
     if (cfg.store == kStoreTma) return launch_write_tma<T, VK, S, MAP>(r, grid, vs, ntiles, st, cfg);
+    if (cfg.store == kStoreSector || cfg.store == kStoreMerge || cfg.store == kStoreMasked)
+        return launch_write_sector<T, VK, S, MAP>(r, grid, vs, ntiles, st, cfg);
     if (cfg.store == kStoreFill) return launch_write_fill<T, VK, S, MAP>(r, grid, vs, ntiles, st, cfg);
     using WS = WriteShape<T, S>;
     bool staged = false;     // the caller resolved kStoreAuto already

@@ -23,11 +23,12 @@ WRITE_SWEEP = dict(levels=tuple(range(8, 17)), rhos=(8, 16, 32, 64),
 # the bounding box gets its own best rho and the same store path.
 WRITE_HEADLINE = dict(r=16, dtype="u8", value="hash", seed=1,
                       map="lambda_unroll", rho=64, order="interleaved", store="fill",
-                      bbox_rho=64, f32_rho=32)
+                      bbox_rho=64, f32_rho=16)
 
 # The same pass with stores that keep arbitrary off-gasket content
-# (read-merge-write of whole chunks; the library default).
-WRITE_PRESERVE = dict(map="lambda_unroll", rho=32, order="rowmajor", store="staged")
+# (read-merge-write of whole 32-byte sectors, one lane per 32 x 32 unit; the
+# library default for such tiles).
+WRITE_PRESERVE = dict(map="lambda_unroll", rho=64, order="interleaved", store="merge")
 
 # The same pass on a grid kept in pinned host memory, read and written in
 # place over the host link (sg_map_write_mapped), with staged

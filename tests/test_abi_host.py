@@ -88,7 +88,7 @@ def test_bad_pointers_and_enums_are_einval(L):
 
 
 def test_bad_launch_options_are_rejected_before_launch(L):
-    bad = [sg.launch_opts(order=5), sg.launch_opts(store=7), sg.launch_opts(ctas_per_sm=-1),
+    bad = [sg.launch_opts(order=5), sg.launch_opts(store=8), sg.launch_opts(ctas_per_sm=-1),
            sg.launch_opts(ctas_per_sm=65)]
     o = sg.launch_opts(order=1)
     o.reserved[2] = 1
@@ -106,10 +106,17 @@ def test_bad_launch_options_are_rejected_before_launch(L):
     assert sg.sg_map_write_ex(8, 8, 0, 0, FAKE, 2, 1, tma) == sg.SG_EUNSUPPORTED
     assert sg.sg_map_write_ex(8, 2, 0, 1, FAKE, 2, 1, tma) == sg.SG_EUNSUPPORTED
     assert sg.sg_map_write_ex(8, 16, 0, 0, FAKE + 8, 2, 1, tma) == sg.SG_EINVAL
-    assert sg.sg_map_write_ex(8, 16, 0, 0, FAKE, 2, 1, sg.launch_opts(store=5)) == sg.SG_EINVAL
+    assert sg.sg_map_write_ex(8, 16, 0, 0, FAKE, 2, 1, sg.launch_opts(store=8)) == sg.SG_EINVAL
     fill = sg.launch_opts(store="fill")
     assert sg.sg_map_write_ex(8, 8, 0, 0, FAKE, 2, 1, fill) == sg.SG_EUNSUPPORTED
     assert sg.sg_map_write_ex(8, 16, 0, 0, FAKE + 4, 2, 1, fill) == sg.SG_EINVAL
+    # the sector modes need 32-byte tile rows and a 32-byte aligned grid
+    for name in ("sector", "merge", "masked"):
+        o = sg.launch_opts(store=name)
+        assert sg.sg_map_write_ex(8, 16, 0, 0, FAKE, 2, 1, o) == sg.SG_EUNSUPPORTED
+        assert sg.sg_map_write_ex(8, 4, 0, 1, FAKE, 2, 1, o) == sg.SG_EUNSUPPORTED
+        assert sg.sg_map_write_ex(8, 32, 0, 0, FAKE + 16, 2, 1, o) == sg.SG_EINVAL
+        assert sg.sg_map_write_ex(8, 8, 0, 1, FAKE + 16, 2, 1, o) == sg.SG_EINVAL
 
 
 def test_fused_steps_validate_before_launch(L):
@@ -220,6 +227,9 @@ def test_mapped_write_refuses_memory_it_cannot_check(L):
     assert sg.sg_map_write_mapped(8, 16, 0, 0, 0, 2, 1) == sg.SG_EINVAL
     assert sg.sg_map_write_mapped(8, 16, 0, 0, ptr, 2, 1,
                                   sg.launch_opts(store="tma")) == sg.SG_EUNSUPPORTED
+    for name in ("sector", "merge", "masked"):
+        assert sg.sg_map_write_mapped(8, 32, 0, 0, ptr, 2, 1,
+                                      sg.launch_opts(store=name)) == sg.SG_EUNSUPPORTED
     assert sg.sg_map_write_mapped(8, 16, 0, 0, ptr, 2, 1,
                                   sg.launch_opts(store="fill")) == sg.SG_EINVAL
     assert sg.sg_map_write_mapped(8, 8, 0, 0, ptr, 2, 1,           # 8-byte tile rows
