@@ -86,6 +86,9 @@ def parse_args():
                    help="with --quick: the gasket level (stencils: default 15; write: 16)")
     p.add_argument("--dtype", default="u8", choices=("u8", "f32"),
                    help="with --quick and the write workload: the grid's element type")
+    p.add_argument("--l2-fetch", type=int, default=None,
+                   help="with --quick: run with this L2 fetch granularity (bytes) as the "
+                        "context's limit")
     return p.parse_args()
 
 
@@ -284,6 +287,16 @@ def run_ours(args, grp: Group):
     dev = torch.device("cuda", grp.local)
     torch.cuda.set_device(dev)
     stream = torch.cuda.current_stream(dev)
+    if args.quick and args.l2_fetch:
+        torch.zeros(1, device=dev)             # the context exists
+        out = _with_l2_fetch_granularity(args.l2_fetch, lambda: run_ours_body(
+            args, grp, sg, torch, dev, stream))
+        return out
+    return run_ours_body(args, grp, sg, torch, dev, stream)
+
+
+def run_ours_body(args, grp, sg, torch, dev, stream):
+    from paper_1706_04552_gb300 import workloads
     if args.quick and args.workload != "write":
         return run_stencil_quick(args, sg, torch, dev, stream)
     w = dict(workloads.WRITE_HEADLINE)
@@ -299,8 +312,9 @@ def run_ours(args, grp: Group):
         w["value"] = args.value
     if args.quick and args.level:
         w["r"] = args.level
-    if args.quick and args.dtype == "f32" and not args.rho:
-        w["rho"] = w["f32_rho"]
+    if args.quick and args.dtype == "f32":
+        w["rho"] = args.rho or w["f32_rho"]
+        w["store"] = args.store or w["f32_store"]
     r, n = w["r"], 1 << w["r"]
     cells = 3 ** r
     grid = torch.zeros(n * n, dtype=torch.uint8 if args.dtype == "u8" or not args.quick
@@ -797,6 +811,46 @@ def _rate(cells, ms):
     return round(cells / (ms / 1e3) / 1e9, 3)
 
 
+def _memset_rate(torch, t, stream, reps=4):
+    """Write bandwidth of cuMemsetD8Async over a whole device tensor (the
+    fastest way to write every byte of it): bytes / best event-timed call."""
+    import ctypes
+    try:
+        cu = ctypes.CDLL("libcuda.so.1")
+    except OSError as e:
+        return {"unavailable": f"libcuda: {e}"}
+    ms = []
+    for i in range(reps + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        rc = cu.cuMemsetD8Async(ctypes.c_uint64(t.data_ptr()), ctypes.c_ubyte(i & 0xFF),
+                                ctypes.c_size_t(t.numel() * t.element_size()),
+                                ctypes.c_void_p(stream.cuda_stream))
+        e1.record(stream)
+        e1.synchronize()
+        if rc != 0:
+            return {"unavailable": f"cuMemsetD8Async returned {rc}"}
+        ms.append(e0.elapsed_time(e1))
+    best = min(ms[1:])
+    nbytes = t.numel() * t.element_size()
+    return {"bytes": nbytes, "ms": round(best, 4), "GBps": round(nbytes / (best / 1e3) / 1e9, 1),
+            "how": "cuMemsetD8Async over the whole grid, best of 4 after one warm-up"}
+
+
+def _add_traffic(entry, key, unit, launch_us):
+    """Attach the recorded ncu DRAM bytes of one launch (profiles/traffic.txt,
+    while the unit's code still matches) and the DRAM rate they give at the
+    measured launch time, as a fraction of the measured HBM peak."""
+    t = recorded_traffic(key, unit)
+    entry["traffic_bytes_per_launch"] = t
+    if t:
+        peak, kind = measured_peak()
+        gbs = t / (launch_us / 1e6) / 1e9
+        entry["dram_GBps"] = round(gbs, 1)
+        entry["dram_frac"] = round(gbs / peak, 4)
+        entry["dram_peak_kind"] = kind
+
+
 def _time_leg(sg, grid, r, cfg, seed, stream, cells, sector_b, steps):
     f = lambda: sg.map_write(grid, r, cfg["rho"], cfg["map"], "hash", seed, stream,
                              order=cfg["order"], store=cfg["store"])
@@ -843,7 +897,8 @@ def compare_workloads(sg, torch, dev, stream, w, grid_u8, headline_launch_ms):
     from paper_1706_04552_gb300 import workloads as wl
     pv = wl.WRITE_PRESERVE
     sector_b = touched_bytes(r, 1, 32)
-    legs = (("bbox_u8", "bbox", w["bbox_rho"], w["order"], w["store"], 20, "hash"),
+    legs = (("bbox_u8", "bbox", w["bbox_rho"], w["order"], w["bbox_store"], 20, "hash"),
+            ("bbox_fill_u8", "bbox", w["bbox_rho"], w["order"], "fill", 20, "hash"),
             ("lambda_preserving_u8", pv["map"], pv["rho"], pv["order"], pv["store"], 200, "hash"),
             ("lambda_staged_u8", pv["map"], 32, "rowmajor", "staged", 200, "hash"),
             ("lambda_masked_u8", pv["map"], 64, w["order"], "masked", 100, "hash"),
@@ -872,29 +927,19 @@ def compare_workloads(sg, torch, dev, stream, w, grid_u8, headline_launch_ms):
     res["lambda_preserving_u8_l2fetch32"] = _with_l2_fetch_granularity(32, lambda: _time_leg(
         sg, grid_u8, r, pv, w["seed"], stream, cells, sector_b, 200))
     # streaming write bandwidth of the same memory: the whole 4.3 GB grid
-    # zeroed by the runtime's fill kernel
-    torch.cuda.synchronize(dev)
-    zl = []
-    for _ in range(4):
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        grid_u8.zero_()
-        e1.record(stream)
-        e1.synchronize()
-        zl.append(e0.elapsed_time(e1))
-    res["stream_write_full_grid"] = {"bytes": grid_u8.numel(), "ms": round(min(zl[1:]), 4),
-                                     "GBps": round(grid_u8.numel() / (min(zl[1:]) / 1e3) / 1e9, 1)}
+    # set by the driver's memset (every byte, in address order)
+    res["stream_write_full_grid"] = _memset_rate(torch, grid_u8, stream)
     grid_u8.zero_()
     res["speedup_lambda_over_bbox"] = round(res["bbox_u8"]["launch_ms"] / headline_launch_ms, 3)
     # float32 grid (17.2 GB)
     g32 = torch.zeros(n * n, dtype=torch.float32, device=dev)
     f = lambda: sg.map_write(g32, r, w["f32_rho"], w["map"], "hash", w["seed"], stream,
-                             order=w["order"], store=w["store"])
+                             order=w["order"], store=w["f32_store"])
     for _ in range(3):
         f()
     ms, per = time_launches(f, 100, stream)
     lb = touched_bytes(r, 4, 128)
-    res["lambda_f32"] = {"map": w["map"], "rho": w["f32_rho"], "store": w["store"],
+    res["lambda_f32"] = {"map": w["map"], "rho": w["f32_rho"], "store": w["f32_store"],
                          "GCells_s": _rate(cells, ms / 100),
                          "launch_ms": round(statistics.mean(per), 5),
                          "line_GBps": round(lb / (statistics.mean(per) / 1e3) / 1e9, 1)}
@@ -924,6 +969,9 @@ def compare_workloads(sg, torch, dev, stream, w, grid_u8, headline_launch_ms):
                                    "GCells_s": _rate(cs, ms / steps),
                                    "launch_ms": round(statistics.mean(per), 5),
                                    "line_GBps": round(lb / (statistics.mean(per) / 1e3) / 1e9, 1)}
+        if mapk == "lambda":
+            _add_traffic(res[f"ca_r{rs}_{mapk}"], f"ca_r{rs}_lambda_rho{rho}", "sg_stencil.cu",
+                         statistics.mean(per) * 1e3)
         del a, b, bufs
     idx, vals = inputs.uniform_sparse(rs, s["diff_seed"])
     for mapk, rho in (("lambda", s["diff_rho"]), ("bbox", s["bbox_diff_rho"])):
@@ -944,6 +992,9 @@ def compare_workloads(sg, torch, dev, stream, w, grid_u8, headline_launch_ms):
                                           "GCells_s": _rate(cs, ms / steps),
                                           "launch_ms": round(statistics.mean(per), 5),
                                           "line_GBps": round(lb / (statistics.mean(per) / 1e3) / 1e9, 1)}
+        if mapk == "lambda":
+            _add_traffic(res[f"diffusion_r{rs}_{mapk}"], f"diffusion_r{rs}_lambda_rho{rho}",
+                         "sg_stencil.cu", statistics.mean(per) * 1e3)
         del a, b, bufs
     torch.cuda.empty_cache()
     # the same step sequences with k steps fused per launch
@@ -992,6 +1043,9 @@ def fused_stencils(sg, torch, dev, stream, r, single):
             "rho": rho, "steps": total, "steps_per_launch": k, "launches": len(chunks),
             "us_per_step": round(ms * 1e3 / total, 2), "GCells_s": round(rate, 3),
             "speedup_vs_single_step": round(rate / base, 3) if base else None}
+        # DRAM bytes of one launch of k steps, spread over its k steps
+        _add_traffic(out[f"{kind}_r{r}_fused"], f"{kind}_fused_r{r}_rho{rho}_k{k}", "sg_fused.cu",
+                     ms * 1e3 / total * k)
         del a, bufs
         torch.cuda.empty_cache()
     return out

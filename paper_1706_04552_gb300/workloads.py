@@ -20,10 +20,11 @@ WRITE_SWEEP = dict(levels=tuple(range(8, 17)), rhos=(8, 16, 32, 64),
 # The headline: the write pass at n = 2^16 into a zero-filled 4.3 GB uint8
 # grid (the paper's benchmark: write into the gasket of a zero matrix).
 # Map, rho, walking order and store path are the measured best on GB300;
-# the bounding box gets its own best rho and the same store path.
+# the bounding box and the float32 grid get their own measured best rho and
+# store path (the write sweep).
 WRITE_HEADLINE = dict(r=16, dtype="u8", value="hash", seed=1,
                       map="lambda_unroll", rho=64, order="interleaved", store="fill",
-                      bbox_rho=64, f32_rho=16)
+                      bbox_rho=64, bbox_store="sector", f32_rho=8, f32_store="sector")
 
 # The same pass with stores that keep arbitrary off-gasket content
 # (read-merge-write of whole 32-byte sectors, one lane per 32 x 32 unit; the
