@@ -86,6 +86,8 @@ def parse_args():
                    help="with --quick: the gasket level (stencils: default 15; write: 16)")
     p.add_argument("--dtype", default="u8", choices=("u8", "f32"),
                    help="with --quick and the write workload: the grid's element type")
+    p.add_argument("--staging", default=None, choices=("chunks", "tma"),
+                   help="with --quick and the ca / diffusion workloads: how tiles are staged")
     p.add_argument("--l2-fetch", type=int, default=None,
                    help="with --quick: run with this L2 fetch granularity (bytes) as the "
                         "context's limit")
@@ -396,6 +398,10 @@ def run_ours_body(args, grp, sg, torch, dev, stream):
     if grp.rank == 0 and not args.no_extras:
         out["compare"] = compare_workloads(sg, torch, dev, stream, w, grid, launch_ms)
         out["compare"]["level_sweep"] = level_sweep(sg, torch, dev, w)
+        # each map at its own best (rho, store path) per level and element type
+        ws = write_sweep(args)
+        out["compare"]["write_sweep_best"] = {"protocol": ws["protocol"],
+                                              "best_per_level": ws["best_per_level"]}
         out["compare"]["batched_ca"] = batched_workload(sg, torch, dev, stream)
         out["serving"] = serving_workload()
     del grid
@@ -450,8 +456,13 @@ def run_stencil_quick(args, sg, torch, dev, stream):
             sg.compact_ca_step(bufs[0], bufs[1], r, rho, stream=stream)
         elif compact:
             sg.compact_diffuse_step(bufs[0], bufs[1], r, rho, s["alpha"], stream=stream)
+        elif kind == "ca" and k == 1:
+            sg.ca_step(bufs[0], bufs[1], r, rho, "lambda", stream, staging=args.staging)
         elif kind == "ca":
             sg.ca_steps(bufs[0], bufs[1], r, rho, k, "lambda", stream)
+        elif k == 1:
+            sg.diffuse_step(bufs[0], bufs[1], r, rho, s["alpha"], "lambda", stream,
+                            staging=args.staging)
         else:
             sg.diffuse_steps(bufs[0], bufs[1], r, rho, k, s["alpha"], "lambda", stream)
         bufs.reverse()
@@ -459,7 +470,8 @@ def run_stencil_quick(args, sg, torch, dev, stream):
         step()
     total_ms, per = time_launches(step, args.steps, stream)
     return {"workload": f"{args.workload}, level {r}, rho {rho}, {k} step(s) per launch, "
-                        + ("compact layout" if compact else "lambda"),
+                        + ("compact layout" if compact else "lambda")
+                        + (f", {args.staging} staging" if args.staging else ""),
             "unit": UNIT, "value": round(3 ** r * k / (total_ms / args.steps / 1e3) / 1e9, 3),
             "launch_ms_mean": round(statistics.mean(per), 5), "steps": args.steps}
 

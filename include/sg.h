@@ -132,7 +132,13 @@ typedef enum {
 /* Launch options of the *_ex calls.  Zero-initialise, then set fields. */
 typedef struct {
     int order;          /* sg_order; -1 = library default */
-    int store;          /* sg_store (write pass only) */
+    int store;          /* sg_store: the write pass's store path; for sg_ca_step_ex
+                           and sg_diffuse_step_ex (and their k = 1 forms),
+                           SG_STORE_TMA stages each tile and its halo with one
+                           2-D bulk tensor copy instead of 16-byte chunk copies
+                           (CA at rho = 32, 64; diffusion at rho = 16, 32;
+                           other tile sides SG_EUNSUPPORTED); other values are
+                           ignored by the stencils */
     int ctas_per_sm;    /* CTAs per SM of the persistent grid; 0 = occupancy maximum */
     int reserved[5];    /* must be 0 */
 } sg_launch_opts;

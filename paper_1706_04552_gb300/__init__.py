@@ -384,11 +384,13 @@ def map_write_mapped(host_grid, r: int, rho: int, map="lambda", value="hash", va
 
 
 def ca_step(inp, out, r: int, rho: int, map="lambda", stream=None, order=None,
-            ctas_per_sm=None):
+            ctas_per_sm=None, staging=None):
+    """One CA step; staging="tma" stages each tile and its halo with one
+    bulk tensor copy (rho 32 and 64) instead of 16-byte chunk copies."""
     import torch
     _grid_check(inp, r, (torch.uint8,), "in")
     _grid_check(out, r, (torch.uint8,), "out")
-    opts = launch_opts(order, None, ctas_per_sm)
+    opts = launch_opts(order, _staging_store(staging), ctas_per_sm)
     with _on_device(inp):
         _check("sg_ca_step", sg_ca_step_ex(r, rho, _map_id(map), inp.data_ptr(),
                                            out.data_ptr(), opts, _stream_handle(inp, stream)))
@@ -396,16 +398,26 @@ def ca_step(inp, out, r: int, rho: int, map="lambda", stream=None, order=None,
 
 
 def diffuse_step(inp, out, r: int, rho: int, alpha: float = 0.2, map="lambda",
-                 stream=None, order=None, ctas_per_sm=None):
+                 stream=None, order=None, ctas_per_sm=None, staging=None):
+    """One diffusion step; staging="tma" stages each tile and its halo with
+    one bulk tensor copy (rho 16 and 32) instead of 16-byte chunk copies."""
     import torch
     _grid_check(inp, r, (torch.float32,), "in")
     _grid_check(out, r, (torch.float32,), "out")
-    opts = launch_opts(order, None, ctas_per_sm)
+    opts = launch_opts(order, _staging_store(staging), ctas_per_sm)
     with _on_device(inp):
         _check("sg_diffuse_step", sg_diffuse_step_ex(r, rho, _map_id(map), inp.data_ptr(),
                                                      out.data_ptr(), float(alpha), opts,
                                                      _stream_handle(inp, stream)))
     return out
+
+
+def _staging_store(staging):
+    if staging in (None, "chunks"):
+        return None
+    if staging == "tma":
+        return "tma"
+    raise ValueError(f"staging must be None, 'chunks' or 'tma', not {staging!r}")
 
 
 FUSE_MAX = 16     # SG_FUSE_MAX: most steps one sg_ca_steps / sg_diffuse_steps launch fuses

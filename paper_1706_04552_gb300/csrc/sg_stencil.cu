@@ -27,6 +27,7 @@
 // bounding-box map every tile is visited and the cells of an empty tile drop
 // out at their membership test.
 #include "sg_stencil.cuh"
+#include "sg_stencil_tma.cuh"
 
 namespace sg {
 
@@ -283,6 +284,10 @@ cudaError_t launch_ca_t(int r, const uint8_t *in, uint8_t *out, cudaStream_t st,
     const uint64_t groups = (ntiles + TPC - 1) / TPC;
     unsigned grid = 1;
     cudaError_t e;
+    if (cfg.store == kStoreTma) {          // tile and halo by one tensor copy
+        if constexpr (S >= 5) return launch_ca_tma<S, MAP>(r, in, out, ntiles, st, cfg);
+        else return cudaErrorNotSupported;
+    }
     if constexpr (S >= 5) {
         static std::atomic<int> occ{0};
         static std::atomic<uint64_t> attr{0};
@@ -319,6 +324,11 @@ cudaError_t launch_diffuse_t(int r, const float *in, float *out, float alpha,
     const uint64_t groups = (ntiles + TPC - 1) / TPC;
     unsigned grid = 1;
     cudaError_t e;
+    if (cfg.store == kStoreTma) {          // tile and halo by one tensor copy
+        if constexpr (S == 4 || S == 5)
+            return launch_diffuse_tma<S, MAP>(r, in, out, alpha, ntiles, st, cfg);
+        else return cudaErrorNotSupported;
+    }
     if constexpr (S == 4 || S == 5) {
         static std::atomic<int> occ{0};
         static std::atomic<uint64_t> attr{0};

@@ -34,13 +34,19 @@ cudaError_t encode_fn(PFN_cuTensorMapEncodeTiled_v12000 *out)
 
 cudaError_t make_grid_tensor_map(CUtensorMap *map, void *grid, int r, int elem_bytes, int rho)
 {
+    return make_box_tensor_map(map, grid, r, elem_bytes, rho, rho);
+}
+
+cudaError_t make_box_tensor_map(CUtensorMap *map, void *grid, int r, int elem_bytes, int box_w,
+                                int box_h)
+{
     PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     cudaError_t e = encode_fn(&fn);
     if (e != cudaSuccess) return e;
     const cuuint64_t n = 1ull << r;
     const cuuint64_t dims[2] = {n, n};
     const cuuint64_t strides[1] = {n * (cuuint64_t)elem_bytes};
-    const cuuint32_t box[2] = {(cuuint32_t)rho, (cuuint32_t)rho};
+    const cuuint32_t box[2] = {(cuuint32_t)box_w, (cuuint32_t)box_h};
     const cuuint32_t estr[2] = {1, 1};
     const CUtensorMapDataType dt =
         elem_bytes == 1 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;

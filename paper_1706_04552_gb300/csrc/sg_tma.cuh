@@ -141,6 +141,10 @@ __device__ __forceinline__ void fence_proxy_async_shared()
 // Host: 2-D tensor map over a row-major n x n grid with rho x rho boxes.
 cudaError_t make_grid_tensor_map(CUtensorMap *map, void *grid, int r, int elem_bytes, int rho);
 
+// Host: the same with box_w x box_h boxes (box_w elements along a row).
+cudaError_t make_box_tensor_map(CUtensorMap *map, void *grid, int r, int elem_bytes, int box_w,
+                                int box_h);
+
 // Host: device address of the current device's status word (cached per device).
 cudaError_t device_status_ptr(int **ptr);
 

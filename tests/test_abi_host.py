@@ -142,6 +142,17 @@ def test_fused_steps_validate_before_launch(L):
     assert df(8, 16, 0, FAKE, FAKE + 8192, 0.2, 4, bad) == sg.SG_EINVAL
 
 
+def test_tma_staging_needs_a_warp_tile_shape(L):
+    tma = sg.launch_opts(store="tma")
+    for rho in (8, 16):                      # CA: tensor-copy staging at rho 32 and 64 only
+        assert sg.sg_ca_step_ex(8, rho, 0, FAKE, FAKE + 65536, tma) == sg.SG_EUNSUPPORTED
+    for rho in (4, 8, 64):                   # diffusion: rho 16 and 32 only
+        assert sg.sg_diffuse_step_ex(8, rho, 0, FAKE, FAKE + 262144, 0.2, tma) == \
+            sg.SG_EUNSUPPORTED
+    with pytest.raises(ValueError):
+        sg._staging_store("bulk")
+
+
 def test_stencils_reject_intra_block_maps(L):
     for m in ("lambda_lut", "lambda_unroll"):
         mid = sg.MAPS[m]
