@@ -920,6 +920,7 @@ def compare_workloads(sg, torch, dev, stream, w, grid_u8, headline_launch_ms):
             ("store_floor_fill_const_u8", w["map"], w["rho"], w["order"], w["store"], 200,
              "const"),
             ("store_floor_sector_const_u8", w["map"], 64, w["order"], "sector", 200, "const"))
+    write_profile = "profiles/write_legs_r16.md"
     for name, mapk, rho, order, store, steps, vk in legs:
         f = lambda: sg.map_write(grid_u8, r, rho, mapk, vk, w["seed"], stream,
                                  order=order, store=store)
@@ -932,12 +933,14 @@ def compare_workloads(sg, torch, dev, stream, w, grid_u8, headline_launch_ms):
                      "launch_ms": round(statistics.mean(per), 5),
                      "line_GBps": round(touched_bytes(r, 1, 128) /
                                         (statistics.mean(per) / 1e3) / 1e9, 1),
-                     "sector_GBps": round(sector_b / (statistics.mean(per) / 1e3) / 1e9, 1)}
+                     "sector_GBps": round(sector_b / (statistics.mean(per) / 1e3) / 1e9, 1),
+                     "profile": write_profile}
     # the preserving merge pass with the L2 fetching 32 bytes per read miss
     # (a per-context limit of the CUDA driver, restored afterwards): DRAM then
     # reads the touched sectors only, instead of their whole 128-byte lines
     res["lambda_preserving_u8_l2fetch32"] = _with_l2_fetch_granularity(32, lambda: _time_leg(
         sg, grid_u8, r, pv, w["seed"], stream, cells, sector_b, 200))
+    res["lambda_preserving_u8_l2fetch32"]["profile"] = write_profile
     # streaming write bandwidth of the same memory: the whole 4.3 GB grid
     # set by the driver's memset (every byte, in address order)
     res["stream_write_full_grid"] = _memset_rate(torch, grid_u8, stream)
@@ -954,7 +957,8 @@ def compare_workloads(sg, torch, dev, stream, w, grid_u8, headline_launch_ms):
     res["lambda_f32"] = {"map": w["map"], "rho": w["f32_rho"], "store": w["f32_store"],
                          "GCells_s": _rate(cells, ms / 100),
                          "launch_ms": round(statistics.mean(per), 5),
-                         "line_GBps": round(lb / (statistics.mean(per) / 1e3) / 1e9, 1)}
+                         "line_GBps": round(lb / (statistics.mean(per) / 1e3) / 1e9, 1),
+                         "profile": write_profile}
     del g32
     torch.cuda.empty_cache()
     # stencils at level 15
@@ -984,6 +988,8 @@ def compare_workloads(sg, torch, dev, stream, w, grid_u8, headline_launch_ms):
         if mapk == "lambda":
             _add_traffic(res[f"ca_r{rs}_{mapk}"], f"ca_r{rs}_lambda_rho{rho}", "sg_stencil.cu",
                          statistics.mean(per) * 1e3)
+            res[f"ca_r{rs}_{mapk}"]["profile"] = ["profiles/ca_lambda_r15_rho64.md",
+                                                  "profiles/stencil_staging_r15.md"]
         del a, b, bufs
     idx, vals = inputs.uniform_sparse(rs, s["diff_seed"])
     for mapk, rho in (("lambda", s["diff_rho"]), ("bbox", s["bbox_diff_rho"])):
@@ -1007,6 +1013,8 @@ def compare_workloads(sg, torch, dev, stream, w, grid_u8, headline_launch_ms):
         if mapk == "lambda":
             _add_traffic(res[f"diffusion_r{rs}_{mapk}"], f"diffusion_r{rs}_lambda_rho{rho}",
                          "sg_stencil.cu", statistics.mean(per) * 1e3)
+            res[f"diffusion_r{rs}_{mapk}"]["profile"] = ["profiles/diffusion_lambda_r14_rho32.md",
+                                                         "profiles/stencil_staging_r15.md"]
         del a, b, bufs
     torch.cuda.empty_cache()
     # the same step sequences with k steps fused per launch
@@ -1058,6 +1066,9 @@ def fused_stencils(sg, torch, dev, stream, r, single):
         # DRAM bytes of one launch of k steps, spread over its k steps
         _add_traffic(out[f"{kind}_r{r}_fused"], f"{kind}_fused_r{r}_rho{rho}_k{k}", "sg_fused.cu",
                      ms * 1e3 / total * k)
+        out[f"{kind}_r{r}_fused"]["profile"] = ("profiles/ca_fused_bits_r15_rho64_k16.md"
+                                                if kind == "ca" else
+                                                "profiles/diffusion_warp_fused_r14_rho64_k8.md")
         del a, bufs
         torch.cuda.empty_cache()
     return out
