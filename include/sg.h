@@ -239,13 +239,16 @@ SG_API sg_status sg_diffuse_step_ex(int r, int rho, sg_map map, const float *in,
  * host link (NVLink-C2C on Grace), so only the touched chunks cross it: no
  * staging copy of the whole grid is made.  The pointer is checked with
  * cudaPointerGetAttributes before any launch (other memory: SG_EINVAL).
- * Stores: SG_STORE_AUTO (staged where the tile rows allow it, else scatter),
+ * Stores: SG_STORE_AUTO (merge for tile rows of >= 32 bytes on a 32-byte
+ * aligned grid, else staged where the tile rows allow it, else scatter),
  * SG_STORE_STAGED, SG_STORE_SCATTER, or SG_STORE_FILL: here the 32-byte
  * sectors that hold gasket cells are written whole with plain stores (0 at
  * their off-gasket cells) and nothing is read, so only the writes cross the
  * link -- equal to the others on a grid that is 0 off the gasket.
- * SG_STORE_TMA (bulk tensor copies) and the sector modes (SG_STORE_SECTOR,
- * SG_STORE_MERGE, SG_STORE_MASKED) are SG_EUNSUPPORTED here.  The allocation must hold
+ * The sector modes (SG_STORE_SECTOR, SG_STORE_MERGE, SG_STORE_MASKED) run as on
+ * a device grid, with 32-byte plain loads and stores over the link (tile rows
+ * of 32 bytes and a 32-byte aligned grid).  SG_STORE_TMA (bulk tensor copies)
+ * is SG_EUNSUPPORTED here.  The allocation must hold
  * the whole n*n grid (its size cannot be queried; a shorter one is the
  * caller's error, as for a device grid).  Otherwise as sg_map_write_ex; the
  * result is in host memory once the stream has completed.

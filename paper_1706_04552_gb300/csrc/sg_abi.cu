@@ -223,9 +223,10 @@ sg_status sg_map_write_mapped(int r, int rho, sg_map map, sg_dtype dtype, void *
     const int elem = dtype == SG_U8 ? 1 : 4;
     // only the paths that move data with plain loads and stores: fill runs
     // as write-only whole chunks of the staged kernel (no bulk tensor copy)
-    if (cfg.store == SG_STORE_TMA || cfg.store == SG_STORE_SECTOR ||
-        cfg.store == SG_STORE_MERGE || cfg.store == SG_STORE_MASKED)
-        return SG_EUNSUPPORTED;
+    if (cfg.store == SG_STORE_TMA) return SG_EUNSUPPORTED;
+    const bool sector_mode = cfg.store == SG_STORE_SECTOR || cfg.store == SG_STORE_MERGE ||
+                             cfg.store == SG_STORE_MASKED;
+    if (sector_mode && rho * elem < 32) return SG_EUNSUPPORTED;   // 32-byte tile rows
     if ((cfg.store == SG_STORE_STAGED || cfg.store == SG_STORE_FILL) && rho * elem < 16)
         return SG_EUNSUPPORTED;                       // whole chunks need 16-byte tile rows
     // the pointer must be page-locked host memory mapped into the device's
@@ -243,11 +244,17 @@ sg_status sg_map_write_mapped(int r, int rho, sg_map map, sg_dtype dtype, void *
     }
     void *grid = attr.devicePointer;
     if (!aligned(grid, (uintptr_t)elem)) return SG_EINVAL;
+    if (sector_mode && !aligned(grid, 32)) return SG_EINVAL;
     const bool can_stage = rho * elem >= 16 && aligned(grid, 16);
     if ((cfg.store == SG_STORE_STAGED || cfg.store == SG_STORE_FILL) && !can_stage)
         return SG_EUNSUPPORTED;
     if (cfg.store == SG_STORE_FILL) cfg.store = kStoreFillPlain;
-    if (cfg.store == SG_STORE_AUTO) cfg.store = can_stage ? kStoreStaged : kStoreScatter;
+    // the same choice as on a device grid: 32-byte read-merge-write carries
+    // over the link better than staged 16-byte chunks
+    if (cfg.store == SG_STORE_AUTO)
+        cfg.store = rho * elem >= 32 && aligned(grid, 32) ? kStoreMerge
+                    : can_stage                            ? kStoreStaged
+                                                           : kStoreScatter;
     if (dtype == SG_U8)
         return finish(launch_write_u8(r, s, (int)map, (int)value_kind, (uint8_t *)grid,
                                       value_or_seed, (cudaStream_t)stream, cfg));

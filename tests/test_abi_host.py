@@ -238,8 +238,8 @@ def test_mapped_write_refuses_memory_it_cannot_check(L):
     assert sg.sg_map_write_mapped(8, 16, 0, 0, 0, 2, 1) == sg.SG_EINVAL
     assert sg.sg_map_write_mapped(8, 16, 0, 0, ptr, 2, 1,
                                   sg.launch_opts(store="tma")) == sg.SG_EUNSUPPORTED
-    for name in ("sector", "merge", "masked"):
-        assert sg.sg_map_write_mapped(8, 32, 0, 0, ptr, 2, 1,
+    for name in ("sector", "merge", "masked"):             # 16-byte tile rows
+        assert sg.sg_map_write_mapped(8, 16, 0, 0, ptr, 2, 1,
                                       sg.launch_opts(store=name)) == sg.SG_EUNSUPPORTED
     assert sg.sg_map_write_mapped(8, 16, 0, 0, ptr, 2, 1,
                                   sg.launch_opts(store="fill")) == sg.SG_EINVAL

@@ -121,3 +121,21 @@ def test_sector_mode_level16_f32_sampled(orc, rho, mapk):
     want = orc.write_expected_at(r, np.float32, orc.VAL_HASH, 1, xs, ys,
                                  np.zeros(len(xs), dtype=np.float32))
     assert np.array_equal(got.view(np.uint32), want.view(np.uint32))
+
+
+@pytest.mark.parametrize("dtype", ["u8", "f32"])
+def test_sector_modes_on_pinned_host_memory(orc, dtype):
+    # the same kernels writing a grid in page-locked host memory in place
+    r = 11
+    n = 1 << r
+    for store in ("merge", "masked", "sector"):
+        before = (np.zeros((n, n), dtype=np.uint8 if dtype == "u8" else np.float32)
+                  if store == "sector" else _random_grid(n, dtype, 1300))
+        host = torch.from_numpy(before.ravel().copy()).pin_memory()
+        for rho in SECTOR_RHOS[dtype]:
+            host.copy_(torch.from_numpy(before.ravel()))
+            sg.map_write_mapped(host, r, rho, "lambda_unroll", "hash", 8, store=store)
+            torch.cuda.synchronize()
+            want = before.copy()
+            orc.map_write(r, want, orc.VAL_HASH, 8)
+            assert _same(host.numpy().reshape(n, n), want), (store, rho)
