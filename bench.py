@@ -788,7 +788,7 @@ def write_sweep(args):
             "peak_GBps": peak, "peak_kind": peak_kind, "points": rows, "best_per_level": best}
 
 
-SATURATION_RATES = (2000.0, 5000.0, 10000.0, 20000.0, 40000.0, 80000.0)
+SATURATION_RATES = (2000.0, 5000.0, 10000.0, 20000.0, 40000.0, 80000.0, 160000.0, 320000.0)
 SATURATION_P99_MS = 5.0
 
 
@@ -797,7 +797,7 @@ def serving_workload():
     gaskets of levels 6..15, 1-32 steps per request, 40 GB budget) in three
     modes: batched launches of one step, batched launches of up to 16 fused
     steps, and one launch per active gasket.  Each mode serves the configured
-    2000 req/s for 2 s and then traces of 5000 to 80000 req/s (4000 requests
+    2000 req/s for 2 s and then traces of 5000 to 320000 req/s (4000 requests
     or 0.25 s, whichever is longer), stopping after the first rate it does not
     sustain.  A mode sustains an offered rate when it serves the trace at
     >= 95 % of the trace's own arrival rate, with p99 latency <= 5 ms and no
