@@ -788,29 +788,32 @@ def write_sweep(args):
             "peak_GBps": peak, "peak_kind": peak_kind, "points": rows, "best_per_level": best}
 
 
-SATURATION_RATES = (2000.0, 5000.0, 10000.0, 20000.0, 40000.0, 80000.0, 160000.0, 320000.0)
+SATURATION_RATES = (2000.0, 5000.0, 10000.0, 20000.0, 40000.0, 80000.0, 160000.0, 320000.0,
+                    640000.0)
 SATURATION_P99_MS = 5.0
 
 
 def serving_workload():
     """Continuous batching of CA-step requests (Poisson arrivals, 500 resident
-    gaskets of levels 6..15, 1-32 steps per request, 40 GB budget) in three
-    modes: batched launches of one step, batched launches of up to 16 fused
-    steps, and one launch per active gasket.  Each mode serves the configured
-    2000 req/s for 2 s and then traces of 5000 to 320000 req/s (4000 requests
+    gaskets of levels 6..15, 1-32 steps per request, 40 GB budget) in four
+    modes: batched launches of one step and of up to 16 fused steps on the
+    native scheduler core, the fused batches again with the scheduler in
+    Python, and one launch per active gasket.  Each mode serves the configured
+    2000 req/s for 2 s and then traces of 5000 to 640000 req/s (4000 requests
     or 0.25 s, whichever is longer), stopping after the first rate it does not
     sustain.  A mode sustains an offered rate when it serves the trace at
     >= 95 % of the trace's own arrival rate, with p99 latency <= 5 ms and no
     failed request; `max_sustained_rps` is the highest such rate."""
     import dataclasses
     from paper_1706_04552_gb300.serve import ServeConfig, Server, make_trace, summarize
-    modes = (("batched", "batched", 1), ("batched_fused16", "batched", 16),
-             ("per_gasket", "per_gasket", 1))
+    modes = (("batched", "batched", 1, "native"), ("batched_fused16", "batched", 16, "native"),
+             ("batched_fused16_python", "batched", 16, "python"),
+             ("per_gasket", "per_gasket", 1, "python"))
     sat = {"p99_bound_ms": SATURATION_P99_MS, "rates_rps": list(SATURATION_RATES),
            "modes": {}}
     out = {}
-    for name, mode, fuse in modes:
-        base = ServeConfig(mode=mode, fuse=fuse)
+    for name, mode, fuse, engine in modes:
+        base = ServeConfig(mode=mode, fuse=fuse, engine=engine)
         server = Server(base)
         rows, best = [], None
         for rate in SATURATION_RATES:

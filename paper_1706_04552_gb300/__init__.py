@@ -31,7 +31,7 @@ __all__ = [
     "sg_compact_diffuse_step", "sg_compact_ca_steps", "compact_size", "compact_pack",
     "compact_unpack", "compact_map_write", "compact_ca_step", "compact_ca_steps",
     "compact_diffuse_step", "sg_compact_map_write_mapped", "compact_map_write_mapped",
-    "CABatch", "Graph", "BatchPlan",
+    "CABatch", "Graph", "BatchPlan", "Sched", "SchedGasketInfo", "SchedResult",
     "map_write", "map_write_host", "map_write_mapped", "sg_map_write_mapped", "ca_step",
     "diffuse_step", "ca_steps", "diffuse_steps",
     "block_map", "launch_stats",
@@ -89,6 +89,24 @@ class SGError(RuntimeError):
 
 def lib_path() -> str:
     return os.environ.get("SG_LIB", _LIB_PATH)
+
+
+class SchedGasketInfo(ctypes.Structure):
+    """sg_sched_gasket_info of include/sg_sched.h."""
+    _fields_ = [("level", ctypes.c_int32), ("queued", ctypes.c_int32),
+                ("head_left", ctypes.c_int32), ("resident", ctypes.c_int32),
+                ("cur", ctypes.c_uint64), ("nxt", ctypes.c_uint64),
+                ("last_use", ctypes.c_uint64), ("steps_done", ctypes.c_uint64)]
+
+
+class SchedResult(ctypes.Structure):
+    """sg_sched_result of include/sg_sched.h."""
+    _fields_ = [("completed", ctypes.c_void_p), ("completed_gasket", ctypes.c_void_p),
+                ("failed", ctypes.c_void_p), ("failed_gasket", ctypes.c_void_p),
+                ("failed_steps_run", ctypes.c_void_p), ("max_entries", ctypes.c_int32),
+                ("n_completed", ctypes.c_int32), ("n_failed", ctypes.c_int32),
+                ("active", ctypes.c_int32), ("launches", ctypes.c_int32),
+                ("cell_steps", ctypes.c_uint64), ("iteration", ctypes.c_uint64)]
 
 
 def lib() -> ctypes.CDLL:
@@ -175,6 +193,27 @@ def lib() -> ctypes.CDLL:
         L.sg_compact_diffuse_step.restype = i32
         L.sg_abi_version.argtypes = []
         L.sg_abi_version.restype = i32
+        # the serving scheduler's core (include/sg_sched.h)
+        L.sg_batch_ca_plan_host.argtypes = [i32, vp, vp, vp, i32, vp, u64, vp, u64, p_plan]
+        L.sg_batch_ca_plan_host.restype = i32
+        L.sg_sched_create.argtypes = [i32, vp, i32, i32, p_opts, ctypes.POINTER(vp)]
+        L.sg_sched_create.restype = i32
+        L.sg_sched_destroy.argtypes = [vp]
+        L.sg_sched_destroy.restype = i32
+        L.sg_sched_set_buffers.argtypes = [vp, i32, vp, vp]
+        L.sg_sched_set_buffers.restype = i32
+        L.sg_sched_submit.argtypes = [vp, i32, vp, vp, vp]
+        L.sg_sched_submit.restype = i32
+        L.sg_sched_waiting.argtypes = [vp, vp, i32, ctypes.POINTER(i32)]
+        L.sg_sched_waiting.restype = i32
+        L.sg_sched_gasket.argtypes = [vp, i32, ctypes.POINTER(SchedGasketInfo)]
+        L.sg_sched_gasket.restype = i32
+        L.sg_sched_drop.argtypes = [vp, i32, vp, vp, i32, ctypes.POINTER(i32)]
+        L.sg_sched_drop.restype = i32
+        L.sg_sched_step.argtypes = [vp, vp, ctypes.POINTER(SchedResult)]
+        L.sg_sched_step.restype = i32
+        L.sg_sched_inject_launch_failure.argtypes = [vp, i32]
+        L.sg_sched_inject_launch_failure.restype = i32
         _lib = L
         return L
 
@@ -573,6 +612,102 @@ class Graph:
             self.close()
         except Exception:
             pass
+
+
+class Sched:
+    """The serving scheduler's native core (include/sg_sched.h): per-gasket
+    request queues and one batched iteration per step(), built and launched
+    in C++.  Argument marshalling only; arrays are numpy."""
+
+    def __init__(self, levels, rho=32, fuse=1, opts=None):
+        import numpy as np
+        self._np = np
+        lv = np.ascontiguousarray(levels, dtype=np.int32)
+        self.count = int(lv.size)
+        h = ctypes.c_void_p()
+        _check("sg_sched_create", int(lib().sg_sched_create(
+            self.count, lv.ctypes.data, int(rho), int(fuse), _opts_ref(opts), ctypes.byref(h))))
+        self._h = h
+        n = max(self.count, 1)
+        self._done = np.zeros(n, dtype=np.int64)
+        self._done_g = np.zeros(n, dtype=np.int32)
+        self._fail = np.zeros(n, dtype=np.int64)
+        self._fail_g = np.zeros(n, dtype=np.int32)
+        self._fail_ran = np.zeros(n, dtype=np.int32)
+        self._res = SchedResult()
+        self._res.completed = self._done.ctypes.data
+        self._res.completed_gasket = self._done_g.ctypes.data
+        self._res.failed = self._fail.ctypes.data
+        self._res.failed_gasket = self._fail_g.ctypes.data
+        self._res.failed_steps_run = self._fail_ran.ctypes.data
+        self._res.max_entries = n
+        self._wait = np.zeros(n, dtype=np.int32)
+
+    def close(self):
+        if self._h is not None and self._h.value:
+            _check("sg_sched_destroy", int(lib().sg_sched_destroy(self._h)))
+        self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_buffers(self, g, cur_ptr, nxt_ptr):
+        _check("sg_sched_set_buffers", int(lib().sg_sched_set_buffers(
+            self._h, int(g), int(cur_ptr) or None, int(nxt_ptr) or None)))
+
+    def submit(self, gaskets, requests, steps):
+        np = self._np
+        g = np.ascontiguousarray(gaskets, dtype=np.int32)
+        r = np.ascontiguousarray(requests, dtype=np.int64)
+        k = np.ascontiguousarray(steps, dtype=np.int32)
+        if not (g.size == r.size == k.size):
+            raise ValueError("one gasket, request id and step count per request")
+        _check("sg_sched_submit", int(lib().sg_sched_submit(
+            self._h, int(g.size), g.ctypes.data, r.ctypes.data, k.ctypes.data)))
+
+    def waiting(self):
+        n = ctypes.c_int(0)
+        _check("sg_sched_waiting", int(lib().sg_sched_waiting(
+            self._h, self._wait.ctypes.data, int(self._wait.size), ctypes.byref(n))))
+        return self._wait[:n.value].copy()
+
+    def gasket(self, g) -> SchedGasketInfo:
+        info = SchedGasketInfo()
+        _check("sg_sched_gasket", int(lib().sg_sched_gasket(self._h, int(g), ctypes.byref(info))))
+        return info
+
+    def drop(self, g):
+        """Remove gasket g's queued requests: (request ids, steps run of each)."""
+        np = self._np
+        q = self.gasket(g).queued
+        req = np.zeros(max(q, 1), dtype=np.int64)
+        ran = np.zeros(max(q, 1), dtype=np.int32)
+        n = ctypes.c_int(0)
+        _check("sg_sched_drop", int(lib().sg_sched_drop(
+            self._h, int(g), req.ctypes.data, ran.ctypes.data, int(req.size), ctypes.byref(n))))
+        return req[:n.value], ran[:n.value]
+
+    def inject_launch_failure(self, g):
+        _check("sg_sched_inject_launch_failure",
+               int(lib().sg_sched_inject_launch_failure(self._h, int(g))))
+
+    def step(self, stream):
+        """One iteration on `stream` (a torch stream or a raw handle).  Returns
+        the SchedResult; completed()/failed() give its arrays."""
+        st = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        _check("sg_sched_step", int(lib().sg_sched_step(self._h, st, ctypes.byref(self._res))))
+        return self._res
+
+    def completed(self):
+        n = self._res.n_completed
+        return self._done[:n], self._done_g[:n]
+
+    def failed(self):
+        n = self._res.n_failed
+        return self._fail[:n], self._fail_g[:n], self._fail_ran[:n]
 
 
 def launch_stats(r: int, rho: int, map="lambda"):

@@ -23,6 +23,7 @@
 #include <vector>
 
 #include "sg.h"
+#include "sg_sched.h"
 #include "sg_bits.cuh"
 #include "sg_stencil.cuh"
 
@@ -279,20 +280,22 @@ uint64_t sg_batch_workspace_bytes(int count)
     return ws_layout(count).total;
 }
 
-sg_status sg_batch_ca_plan(int count, const int *levels, uint8_t *const *buf_a,
-                           uint8_t *const *buf_b, int rho, void *workspace,
-                           uint64_t workspace_bytes, sg_batch_plan *plan, void *stream)
+sg_status sg_batch_ca_plan_host(int count, const int *levels, uint8_t *const *buf_a,
+                                uint8_t *const *buf_b, int rho, void *host_image,
+                                uint64_t image_bytes, void *workspace, uint64_t workspace_bytes,
+                                sg_batch_plan *plan)
 {
-    if (plan == nullptr || levels == nullptr || buf_a == nullptr || buf_b == nullptr)
+    if (plan == nullptr || levels == nullptr || buf_a == nullptr || buf_b == nullptr ||
+        host_image == nullptr)
         return SG_EINVAL;
     if (count < 1 || count > kMaxBatch) return SG_EINVAL;
     if (rho != 16 && rho != 32 && rho != 64) return SG_EUNSUPPORTED;
     if (workspace == nullptr || ((uintptr_t)workspace & 15) != 0) return SG_EINVAL;
     const WsLayout L = ws_layout(count);
-    if (workspace_bytes < L.total) return SG_EINVAL;
+    if (workspace_bytes < L.total || image_bytes < L.total) return SG_EINVAL;
     int s = 0;
     while ((1 << s) < rho) ++s;
-    std::vector<uint32_t> prefix(count + 1);
+    // validate everything before the image is touched
     uint64_t total = 0;
     int max_level = 0;
     for (int i = 0; i < count; ++i) {
@@ -300,25 +303,22 @@ sg_status sg_batch_ca_plan(int count, const int *levels, uint8_t *const *buf_a,
         if (r < s || r > 16) return SG_EINVAL;        // every gasket holds whole tiles
         if (buf_a[i] == nullptr || buf_b[i] == nullptr || buf_a[i] == buf_b[i]) return SG_EINVAL;
         if (((uintptr_t)buf_a[i] & 15) || ((uintptr_t)buf_b[i] & 15)) return SG_EINVAL;
-        prefix[i] = (uint32_t)total;
         total += (uint64_t)pow3i(r - s);
         max_level = std::max(max_level, r);
         if (total >= (1ull << 32)) return SG_EINVAL;
     }
-    prefix[count] = (uint32_t)total;
-    // host image of the workspace, copied in one transfer (pageable memory:
-    // the call returns once the bytes are staged, so the vector may go)
-    std::vector<unsigned char> img(L.total, 0);
-    std::memcpy(img.data() + L.prefix, prefix.data(), 4ull * (count + 1));
-    std::memcpy(img.data() + L.level, levels, 4ull * count);
+    unsigned char *img = static_cast<unsigned char *>(host_image);
+    std::memset(img, 0, L.total);
+    uint32_t run = 0;
     for (int i = 0; i < count; ++i) {
+        std::memcpy(img + L.prefix + 4ull * i, &run, 4);
+        run += (uint32_t)pow3i(levels[i] - s);
         const uint64_t pa = (uint64_t)(uintptr_t)buf_a[i], pb = (uint64_t)(uintptr_t)buf_b[i];
-        std::memcpy(img.data() + L.a + 8ull * i, &pa, 8);
-        std::memcpy(img.data() + L.b + 8ull * i, &pb, 8);
+        std::memcpy(img + L.a + 8ull * i, &pa, 8);
+        std::memcpy(img + L.b + 8ull * i, &pb, 8);
     }
-    cudaError_t e = cudaMemcpyAsync(workspace, img.data(), L.total, cudaMemcpyHostToDevice,
-                                    (cudaStream_t)stream);
-    if (e != cudaSuccess) return cuda_fail(e);
+    std::memcpy(img + L.prefix + 4ull * count, &run, 4);
+    std::memcpy(img + L.level, levels, 4ull * count);
     *plan = sg_batch_plan{};
     plan->workspace = workspace;
     plan->workspace_bytes = workspace_bytes;
@@ -326,6 +326,26 @@ sg_status sg_batch_ca_plan(int count, const int *levels, uint8_t *const *buf_a,
     plan->rho = rho;
     plan->total_tiles = (uint32_t)total;
     plan->max_level = (uint32_t)max_level;
+    return SG_OK;
+}
+
+sg_status sg_batch_ca_plan(int count, const int *levels, uint8_t *const *buf_a,
+                           uint8_t *const *buf_b, int rho, void *workspace,
+                           uint64_t workspace_bytes, sg_batch_plan *plan, void *stream)
+{
+    if (count < 1 || count > kMaxBatch) return SG_EINVAL;
+    // host image of the workspace, copied in one transfer (pageable memory:
+    // the call returns once the bytes are staged, so the vector may go)
+    const WsLayout L = ws_layout(count);
+    std::vector<unsigned char> img(L.total);
+    sg_batch_plan p;
+    const sg_status st = sg_batch_ca_plan_host(count, levels, buf_a, buf_b, rho, img.data(),
+                                               L.total, workspace, workspace_bytes, &p);
+    if (st != SG_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(workspace, img.data(), L.total, cudaMemcpyHostToDevice,
+                                    (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *plan = p;
     return SG_OK;
 }
 

@@ -25,6 +25,17 @@ request, so every result is still the plain per-gasket step sequence.
 mode="per_gasket" runs the same scheduler with one single-gasket launch per
 active gasket per iteration instead of the batched launch, for comparison.
 
+Two engines run the batched mode.  engine="native" hands the queues and the
+iteration to the C++ core (include/sg_sched.h): Python admits arrivals in
+slices, keeps residency (loads and evictions) and stamps completions, and
+each iteration's grouping, work lists and launches are built natively.  Its
+work lists reach the device by an asynchronous copy from page-locked memory,
+so up to `pipeline` iterations are in flight: the host prepares the next one
+while the device runs the current one, and a request's completion is stamped
+when the host sees its iteration's event complete.  engine="python" is the
+same policy written out in Python, one iteration at a time (and the one the
+per-gasket comparison uses).
+
 Failures are contained on the host.  A launch that the library refuses
 (an SGError from its C ABI) fails the head requests of the gaskets it was
 for: nothing ran, their states stay as they were, and the rest of the
@@ -62,6 +73,8 @@ class ServeConfig:
     rho: int = 32
     mode: str = "batched"             # or "per_gasket"
     fuse: int = 1                     # most steps one iteration advances a gasket (batched)
+    engine: str = "native"            # batched mode: "native" (sg_sched) or "python"
+    pipeline: int = 2                 # native: iterations in flight on the stream
 
 
 def gasket_levels(cfg: ServeConfig) -> np.ndarray:
@@ -152,6 +165,12 @@ class Server:
         self._pa = np.zeros(cnt, dtype=np.uint64)
         self._pb = np.zeros(cnt, dtype=np.uint64)
         self._plan = sg.BatchPlan()
+        if cfg.engine not in ("native", "python"):
+            raise ValueError("engine must be 'native' or 'python'")
+        if cfg.pipeline < 1:
+            raise ValueError("pipeline must be >= 1")
+        self.native = cfg.mode == "batched" and cfg.engine == "native"
+        self.sched = sg.Sched(levels, cfg.rho, cfg.fuse) if self.native else None
         self.tick = 0
         self._preload()
         self._warm_up()
@@ -191,13 +210,28 @@ class Server:
         self.stream.synchronize()
 
     # ------------------------------------------------------------ residency
+    def _idle(self, g):
+        return (self.sched.gasket(g.gid).queued == 0) if self.native else not g.queue
+
+    def _last_use(self, g):
+        return int(self.sched.gasket(g.gid).last_use) if self.native else g.last_use
+
+    def _sync_bufs(self, g):
+        """Native engine: point g.cur at the buffer the scheduler holds as
+        current (it swaps the two after every iteration that advances g)."""
+        if self.native and g.resident and self.sched.gasket(g.gid).cur != g.cur.data_ptr():
+            g.cur, g.nxt = g.nxt, g.cur
+
     def _evict_one(self, protect):
-        idle = [g for g in self.gaskets if g.resident and not g.queue and g.gid not in protect]
+        idle = [g for g in self.gaskets if g.resident and g.gid not in protect and self._idle(g)]
         if not idle:
             return False
-        v = min(idle, key=lambda g: g.last_use)
+        v = min(idle, key=self._last_use)
+        self._sync_bufs(v)
         v.host.copy_(v.cur, non_blocking=True)           # current state back to host
         self.stream.synchronize()
+        if self.native:
+            self.sched.set_buffers(v.gid, 0, 0)
         v.cur = v.nxt = None
         v.resident = False
         self.used -= v.device_bytes
@@ -215,6 +249,8 @@ class Server:
         g.nxt = torch.zeros(g.n2, dtype=torch.uint8, device=self.dev)
         g.cur.copy_(g.host, non_blocking=True)
         g.resident = True
+        if self.native:
+            self.sched.set_buffers(g.gid, g.cur.data_ptr(), g.nxt.data_ptr())
         self.used += g.device_bytes
         self.loads += 1
         return True
@@ -270,7 +306,13 @@ class Server:
         """Serve a trace (arrival s, gasket, steps).  on_complete(req, gasket)
         is called right after a request's last step (state in gasket.cur).
         Returns per-request arrival/completion times, which requests failed,
-        and counters."""
+        and counters.  busy_s is device time: CUDA events around every
+        iteration's work on the serving stream."""
+        if self.native:
+            return self._run_native(trace, on_complete)
+        torch = self.torch
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
         t_arr, g_id, k_steps = trace
         nreq = len(t_arr)
         done_at = np.full(nreq, np.nan)
@@ -323,11 +365,13 @@ class Server:
             for g in active:
                 g.advance = self._steps_for(g) if self.cfg.mode == "batched" else 1
             tb = time.perf_counter()
+            ev0.record(self.stream)
             n_launch, refused = self._step(active)
+            ev1.record(self.stream)
             launches += n_launch
             self.stream.synchronize()
             te = time.perf_counter()
-            busy += te - tb
+            busy += ev0.elapsed_time(ev1) / 1e3
             iters += 1
             tdone = te - t0
             for g in active:
@@ -363,10 +407,118 @@ class Server:
                 "busy_s": busy, "cell_steps": cells, "latency_s": lat, "arrival_s": t_arr,
                 "failed": failed, "evictions": self.evictions, "loads": self.loads}
 
+    def _run_native(self, trace, on_complete):
+        """run() on the native core (sg_sched): admission in slices, up to
+        cfg.pipeline iterations in flight, completions stamped when their
+        iteration's event is seen complete."""
+        import collections
+        torch, sched, sg = self.torch, self.sched, self.sg
+        t_arr, g_id, k_steps = trace
+        nreq = len(t_arr)
+        t_arr = np.asarray(t_arr, dtype=np.float64)
+        gid32 = np.ascontiguousarray(g_id, dtype=np.int32)
+        k32 = np.ascontiguousarray(k_steps, dtype=np.int32)
+        ids = np.arange(nreq, dtype=np.int64)
+        done_at = np.full(nreq, np.nan)
+        failed = np.zeros(nreq, dtype=bool)
+        depth = int(self.cfg.pipeline)
+        # one pair of events per iteration in flight, reused round robin
+        ring = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(depth)]
+        inflight = collections.deque()         # (events, requests it completes)
+        busy = 0.0
+        iters = launches = cells = 0
+        nxt = 0
+        remaining = nreq
+        t0 = time.perf_counter()
+
+        def retire(block):
+            # stamp the iterations that have finished (the oldest one waited
+            # for when block); returns how many requests that completed
+            nonlocal busy, remaining
+            while inflight:
+                (e0, e1), done = inflight[0]
+                if block:
+                    e1.synchronize()
+                    block = False
+                elif not e1.query():
+                    return
+                busy += e0.elapsed_time(e1) / 1e3
+                done_at[done] = time.perf_counter() - t0
+                remaining -= len(done)
+                inflight.popleft()
+
+        while remaining:
+            now = time.perf_counter() - t0
+            if nxt < nreq:
+                j = int(np.searchsorted(t_arr, now, side="right"))
+                if j > nxt:
+                    sched.submit(gid32[nxt:j], ids[nxt:j], k32[nxt:j])
+                    nxt = j
+            unfit = False
+            for g in sched.waiting().tolist():
+                gg = self.gaskets[g]
+                try:
+                    ok = self._make_resident(gg, set())
+                except Exception as e:          # the copy in failed: its requests fail
+                    req, ran = sched.drop(g)
+                    tnow = time.perf_counter() - t0
+                    for rq, kr in zip(req.tolist(), ran.tolist()):
+                        self.failures.append((rq, g, kr, str(e)))
+                    failed[req] = True
+                    done_at[req] = tnow
+                    remaining -= len(req)
+                    continue
+                unfit |= not ok
+            if len(inflight) >= depth:
+                retire(True)
+            e0, e1 = ring[iters % depth]
+            e0.record(self.stream)
+            res = sched.step(self.stream)
+            if res.iteration == 0:              # nothing resident to advance
+                retire(False)
+                if unfit and not inflight:
+                    raise RuntimeError("a requested gasket does not fit the device budget")
+                if not inflight and nxt < nreq:
+                    dt = t_arr[nxt] - (time.perf_counter() - t0)
+                    if dt > 0:
+                        time.sleep(min(dt, 0.0001))
+                continue
+            e1.record(self.stream)
+            iters += 1
+            launches += int(res.launches)
+            cells += int(res.cell_steps)
+            done, done_g = sched.completed()
+            done = done.copy()
+            if res.n_failed:                    # launches refused: nothing ran for them
+                freq, fg, fran = sched.failed()
+                err = "batched launch refused: " + sg.lib().sg_last_error_string().decode()
+                tnow = time.perf_counter() - t0
+                for rq, g, kr in zip(freq.tolist(), fg.tolist(), fran.tolist()):
+                    self.failures.append((rq, g, kr, err))
+                failed[freq] = True
+                done_at[freq] = tnow
+                remaining -= int(res.n_failed)
+            if on_complete is not None:
+                for rq, g in zip(done.tolist(), done_g.tolist()):
+                    gg = self.gaskets[g]
+                    self._sync_bufs(gg)
+                    on_complete(rq, gg)
+            inflight.append(((e0, e1), done))
+            retire(False)
+        wall = time.perf_counter() - t0
+        for g in self.gaskets:
+            self._sync_bufs(g)
+        lat = done_at - t_arr
+        return {"requests": nreq, "wall_s": wall, "iterations": iters, "launches": launches,
+                "busy_s": busy, "cell_steps": cells, "latency_s": lat, "arrival_s": t_arr,
+                "failed": failed, "evictions": self.evictions, "loads": self.loads}
+
     def state_of(self, gid):
         """Current state of gasket gid (host numpy copy)."""
         g = self.gaskets[gid]
         n = 1 << g.level
+        self._sync_bufs(g)
         src = g.cur if g.resident else g.host
         self.stream.synchronize()
         return src.cpu().numpy().reshape(n, n)

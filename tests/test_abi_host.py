@@ -1,9 +1,14 @@
-"""The C ABI on the host: libsg.so loads, exports every symbol include/sg.h
-declares, reports its status strings and launch accounting, and rejects bad
+"""The C ABI on the host: libsg.so loads, exports every symbol the headers
+under include/ declare, reports its status strings and launch accounting, and rejects bad
 arguments before launching anything (no call here reaches a kernel)."""
+import ctypes
+import glob
 import os
 import re
+import subprocess
+import sys
 
+import numpy as np
 import pytest
 
 from conftest import ROOT
@@ -19,8 +24,11 @@ def L():
 
 
 def _declared_symbols():
-    text = open(os.path.join(ROOT, "include", "sg.h")).read()
-    return sorted(set(re.findall(r"SG_API\s+[\w\s\*]+?\b(sg_\w+)\s*\(", text)))
+    names = set()
+    for h in sorted(glob.glob(os.path.join(ROOT, "include", "*.h"))):
+        text = open(h).read()
+        names |= set(re.findall(r"SG_API\s+[\w\s\*]+?\b(sg_\w+)\s*\(", text))
+    return sorted(names)
 
 
 def test_header_declares_the_boundary():
@@ -42,7 +50,15 @@ def test_abi_version_and_status_strings(L):
     for code in range(1, 6):
         assert sg.sg_status_str(code).startswith("SG_E")
     assert "unknown" in sg.sg_status_str(99)
-    assert sg.lib().sg_last_error_string() == b""
+    # the last error message is process-wide: empty in a fresh process, or
+    # whatever an earlier test's refused call left there
+    msg = sg.lib().sg_last_error_string()
+    assert isinstance(msg, bytes)
+    fresh = subprocess.run(
+        [sys.executable, "-c", "import paper_1706_04552_gb300 as sg; "
+         "print(sg.lib().sg_last_error_string())"],
+        cwd=ROOT, capture_output=True, text=True, timeout=120)
+    assert fresh.returncode == 0 and fresh.stdout.strip() == "b''", fresh.stderr
 
 
 @pytest.mark.parametrize("r,rho", [(0, 1), (4, 2), (8, 8), (10, 16), (12, 32), (16, 64)])
@@ -298,3 +314,59 @@ def test_compact_mapped_write_refuses_memory_it_cannot_check(L):
     assert sg.sg_compact_map_write_mapped(17, 16, u8, buf.ctypes.data, 2, 1) == sg.SG_EINVAL
     assert sg.sg_compact_map_write_mapped(8, 16, u8, buf.ctypes.data, 2, 1,
                                           sg.launch_opts(store="fill")) == sg.SG_EUNSUPPORTED
+
+
+def test_sched_headers_declare_the_serving_core():
+    names = _declared_symbols()
+    for want in ("sg_batch_ca_plan_host", "sg_sched_create", "sg_sched_destroy",
+                 "sg_sched_set_buffers", "sg_sched_submit", "sg_sched_waiting",
+                 "sg_sched_gasket", "sg_sched_drop", "sg_sched_step",
+                 "sg_sched_inject_launch_failure"):
+        assert want in names
+
+
+def test_sched_argument_checks_on_the_host(L):
+    # everything refused before any CUDA call: no device is needed
+    lv = (ctypes.c_int * 3)(6, 7, 8)
+    h = ctypes.c_void_p()
+    assert L.sg_sched_create(0, lv, 32, 1, None, ctypes.byref(h)) == sg.SG_EINVAL
+    assert L.sg_sched_create(3, lv, 48, 1, None, ctypes.byref(h)) == sg.SG_EUNSUPPORTED
+    assert L.sg_sched_create(3, lv, 32, 0, None, ctypes.byref(h)) == sg.SG_EINVAL
+    assert L.sg_sched_create(3, lv, 32, 17, None, ctypes.byref(h)) == sg.SG_EINVAL
+    low = (ctypes.c_int * 3)(6, 4, 8)                  # level 4 holds no 32 x 32 tile
+    assert L.sg_sched_create(3, low, 32, 1, None, ctypes.byref(h)) == sg.SG_EINVAL
+    assert L.sg_sched_create(3, lv, 32, 1, None, None) == sg.SG_EINVAL
+    assert L.sg_sched_destroy(None) == sg.SG_EINVAL
+    assert L.sg_sched_step(None, None, None) == sg.SG_EINVAL
+    assert L.sg_sched_submit(None, 0, None, None, None) == sg.SG_EINVAL
+
+
+def test_batch_plan_host_writes_the_work_list(L):
+    # the work list image: prefix sums of 3^(r - s), levels, both pointers
+    levels = [5, 6, 8]
+    rho, s = 32, 5
+    n = len(levels)
+    nbytes = int(L.sg_batch_workspace_bytes(n))
+    img = (ctypes.c_ubyte * nbytes)()
+    lv = (ctypes.c_int * n)(*levels)
+    pa = (ctypes.c_void_p * n)(0x1000, 0x2000, 0x3000)
+    pb = (ctypes.c_void_p * n)(0x1100, 0x2100, 0x3100)
+    plan = sg.BatchPlan()
+    st = L.sg_batch_ca_plan_host(n, lv, pa, pb, rho, img, nbytes, 0x10000, nbytes,
+                                 ctypes.byref(plan))
+    assert st == sg.SG_OK
+    assert plan.count == n and plan.rho == rho and plan.max_level == 8
+    tiles = [3 ** (r - s) for r in levels]
+    assert plan.total_tiles == sum(tiles)
+    raw = bytes(img)
+    prefix = np.frombuffer(raw[:4 * (n + 1)], dtype=np.uint32)
+    assert list(prefix) == [0, tiles[0], tiles[0] + tiles[1], sum(tiles)]
+    # the image is too small, a pointer is unaligned, a level is below the tile
+    assert L.sg_batch_ca_plan_host(n, lv, pa, pb, rho, img, nbytes - 16, 0x10000, nbytes,
+                                   ctypes.byref(plan)) == sg.SG_EINVAL
+    bad = (ctypes.c_void_p * n)(0x1000, 0x2008, 0x3000)
+    assert L.sg_batch_ca_plan_host(n, lv, bad, pb, rho, img, nbytes, 0x10000, nbytes,
+                                   ctypes.byref(plan)) == sg.SG_EINVAL
+    low = (ctypes.c_int * n)(4, 6, 8)
+    assert L.sg_batch_ca_plan_host(n, low, pa, pb, rho, img, nbytes, 0x10000, nbytes,
+                                   ctypes.byref(plan)) == sg.SG_EINVAL

@@ -51,16 +51,19 @@ def _serve_and_check(orc, cfg, expect_evictions=False):
     return s
 
 
-def test_serve_batched_same_alone_and_in_the_mix(orc):
-    cfg = ServeConfig(gaskets=48, level_max=11, rate=2000.0, duration=0.25, seed=7)
+@pytest.mark.parametrize("engine", ["native", "python"])
+def test_serve_batched_same_alone_and_in_the_mix(orc, engine):
+    cfg = ServeConfig(gaskets=48, level_max=11, rate=2000.0, duration=0.25, seed=7,
+                      engine=engine)
     s = _serve_and_check(orc, cfg)
     assert s["launches"] == s["iterations"]
 
 
-def test_serve_with_evictions_to_host(orc):
+@pytest.mark.parametrize("engine,pipeline", [("native", 2), ("native", 1), ("python", 1)])
+def test_serve_with_evictions_to_host(orc, engine, pipeline):
     # a budget of a few MB forces idle gaskets out to pinned host memory
     cfg = ServeConfig(gaskets=32, level_max=10, rate=3000.0, duration=0.2, seed=9,
-                      budget_bytes=3 << 20)
+                      budget_bytes=3 << 20, engine=engine, pipeline=pipeline)
     _serve_and_check(orc, cfg, expect_evictions=True)
 
 
@@ -71,10 +74,12 @@ def test_serve_per_gasket_mode(orc):
     assert s["launches"] >= s["iterations"]
 
 
-def test_serve_fused_same_alone_and_in_the_mix(orc):
+@pytest.mark.parametrize("engine,pipeline", [("native", 2), ("native", 4), ("python", 1)])
+def test_serve_fused_same_alone_and_in_the_mix(orc, engine, pipeline):
     # iterations advance gaskets by up to 16 fused steps, grouped by the steps
     # left in each head request; every result still equals stepping alone
-    cfg = ServeConfig(gaskets=48, level_max=11, rate=3000.0, duration=0.25, seed=8, fuse=16)
+    cfg = ServeConfig(gaskets=48, level_max=11, rate=3000.0, duration=0.25, seed=8, fuse=16,
+                      engine=engine, pipeline=pipeline)
     s = _serve_and_check(orc, cfg)
     assert s["launches"] >= s["iterations"]
 
@@ -85,14 +90,16 @@ def test_serve_fused_with_evictions_to_host(orc):
     _serve_and_check(orc, cfg, expect_evictions=True)
 
 
-def test_serve_contains_host_side_failures(orc):
+@pytest.mark.parametrize("engine", ["native", "python"])
+def test_serve_contains_host_side_failures(orc, engine):
     # failures injected on the host: one batched launch is refused (an SGError
-    # from the C ABI, as a bad plan would give) and one gasket's copy onto the
-    # device fails.  The affected requests are reported failed; every other
-    # request still equals stepping its gasket alone through the steps that
-    # actually ran, and the trace is served to the end.
+    # from the C ABI, as a bad plan would give; in the native core its
+    # host-side injection) and one gasket's copy onto the device fails.  The
+    # affected requests are reported failed; every other request still equals
+    # stepping its gasket alone through the steps that actually ran, and the
+    # trace is served to the end.
     cfg = ServeConfig(gaskets=24, level_max=9, rate=3000.0, duration=0.15, seed=13,
-                      budget_bytes=1 << 20, fuse=4)
+                      budget_bytes=1 << 20, fuse=4, engine=engine)
     server = Server(cfg)
     initial = [g.host.clone() for g in server.gaskets]
     trace = make_trace(cfg)
@@ -117,7 +124,11 @@ def test_serve_contains_host_side_failures(orc):
             raise RuntimeError("injected copy failure")
         return make_resident(g, protect)
 
-    server._launch = failing_launch
+    if engine == "native":
+        server.sched.inject_launch_failure(launch_victim)
+        fired["launch"] += 1
+    else:
+        server._launch = failing_launch
     server._make_resident = failing_resident
     snap = {}
 
