@@ -842,30 +842,33 @@ def _rate(cells, ms):
     return round(cells / (ms / 1e3) / 1e9, 3)
 
 
-def _memset_rate(torch, t, stream, reps=4):
-    """Write bandwidth of cuMemsetD8Async over a whole device tensor (the
-    fastest way to write every byte of it): bytes / best event-timed call."""
+def _memset_rate(torch, t, stream, reps=4, nbytes=None):
+    """Write bandwidth of cuMemsetD8Async over a whole device tensor, or over
+    its first `nbytes` bytes (the fastest way to write every byte of it):
+    bytes / best event-timed call."""
     import ctypes
     try:
         cu = ctypes.CDLL("libcuda.so.1")
     except OSError as e:
         return {"unavailable": f"libcuda: {e}"}
+    whole = nbytes is None
+    nbytes = t.numel() * t.element_size() if whole else min(int(nbytes), t.numel() *
+                                                              t.element_size())
     ms = []
     for i in range(reps + 1):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         rc = cu.cuMemsetD8Async(ctypes.c_uint64(t.data_ptr()), ctypes.c_ubyte(i & 0xFF),
-                                ctypes.c_size_t(t.numel() * t.element_size()),
-                                ctypes.c_void_p(stream.cuda_stream))
+                                ctypes.c_size_t(nbytes), ctypes.c_void_p(stream.cuda_stream))
         e1.record(stream)
         e1.synchronize()
         if rc != 0:
             return {"unavailable": f"cuMemsetD8Async returned {rc}"}
         ms.append(e0.elapsed_time(e1))
     best = min(ms[1:])
-    nbytes = t.numel() * t.element_size()
+    what = "the whole grid" if whole else "the grid's first bytes, contiguous"
     return {"bytes": nbytes, "ms": round(best, 4), "GBps": round(nbytes / (best / 1e3) / 1e9, 1),
-            "how": "cuMemsetD8Async over the whole grid, best of 4 after one warm-up"}
+            "how": f"cuMemsetD8Async over {what}, best of 4 after one warm-up"}
 
 
 def _add_traffic(entry, key, unit, launch_us):
@@ -963,6 +966,10 @@ def compare_workloads(sg, torch, dev, stream, w, grid_u8, headline_launch_ms):
     # streaming write bandwidth of the same memory: the whole 4.3 GB grid
     # set by the driver's memset (every byte, in address order)
     res["stream_write_full_grid"] = _memset_rate(torch, grid_u8, stream)
+    # the same number of bytes as the touched sectors, written contiguously:
+    # what the pass would cost if its sectors were not scattered over the grid
+    res["stream_write_sector_bytes_contiguous"] = _memset_rate(
+        torch, grid_u8, stream, nbytes=touched_bytes(r, 1, 32))
     grid_u8.zero_()
     res["speedup_lambda_over_bbox"] = round(res["bbox_u8"]["launch_ms"] / headline_launch_ms, 3)
     # float32 grid (17.2 GB)
