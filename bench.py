@@ -1094,7 +1094,7 @@ def fused_stencils(sg, torch, dev, stream, r, single):
                      ms * 1e3 / total * k)
         out[f"{kind}_r{r}_fused"]["profile"] = ("profiles/ca_fused_bits_r15_rho64_k16.md"
                                                 if kind == "ca" else
-                                                "profiles/diffusion_warp_fused_r14_rho64_k8.md")
+                                                "profiles/diffusion_warp_fused_r14_rho32_k8.md")
         del a, bufs
         torch.cuda.empty_cache()
     return out

@@ -102,15 +102,20 @@ __device__ __forceinline__ void bits_stage(uint32_t *bits, uint32_t *mask,
 
 // Word w of a staged row and its left and right neighbour planes (bit j <-
 // bit j-1 and bit j <- bit j+1).  p points at the word; its neighbours are
-// read at p[-1] and p[+1] and masked with kl / kr, which are 0 at the row's
-// ends (there the reads land in the next or previous row, or in a pad word).
+// read at p[-1] and p[+1].  At the row's ends those reads land in the
+// previous or next row (or in a pad word), so the outermost staged column on
+// each side takes a wrong neighbour.  That costs nothing: the staged halo is
+// 16 columns wide and a wrong value moves one column per step, so after
+// k <= 16 steps it has reached at most the column next to the tile -- the
+// light cone that already limits every halo cell (their own neighbours
+// outside the staged window are not there either).
 struct BitRow {
     uint32_t v, l, r;
 };
-__device__ __forceinline__ BitRow bit_row(const uint32_t *p, uint32_t kl, uint32_t kr)
+__device__ __forceinline__ BitRow bit_row(const uint32_t *p)
 {
-    const uint32_t v = p[0], vl = p[-1] & kl, vr = p[1] & kr;
-    return BitRow{v, __funnelshift_l(vl, v, 1), __funnelshift_r(v, vr, 1)};
+    const uint32_t v = p[0];
+    return BitRow{v, __funnelshift_l(p[-1], v, 1), __funnelshift_r(v, p[1], 1)};
 }
 
 // One step over the window rows [s, ROWS - s): src -> dst.  The lanes form
@@ -131,13 +136,12 @@ __device__ __forceinline__ void bits_ca_step(const uint32_t *src, uint32_t *dst,
     const int first = s + g * run;
     const int last = min(first + run, B::ROWS - s);
     if (first >= last) return;
-    const uint32_t kl = w > 0 ? 0xFFFFFFFFu : 0u, kr = w < B::WPR - 1 ? 0xFFFFFFFFu : 0u;
     const uint32_t *p = src + (first - 1) * B::WPR + w;
-    const BitRow u = bit_row(p, kl, kr);
+    const BitRow u = bit_row(p);
     uint32_t us, uc;                                  // 3-sum of the row above
     full_add(u.l, u.v, u.r, us, uc);
     p += B::WPR;
-    BitRow m = bit_row(p, kl, kr);
+    BitRow m = bit_row(p);
     uint32_t ms3, mc3;                                // 3-sum of the current row
     full_add(m.l, m.v, m.r, ms3, mc3);
     const uint32_t *pk = mask + first * B::WPR + w;
@@ -145,7 +149,7 @@ __device__ __forceinline__ void bits_ca_step(const uint32_t *src, uint32_t *dst,
 #pragma unroll 2
     for (int row = first; row < last; ++row) {
         p += B::WPR;
-        const BitRow d = bit_row(p, kl, kr);
+        const BitRow d = bit_row(p);
         uint32_t ds3, dc3;
         full_add(d.l, d.v, d.r, ds3, dc3);
         const uint32_t ms2 = m.l ^ m.r, mc2 = m.l & m.r;   // 2-sum of the current row

@@ -43,7 +43,7 @@ STENCILS = dict(levels=(14, 15), ca_p=0.3, ca_seed=0, ca_steps=256,
                 diff_seed=0, diff_steps=100, alpha=0.2,
                 ca_rho=64, diff_rho=32, bbox_ca_rho=64, bbox_diff_rho=64,
                 # the same sequences with k steps fused per launch
-                ca_fuse=16, ca_fuse_rho=64, diff_fuse=8, diff_fuse_rho=64)
+                ca_fuse=16, ca_fuse_rho=64, diff_fuse=8, diff_fuse_rho=32)
 
 # The same write pass and stencil sequences on compact arrays (the 3^r
 # gasket cells only, tiles in launch order): 43 MB instead of 4.3 GB for the
