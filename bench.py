@@ -249,6 +249,16 @@ def recorded_traffic(kernel_key: str, unit: str):
 # --------------------------------------------------------------------------
 # timing on the device
 # --------------------------------------------------------------------------
+def balanced_chunks(total: int, k: int) -> list[int]:
+    """Split `total` steps into the fewest launches of at most k steps, as
+    even as they go (100 steps at k = 8: nine launches of 8 and four of 7).
+    A launch of few steps costs nearly as much as one of k (both make one
+    pass over the grid), so a short remainder launch is avoided."""
+    n = -(-total // k)
+    base, extra = divmod(total, n)
+    return [base + 1] * extra + [base] * (n - extra)
+
+
 def time_launches(fn, steps: int, stream):
     """Run fn() `steps` times on `stream`; CUDA events around the whole run
     and around every launch.  Returns (total ms, list of per-launch ms)."""
@@ -1068,7 +1078,7 @@ def fused_stencils(sg, torch, dev, stream, r, single):
         a = torch.zeros(n * n, dtype=dt, device=dev)
         a[torch.from_numpy(idx).to(dev)] = torch.from_numpy(vals).to(dev)
         bufs = [a, torch.zeros_like(a)]
-        chunks = [k] * (total // k) + ([total % k] if total % k else [])
+        chunks = balanced_chunks(total, k)
         pos = [0]
 
         def launch():
@@ -1087,6 +1097,7 @@ def fused_stencils(sg, torch, dev, stream, r, single):
         base = single.get(f"{kind}_r{r}_lambda", {}).get("GCells_s")
         out[f"{kind}_r{r}_fused"] = {
             "rho": rho, "steps": total, "steps_per_launch": k, "launches": len(chunks),
+            "launch_steps": chunks,
             "us_per_step": round(ms * 1e3 / total, 2), "GCells_s": round(rate, 3),
             "speedup_vs_single_step": round(rate / base, 3) if base else None}
         # DRAM bytes of one launch of k steps, spread over its k steps
@@ -1152,7 +1163,7 @@ def compact_layout(sg, torch, dev, stream, rw, rs, single, headline_launch_ms):
         if kind == "ca":
             # the same sequence as launches of k fused steps
             k = s["ca_fuse"]
-            chunks = [k] * (total // k) + ([total % k] if total % k else [])
+            chunks = balanced_chunks(total, k)
             pos = [0]
 
             def launch():

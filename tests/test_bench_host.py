@@ -78,3 +78,13 @@ def test_recorded_traffic_needs_the_current_digest():
     import bench
     # the committed record names a kernel; an unknown key or unit gives None
     assert bench.recorded_traffic("no_such_kernel", "sg_write_u8.cu") is None
+
+
+def test_balanced_chunks_cover_the_sequence_evenly():
+    assert bench.balanced_chunks(100, 8) == [8] * 9 + [7] * 4
+    assert bench.balanced_chunks(256, 16) == [16] * 16
+    for total in range(1, 300):
+        for k in (1, 2, 3, 4, 8, 16):
+            c = bench.balanced_chunks(total, k)
+            assert sum(c) == total and max(c) <= k and len(c) == -(-total // k)
+            assert max(c) - min(c) <= 1
