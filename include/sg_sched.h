@@ -10,10 +10,12 @@
  *
  *   - a FIFO of requests per gasket, each asking for k CA steps;
  *   - one iteration (sg_sched_step): every resident gasket with a queued
- *     request advances by the largest power of two <= min(fuse, steps left in
- *     its head request); gaskets with equal advances share one batched
- *     launch, so a gasket never steps past a request and every result is the
- *     plain per-gasket step sequence in the order its requests were queued;
+ *     request advances by min(fuse, steps left in its head request), so a
+ *     gasket never steps past a request and every result is the plain
+ *     per-gasket step sequence in the order its requests were queued.  One
+ *     batched launch serves each class of advances that share a halo size:
+ *     1 step, 2..4, 5..8 and 9..16 (each gasket runs its own step count
+ *     within its launch: sg_batch_ca_plan_host with steps);
  *   - the work lists of an iteration are written into page-locked host memory
  *     and reach the device in one asynchronous copy, so an iteration does not
  *     wait for the previous one: the host may prepare iteration i + 1 while
@@ -50,11 +52,18 @@ typedef struct sg_sched sg_sched;  /* opaque */
  * for an asynchronous copy) and *plan describes it as if it were already in
  * `workspace` (device memory of workspace_bytes bytes, 16-byte aligned).  The
  * caller copies the image to the workspace before launching the plan.
- * Arguments and errors as sg_batch_ca_plan.  Host-only.
+ *
+ * steps (host array, or NULL) gives every gasket its own step count, 1 ..
+ * SG_FUSE_MAX: a launch of the plan with sg_batch_ca_steps(plan, parity, k)
+ * then advances gasket i by steps[i] (the halo is sized for k), and requires
+ * k >= every steps[i]; the largest is recorded in plan->reserved[0].  Such a
+ * plan cannot be captured into a graph, and sg_batch_ca_step (one step) takes
+ * it only when every steps[i] is 1.  NULL: every gasket takes the launch's k.
+ * Other arguments and errors as sg_batch_ca_plan.  Host-only.
  */
-SG_API sg_status sg_batch_ca_plan_host(int count, const int *levels, uint8_t *const *buf_a,
-                                       uint8_t *const *buf_b, int rho, void *host_image,
-                                       uint64_t image_bytes, void *workspace,
+SG_API sg_status sg_batch_ca_plan_host(int count, const int *levels, const int *steps,
+                                       uint8_t *const *buf_a, uint8_t *const *buf_b, int rho,
+                                       void *host_image, uint64_t image_bytes, void *workspace,
                                        uint64_t workspace_bytes, sg_batch_plan *plan);
 
 /*

@@ -194,7 +194,7 @@ def lib() -> ctypes.CDLL:
         L.sg_abi_version.argtypes = []
         L.sg_abi_version.restype = i32
         # the serving scheduler's core (include/sg_sched.h)
-        L.sg_batch_ca_plan_host.argtypes = [i32, vp, vp, vp, i32, vp, u64, vp, u64, p_plan]
+        L.sg_batch_ca_plan_host.argtypes = [i32, vp, vp, vp, vp, i32, vp, u64, vp, u64, p_plan]
         L.sg_batch_ca_plan_host.restype = i32
         L.sg_sched_create.argtypes = [i32, vp, i32, i32, p_opts, ctypes.POINTER(vp)]
         L.sg_sched_create.restype = i32

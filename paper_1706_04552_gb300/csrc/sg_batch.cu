@@ -12,7 +12,8 @@
 //
 // Workspace (caller-owned device memory, sg_batch_workspace_bytes(count)):
 //   uint32 prefix[count + 1]   first work item of gasket i (prefix[count] = total)
-//   int32  level[count]
+//   int32  level[count]      bits 0..7 the level; bits 8..15 the gasket's own
+//                            step count in a fused launch (0: the launch's k)
 //   uint64 buf_a[count], buf_b[count]   state buffers (parity 0 reads a, writes b)
 #include <algorithm>
 #include <cstdio>
@@ -99,7 +100,7 @@ ca_batch_kernel(BatchView bv, uint32_t total, int parity, int order)
             StencilTile<uint8_t> tl{kNoTile, kNoTile, 0, nullptr, nullptr};
             if (q < total) {                                  // warp-uniform
                 const uint32_t i = batch_instance(bv.prefix, bv.count, q);
-                const int r = __ldg(bv.level + i);
+                const int r = __ldg(bv.level + i) & 0xFF;
                 const int rb = r - S;
                 const uint32_t local = q - __ldg(bv.prefix + i);
                 ll.set_level(lane, rb);
@@ -135,7 +136,7 @@ ca_batch_warp_kernel(BatchView bv, uint32_t total, int parity, int order)
     const uint64_t stride = (uint64_t)gridDim.x * kWarpTileWarps;
     for (uint64_t q = (uint64_t)blockIdx.x * kWarpTileWarps + warp; q < total; q += stride) {
         const uint32_t i = batch_instance(bv.prefix, bv.count, (uint32_t)q);   // warp-uniform
-        const int r = __ldg(bv.level + i), rb = r - S;
+        const int r = __ldg(bv.level + i) & 0xFF, rb = r - S;
         const uint32_t local = (uint32_t)q - __ldg(bv.prefix + i);
         ll.set_level(lane, rb);
         const uint32_t W = pi_word(order, rb);
@@ -204,7 +205,9 @@ ca_batch_bits_kernel(BatchView bv, uint32_t total, int parity, int order, int k)
     const uint64_t stride = (uint64_t)gridDim.x * B::WARPS;
     for (uint64_t q = (uint64_t)blockIdx.x * B::WARPS + warp; q < total; q += stride) {
         const uint32_t i = batch_instance(bv.prefix, bv.count, (uint32_t)q);   // warp-uniform
-        const int r = __ldg(bv.level + i), rb = r - S;
+        const int lv = __ldg(bv.level + i);
+        const int r = lv & 0xFF, rb = r - S;
+        const int kk = (lv >> 8) ? (lv >> 8) : k;            // the gasket's own steps, <= KH
         const uint32_t local = (uint32_t)q - __ldg(bv.prefix + i);
         ll.set_level(lane, rb);
         const uint32_t W = pi_word(order, rb);
@@ -213,7 +216,7 @@ ca_batch_bits_kernel(BatchView bv, uint32_t total, int parity, int order, int k)
         const uint64_t pa = __ldg(bv.buf_a + i), pb = __ldg(bv.buf_b + i);
         bits_tile_steps<S, KH>(st0, st1, mk, reinterpret_cast<const uint8_t *>(parity ? pb : pa),
                                reinterpret_cast<uint8_t *>(parity ? pa : pb), r,
-                               (int)(c.x << S), (int)(c.y << S), k, lane);
+                               (int)(c.x << S), (int)(c.y << S), kk, lane);
     }
 }
 
@@ -257,7 +260,8 @@ cudaError_t launch_batch_k(const sg_batch_plan *p, int parity, int k, cudaStream
 bool plan_ok(const sg_batch_plan *p)
 {
     return p != nullptr && p->workspace != nullptr && p->count >= 1 && p->count <= kMaxBatch &&
-           (p->rho == 16 || p->rho == 32 || p->rho == 64) && p->total_tiles > 0;
+           (p->rho == 16 || p->rho == 32 || p->rho == 64) && p->total_tiles > 0 &&
+           p->reserved[0] >= 0 && p->reserved[0] <= SG_FUSE_MAX;
 }
 
 sg_status cuda_fail(cudaError_t e) { return set_last_cuda_error(e); }
@@ -280,10 +284,10 @@ uint64_t sg_batch_workspace_bytes(int count)
     return ws_layout(count).total;
 }
 
-sg_status sg_batch_ca_plan_host(int count, const int *levels, uint8_t *const *buf_a,
-                                uint8_t *const *buf_b, int rho, void *host_image,
-                                uint64_t image_bytes, void *workspace, uint64_t workspace_bytes,
-                                sg_batch_plan *plan)
+sg_status sg_batch_ca_plan_host(int count, const int *levels, const int *steps,
+                                uint8_t *const *buf_a, uint8_t *const *buf_b, int rho,
+                                void *host_image, uint64_t image_bytes, void *workspace,
+                                uint64_t workspace_bytes, sg_batch_plan *plan)
 {
     if (plan == nullptr || levels == nullptr || buf_a == nullptr || buf_b == nullptr ||
         host_image == nullptr)
@@ -297,14 +301,16 @@ sg_status sg_batch_ca_plan_host(int count, const int *levels, uint8_t *const *bu
     while ((1 << s) < rho) ++s;
     // validate everything before the image is touched
     uint64_t total = 0;
-    int max_level = 0;
+    int max_level = 0, max_steps = 0;
     for (int i = 0; i < count; ++i) {
         const int r = levels[i];
         if (r < s || r > 16) return SG_EINVAL;        // every gasket holds whole tiles
+        if (steps != nullptr && (steps[i] < 1 || steps[i] > SG_FUSE_MAX)) return SG_EINVAL;
         if (buf_a[i] == nullptr || buf_b[i] == nullptr || buf_a[i] == buf_b[i]) return SG_EINVAL;
         if (((uintptr_t)buf_a[i] & 15) || ((uintptr_t)buf_b[i] & 15)) return SG_EINVAL;
         total += (uint64_t)pow3i(r - s);
         max_level = std::max(max_level, r);
+        if (steps != nullptr) max_steps = std::max(max_steps, steps[i]);
         if (total >= (1ull << 32)) return SG_EINVAL;
     }
     unsigned char *img = static_cast<unsigned char *>(host_image);
@@ -318,7 +324,10 @@ sg_status sg_batch_ca_plan_host(int count, const int *levels, uint8_t *const *bu
         std::memcpy(img + L.b + 8ull * i, &pb, 8);
     }
     std::memcpy(img + L.prefix + 4ull * count, &run, 4);
-    std::memcpy(img + L.level, levels, 4ull * count);
+    for (int i = 0; i < count; ++i) {
+        const int32_t lv = levels[i] | (steps != nullptr ? steps[i] << 8 : 0);
+        std::memcpy(img + L.level + 4ull * i, &lv, 4);
+    }
     *plan = sg_batch_plan{};
     plan->workspace = workspace;
     plan->workspace_bytes = workspace_bytes;
@@ -326,6 +335,7 @@ sg_status sg_batch_ca_plan_host(int count, const int *levels, uint8_t *const *bu
     plan->rho = rho;
     plan->total_tiles = (uint32_t)total;
     plan->max_level = (uint32_t)max_level;
+    plan->reserved[0] = max_steps;                    // launches need k >= every gasket's steps
     return SG_OK;
 }
 
@@ -339,8 +349,9 @@ sg_status sg_batch_ca_plan(int count, const int *levels, uint8_t *const *buf_a,
     const WsLayout L = ws_layout(count);
     std::vector<unsigned char> img(L.total);
     sg_batch_plan p;
-    const sg_status st = sg_batch_ca_plan_host(count, levels, buf_a, buf_b, rho, img.data(),
-                                               L.total, workspace, workspace_bytes, &p);
+    const sg_status st = sg_batch_ca_plan_host(count, levels, nullptr, buf_a, buf_b, rho,
+                                               img.data(), L.total, workspace, workspace_bytes,
+                                               &p);
     if (st != SG_OK) return st;
     cudaError_t e = cudaMemcpyAsync(workspace, img.data(), L.total, cudaMemcpyHostToDevice,
                                     (cudaStream_t)stream);
@@ -352,7 +363,7 @@ sg_status sg_batch_ca_plan(int count, const int *levels, uint8_t *const *buf_a,
 sg_status sg_batch_ca_step(const sg_batch_plan *plan, int parity, const sg_launch_opts *opts,
                            void *stream)
 {
-    if (!plan_ok(plan) || (parity != 0 && parity != 1)) return SG_EINVAL;
+    if (!plan_ok(plan) || (parity != 0 && parity != 1) || plan->reserved[0] > 1) return SG_EINVAL;
     LaunchCfg cfg;
     if (!read_launch_opts(opts, &cfg)) return SG_EINVAL;
     const cudaError_t e = launch_batch(plan, parity, (cudaStream_t)stream, cfg);
@@ -370,7 +381,8 @@ sg_status capture_batch(const sg_batch_plan *plan, int steps, int k, int start_p
                         const sg_launch_opts *opts, void **graph)
 {
     if (!plan_ok(plan) || graph == nullptr || steps < 1 || steps > 1000000 ||
-        k < 1 || k > SG_FUSE_MAX || (start_parity != 0 && start_parity != 1))
+        k < 1 || k > SG_FUSE_MAX || (start_parity != 0 && start_parity != 1) ||
+        plan->reserved[0] != 0)                       // per-gasket step counts: not captured
         return SG_EINVAL;
     LaunchCfg cfg;
     if (!read_launch_opts(opts, &cfg)) return SG_EINVAL;
@@ -422,7 +434,8 @@ sg_status sg_batch_ca_graph_create_fused(const sg_batch_plan *plan, int steps, i
 sg_status sg_batch_ca_steps(const sg_batch_plan *plan, int parity, int k,
                             const sg_launch_opts *opts, void *stream)
 {
-    if (!plan_ok(plan) || (parity != 0 && parity != 1) || k < 1 || k > SG_FUSE_MAX)
+    if (!plan_ok(plan) || (parity != 0 && parity != 1) || k < 1 || k > SG_FUSE_MAX ||
+        plan->reserved[0] > k || (k == 1 && plan->reserved[0] > 1))
         return SG_EINVAL;
     LaunchCfg cfg;
     if (!read_launch_opts(opts, &cfg)) return SG_EINVAL;

@@ -2,8 +2,9 @@
 //
 // Host code only: the kernels are the batch steps of sg_batch.cu, called
 // through the public C ABI (sg_batch_ca_plan_host, sg_batch_ca_steps).  An
-// iteration walks the gaskets that hold requests, groups the resident ones by
-// how many steps they advance (1, 2, 4, ... up to fuse), writes every group's
+// iteration walks the gaskets that hold requests, advances each resident one
+// by min(fuse, steps left in its head request), groups them by the halo that
+// advance needs (1 step; 2..4; 5..8; 9..16), writes every group's
 // work list into one page-locked image, copies it to the device in one
 // asynchronous copy and issues one batched launch per group.  The host-side
 // state (queues, which buffer is current) is updated as the work is
@@ -63,7 +64,7 @@ struct sg_sched {
     bool have_opts = false;
     std::vector<Gasket> g;
     std::vector<int32_t> pending;                  // gaskets with queued requests
-    std::vector<int> ks;                           // launch groups: 1, 2, 4, ... <= fuse
+    int classes = 1;                               // halo classes in use (by fuse)
     uint64_t slot_bytes = 0;
     unsigned char *img[kSlots] = {nullptr, nullptr};   // page-locked images
     void *dev[kSlots] = {nullptr, nullptr};            // device work lists
@@ -76,7 +77,8 @@ struct sg_sched {
     std::vector<std::vector<int32_t>> members;
     std::vector<sg_batch_plan> plans;
     std::vector<sg_status> planned;
-    std::vector<int> lv;
+    std::vector<int> lv, kk;
+    std::vector<int> adv;                          // per gasket: this iteration's advance
     std::vector<uint8_t *> pa, pb;
 };
 
@@ -97,14 +99,11 @@ void free_sched(sg_sched *s)
     delete s;
 }
 
-// Largest launch group not above `left` (ks ascending, ks[0] = 1).
-int advance_for(const std::vector<int> &ks, int left)
-{
-    int k = 1;
-    for (int v : ks)
-        if (v <= left) k = v;
-    return k;
-}
+// The launch class of an advance of k steps: the halo its fused launch
+// stages (sg_batch_ca_steps sizes it from the launch's k) -- 1 step (the
+// single-step kernel), 2..4, 5..8, 9..16.
+constexpr int kClasses = 4;
+int class_of(int k) { return k <= 1 ? 0 : k <= 4 ? 1 : k <= 8 ? 2 : 3; }
 
 }  // namespace
 
@@ -138,13 +137,14 @@ sg_status sg_sched_create(int count, const int *levels, int rho, int fuse,
         S->g[i].level = levels[i];
         S->g[i].cells = pow3(levels[i]);
     }
-    for (int k = 1; k <= fuse; k <<= 1) S->ks.push_back(k);
-    S->members.resize(S->ks.size());
-    S->plans.resize(S->ks.size());
-    S->planned.resize(S->ks.size());
+    S->classes = class_of(fuse) + 1;
+    S->members.resize(kClasses);
+    S->plans.resize(kClasses);
+    S->planned.resize(kClasses);
+    S->adv.assign(count, 0);
     // every group's work list at a 16-byte boundary: the whole batch's
     // layout plus 64 bytes of slack for each group's own layout and alignment
-    S->slot_bytes = up16(sg_batch_workspace_bytes(count) + 64ull * S->ks.size() + 64);
+    S->slot_bytes = up16(sg_batch_workspace_bytes(count) + 64ull * kClasses + 64);
     cudaError_t e = cudaSuccess;
     for (int j = 0; j < kSlots && e == cudaSuccess; ++j) {
         e = cudaHostAlloc(reinterpret_cast<void **>(&S->img[j]), S->slot_bytes,
@@ -275,15 +275,15 @@ sg_status sg_sched_step(sg_sched *s, void *stream, sg_sched_result *res)
         return SG_EINVAL;
     cudaStream_t st = (cudaStream_t)stream;
 
-    // group the resident gaskets with requests by their advance
+    // the resident gaskets with requests: each advances by min(fuse, steps
+    // left in its head request), grouped by the halo class of that advance
     for (auto &m : s->members) m.clear();
     for (int32_t g : s->pending) {
         Gasket &G = s->g[g];
         if (G.cur == nullptr || G.queue.empty()) continue;
-        const int k = advance_for(s->ks, G.queue.front().left);
-        int slot = 0;
-        while (s->ks[slot] != k) ++slot;
-        s->members[slot].push_back(g);
+        const int k = std::min(s->fuse, G.queue.front().left);
+        s->adv[g] = k;
+        s->members[class_of(k)].push_back(g);
     }
 
     // the image slot: wait for the copy that last read it
@@ -298,24 +298,29 @@ sg_status sg_sched_step(sg_sched *s, void *stream, sg_sched_result *res)
     auto &planned = s->planned;
     std::fill(planned.begin(), planned.end(), SG_EINVAL);
     uint64_t off = 0;
-    for (size_t gi = 0; gi < s->ks.size(); ++gi) {
+    int launch_k[kClasses] = {1, 1, 1, 1};
+    for (int gi = 0; gi < s->classes; ++gi) {
         const auto &m = s->members[gi];
         if (m.empty()) continue;
         const int cnt = (int)m.size();
         s->lv.resize(cnt);
+        s->kk.resize(cnt);
         s->pa.resize(cnt);
         s->pb.resize(cnt);
         for (int i = 0; i < cnt; ++i) {
             const Gasket &G = s->g[m[i]];
             s->lv[i] = G.level;
+            s->kk[i] = s->adv[m[i]];
+            launch_k[gi] = std::max(launch_k[gi], s->kk[i]);
             s->pa[i] = G.cur;
             s->pb[i] = G.nxt;
         }
         const uint64_t need = sg_batch_workspace_bytes(cnt);
-        planned[gi] = sg_batch_ca_plan_host(cnt, s->lv.data(), s->pa.data(), s->pb.data(), s->rho,
-                                            s->img[j] + off, need,
-                                            static_cast<unsigned char *>(s->dev[j]) + off, need,
-                                            &plans[gi]);
+        // single steps need no per-gasket counts; the fused classes carry them
+        planned[gi] = sg_batch_ca_plan_host(cnt, s->lv.data(), gi == 0 ? nullptr : s->kk.data(),
+                                            s->pa.data(), s->pb.data(), s->rho, s->img[j] + off,
+                                            need, static_cast<unsigned char *>(s->dev[j]) + off,
+                                            need, &plans[gi]);
         if (planned[gi] == SG_OK) off = up16(off + need);
     }
     if (off > 0) {
@@ -328,10 +333,10 @@ sg_status sg_sched_step(sg_sched *s, void *stream, sg_sched_result *res)
 
     // one launch per group; the host state follows the enqueued work
     const sg_launch_opts *opts = s->have_opts ? &s->opts : nullptr;
-    for (size_t gi = 0; gi < s->ks.size(); ++gi) {
+    for (int gi = 0; gi < s->classes; ++gi) {
         const auto &m = s->members[gi];
         if (m.empty()) continue;
-        const int k = s->ks[gi];
+        const int k = launch_k[gi];
         sg_status st_launch = planned[gi];
         bool injected = false;
         for (int32_t g : m)
@@ -357,10 +362,11 @@ sg_status sg_sched_step(sg_sched *s, void *stream, sg_sched_result *res)
                 G.queue.pop_front();
                 continue;
             }
+            const int a = s->adv[g];             // this gasket's own advance (<= k)
             std::swap(G.cur, G.nxt);
-            G.steps_done += (uint64_t)k;
-            res->cell_steps += G.cells * (uint64_t)k;
-            h.left -= k;
+            G.steps_done += (uint64_t)a;
+            res->cell_steps += G.cells * (uint64_t)a;
+            h.left -= a;
             if (h.left == 0) {
                 res->completed[res->n_completed] = h.id;
                 res->completed_gasket[res->n_completed] = g;

@@ -28,7 +28,11 @@ active gasket per iteration instead of the batched launch, for comparison.
 Two engines run the batched mode.  engine="native" hands the queues and the
 iteration to the C++ core (include/sg_sched.h): Python admits arrivals in
 slices, keeps residency (loads and evictions) and stamps completions, and
-each iteration's grouping, work lists and launches are built natively.  Its
+each iteration's grouping, work lists and launches are built natively.  The
+core advances a gasket by min(fuse, steps left in its head request) in one
+launch rather than by a power of two: gaskets whose advances stage the same
+halo (1 step; 2..4; 5..8; 9..16) share a launch, each running its own count,
+so a request of 7 steps takes one launch instead of three.  Its
 work lists reach the device by an asynchronous copy from page-locked memory,
 so up to `pipeline` iterations are in flight: the host prepares the next one
 while the device runs the current one, and a request's completion is stamped

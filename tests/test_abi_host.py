@@ -352,21 +352,45 @@ def test_batch_plan_host_writes_the_work_list(L):
     pa = (ctypes.c_void_p * n)(0x1000, 0x2000, 0x3000)
     pb = (ctypes.c_void_p * n)(0x1100, 0x2100, 0x3100)
     plan = sg.BatchPlan()
-    st = L.sg_batch_ca_plan_host(n, lv, pa, pb, rho, img, nbytes, 0x10000, nbytes,
+    st = L.sg_batch_ca_plan_host(n, lv, None, pa, pb, rho, img, nbytes, 0x10000, nbytes,
                                  ctypes.byref(plan))
     assert st == sg.SG_OK
     assert plan.count == n and plan.rho == rho and plan.max_level == 8
+    assert plan.reserved[0] == 0                       # no per-gasket step counts
     tiles = [3 ** (r - s) for r in levels]
     assert plan.total_tiles == sum(tiles)
     raw = bytes(img)
     prefix = np.frombuffer(raw[:4 * (n + 1)], dtype=np.uint32)
     assert list(prefix) == [0, tiles[0], tiles[0] + tiles[1], sum(tiles)]
     # the image is too small, a pointer is unaligned, a level is below the tile
-    assert L.sg_batch_ca_plan_host(n, lv, pa, pb, rho, img, nbytes - 16, 0x10000, nbytes,
+    assert L.sg_batch_ca_plan_host(n, lv, None, pa, pb, rho, img, nbytes - 16, 0x10000, nbytes,
                                    ctypes.byref(plan)) == sg.SG_EINVAL
     bad = (ctypes.c_void_p * n)(0x1000, 0x2008, 0x3000)
-    assert L.sg_batch_ca_plan_host(n, lv, bad, pb, rho, img, nbytes, 0x10000, nbytes,
+    assert L.sg_batch_ca_plan_host(n, lv, None, bad, pb, rho, img, nbytes, 0x10000, nbytes,
                                    ctypes.byref(plan)) == sg.SG_EINVAL
     low = (ctypes.c_int * n)(4, 6, 8)
-    assert L.sg_batch_ca_plan_host(n, low, pa, pb, rho, img, nbytes, 0x10000, nbytes,
+    assert L.sg_batch_ca_plan_host(n, low, None, pa, pb, rho, img, nbytes, 0x10000, nbytes,
                                    ctypes.byref(plan)) == sg.SG_EINVAL
+    # per-gasket step counts: level in bits 0..7, steps in bits 8..15, the
+    # largest in the plan; out-of-range counts are refused
+    steps = (ctypes.c_int * n)(3, 8, 1)
+    assert L.sg_batch_ca_plan_host(n, lv, steps, pa, pb, rho, img, nbytes, 0x10000, nbytes,
+                                   ctypes.byref(plan)) == sg.SG_OK
+    assert plan.reserved[0] == 8
+    lvl_off = 4 * (n + 1)
+    lvl_off = (lvl_off + 15) // 16 * 16
+    words = np.frombuffer(bytes(img)[lvl_off:lvl_off + 4 * n], dtype=np.int32)
+    assert list(words) == [r | (k << 8) for r, k in zip(levels, (3, 8, 1))]
+    for badk in (0, 17):
+        steps[1] = badk
+        assert L.sg_batch_ca_plan_host(n, lv, steps, pa, pb, rho, img, nbytes, 0x10000, nbytes,
+                                       ctypes.byref(plan)) == sg.SG_EINVAL
+    # a launch needs k >= every gasket's count (checked before any CUDA call)
+    steps[1] = 8
+    L.sg_batch_ca_plan_host(n, lv, steps, pa, pb, rho, img, nbytes, 0x10000, nbytes,
+                            ctypes.byref(plan))
+    assert L.sg_batch_ca_steps(ctypes.byref(plan), 0, 4, None, None) == sg.SG_EINVAL
+    assert L.sg_batch_ca_step(ctypes.byref(plan), 0, None, None) == sg.SG_EINVAL
+    g = ctypes.c_void_p()
+    assert L.sg_batch_ca_graph_create_fused(ctypes.byref(plan), 16, 8, 0, None,
+                                            ctypes.byref(g)) == sg.SG_EINVAL
