@@ -799,7 +799,7 @@ def write_sweep(args):
 
 
 SATURATION_RATES = (2000.0, 5000.0, 10000.0, 20000.0, 40000.0, 80000.0, 160000.0, 320000.0,
-                    640000.0, 1280000.0)
+                    640000.0, 1280000.0, 2560000.0)
 SATURATION_P99_MS = 5.0
 
 
@@ -809,7 +809,7 @@ def serving_workload():
     modes: batched launches of one step and of up to 16 fused steps on the
     native scheduler core, the fused batches again with the scheduler in
     Python, and one launch per active gasket.  Each mode serves the configured
-    2000 req/s for 2 s and then traces of 5000 to 1280000 req/s (4000 requests
+    2000 req/s for 2 s and then traces of 5000 to 2560000 req/s (4000 requests
     or 0.25 s, whichever is longer), stopping after the first rate it does not
     sustain.  A mode sustains an offered rate when it serves the trace at
     >= 95 % of the trace's own arrival rate, with p99 latency <= 5 ms and no

@@ -74,7 +74,7 @@ class ServeConfig:
     budget_bytes: int = 40 << 30      # device bytes for resident gasket states
     seed: int = 3
     ca_p: float = 0.3
-    rho: int = 32
+    rho: int = 64
     mode: str = "batched"             # or "per_gasket"
     fuse: int = 1                     # most steps one iteration advances a gasket (batched)
     engine: str = "native"            # batched mode: "native" (sg_sched) or "python"
