@@ -77,11 +77,13 @@ def parse_args():
                         "as 100 sub-averages of 10 consecutive calls; prints one JSON line")
     p.add_argument("--workload", choices=("write", "ca", "diffusion", "ca_fused",
                                           "diffusion_fused", "ca_compact",
-                                          "diffusion_compact", "ca_compact_fused"),
+                                          "diffusion_compact", "ca_compact_fused",
+                                          "batch_ca_fused"),
                    default="write",
                    help="with --quick: time the level-15 CA or diffusion step (or its "
-                        "fused form, k steps per launch) instead of the write pass (the "
-                        "form used to profile those kernels)")
+                        "fused form, k steps per launch), or the batch of 64 gaskets' "
+                        "16-step fused launch (batch_ca_fused), instead of the write pass "
+                        "(the form used to profile those kernels)")
     p.add_argument("--level", type=int, default=None,
                    help="with --quick: the gasket level (stencils: default 15; write: 16)")
     p.add_argument("--dtype", default="u8", choices=("u8", "f32"),
@@ -309,6 +311,8 @@ def run_ours(args, grp: Group):
 
 def run_ours_body(args, grp, sg, torch, dev, stream):
     from paper_1706_04552_gb300 import workloads
+    if args.quick and args.workload == "batch_ca_fused":
+        return run_batch_quick(args, sg, torch, dev, stream)
     if args.quick and args.workload != "write":
         return run_stencil_quick(args, sg, torch, dev, stream)
     w = dict(workloads.WRITE_HEADLINE)
@@ -451,6 +455,38 @@ def run_ours_body(args, grp, sg, torch, dev, stream):
     return out
 
 
+def run_batch_quick(args, sg, torch, dev, stream):
+    """K launches of 16 fused CA steps of the batch of 64 gaskets (levels
+    8..14, or 8..--level, rho 64, no autotuning), the batched serving
+    kernel; for ncu."""
+    from paper_1706_04552_gb300 import inputs, workloads
+    w = workloads.BATCH
+    hi = args.level if args.level else w["level_hi"]
+    levels = inputs.batch_levels(w["count"], w["level_lo"], hi, w["level_seed"])
+    a, b = [], []
+    for i, r in enumerate(levels):
+        idx, vals = inputs.ca_seed_sparse(r, w["ca_p"], inputs.instance_seed(w["ca_seed"], i))
+        t = torch.zeros(1 << (2 * r), dtype=torch.uint8, device=dev)
+        t[torch.from_numpy(idx).to(dev)] = torch.from_numpy(vals).to(dev)
+        a.append(t)
+        b.append(torch.zeros_like(t))
+    k = w["fuse"]
+    batch = sg.CABatch(levels, a, b, rho=64, stream=stream)
+    par = [0]
+
+    def step():
+        batch.steps(k, par[0], stream)
+        par[0] ^= 1
+    for _ in range(max(3, args.warmup)):
+        step()
+    total_ms, per = time_launches(step, args.steps, stream)
+    cells = sum(3 ** r for r in levels)
+    return {"workload": f"{args.workload}, {len(levels)} gaskets of levels "
+                        f"{w['level_lo']}..{hi}, rho 64, {k} steps per launch",
+            "unit": UNIT, "value": round(cells * k / (total_ms / args.steps / 1e3) / 1e9, 3),
+            "launch_ms_mean": round(statistics.mean(per), 5), "steps": args.steps}
+
+
 def run_stencil_quick(args, sg, torch, dev, stream):
     """K launches of the level-15 (or --level) CA or diffusion step, or of
     its fused form (k steps per launch), lambda map; for ncu."""
@@ -523,6 +559,7 @@ def batched_workload(sg, torch, dev, stream):
     opts = batch.opts
     order = "interleaved" if opts.order == 1 else "rowmajor"
     res = {"gaskets": len(levels), "levels": levels, "steps": steps,
+           "profile": "profiles/batch_ca_bits_l8to12_rho64_k16.md",
            "cells_per_step": sum(3 ** r for r in levels),
            "tuned": {"rho": batch.rho, "order": order, "ctas_per_sm": opts.ctas_per_sm}}
 
