@@ -47,3 +47,13 @@ def test_fused_launch_groups_never_cross_a_request():
                 left -= k
             assert sum(seen) == steps
             assert len(seen) <= steps // fuse + 5
+
+
+def test_default_config_fits_whole_tiles_and_the_budget():
+    # every gasket of the default mix holds whole rho-tiles (level >= log2 rho,
+    # as the batch calls require), and the preloaded states fit the budget
+    cfg = ServeConfig()
+    assert cfg.rho in (16, 32, 64) and cfg.level_min >= cfg.rho.bit_length() - 1
+    assert cfg.engine == "native" and cfg.pipeline >= 1 and 1 <= cfg.fuse <= 16
+    lv = gasket_levels(cfg)
+    assert int(np.sum(2 * 4 ** lv.astype(np.int64))) <= cfg.budget_bytes
