@@ -39,7 +39,11 @@ __host__ __device__ constexpr int pow3i(int k) { return k == 0 ? 1 : 3 * pow3i(k
 // The per-lane divisor 3^k (k <= 7) is replaced by a fixed-point reciprocal
 // m = ceil(2^32 / 3^k): for w < 3^8, floor(w * m / 2^32) is exactly
 // floor(w / 3^k) because w * (m * 3^k - 2^32) < 2^32.  For k = 0, m = 2^32
-// does not fit a word; that lane keeps m = 0 and adds w itself.
+// does not fit a word; that lane keeps m = 0 and adds w itself.  This is the
+// published method of division by an invariant integer through a multiply by
+// a rounded-up reciprocal (Granlund and Montgomery, "Division by Invariant
+// Integers using Multiplication", PLDI 1994); the inequality above is its
+// exactness condition for this dividend range, and the host tests check it.
 // ---------------------------------------------------------------------------
 enum : int { kOrderRowMajor = 0, kOrderInterleaved = 1 };
 
@@ -97,7 +101,9 @@ struct LambdaLane {
     {
         const uint32_t w = reads_b ? b : a;
         const uint32_t d = __umulhi(w, recip) + (w & keep_w);
-        const uint32_t beta = d - 3u * ((d * 0xAAABu) >> 17);   // d mod 3, d < 2^16
+        // d mod 3 for d < 2^16: 0xAAAB = ceil(2^17 / 3), the same
+        // rounded-up-reciprocal division (exact: d * (3 * 0xAAAB - 2^17) < 2^17)
+        const uint32_t beta = d - 3u * ((d * 0xAAABu) >> 17);
         const uint32_t dx = beta >> 1, dy = beta - dx;
         const uint32_t tau = active ? ((dx << shift) | (dy << (shift + 16))) : 0u;
         const uint32_t sum = __reduce_add_sync(0xffffffffu, tau);
