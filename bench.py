@@ -78,11 +78,12 @@ def parse_args():
     p.add_argument("--workload", choices=("write", "ca", "diffusion", "ca_fused",
                                           "diffusion_fused", "ca_compact",
                                           "diffusion_compact", "ca_compact_fused",
-                                          "batch_ca_fused"),
+                                          "batch_ca_fused", "serve_fused"),
                    default="write",
                    help="with --quick: time the level-15 CA or diffusion step (or its "
                         "fused form, k steps per launch), or the batch of 64 gaskets' "
-                        "16-step fused launch (batch_ca_fused), instead of the write pass "
+                        "16-step fused launch (batch_ca_fused), or a saturated serving "
+                        "trace (serve_fused), instead of the write pass "
                         "(the form used to profile those kernels)")
     p.add_argument("--level", type=int, default=None,
                    help="with --quick: the gasket level (stencils: default 15; write: 16)")
@@ -313,6 +314,8 @@ def run_ours_body(args, grp, sg, torch, dev, stream):
     from paper_1706_04552_gb300 import workloads
     if args.quick and args.workload == "batch_ca_fused":
         return run_batch_quick(args, sg, torch, dev, stream)
+    if args.quick and args.workload == "serve_fused":
+        return run_serve_quick(args)
     if args.quick and args.workload != "write":
         return run_stencil_quick(args, sg, torch, dev, stream)
     w = dict(workloads.WRITE_HEADLINE)
@@ -485,6 +488,25 @@ def run_batch_quick(args, sg, torch, dev, stream):
                         f"{w['level_lo']}..{hi}, rho 64, {k} steps per launch",
             "unit": UNIT, "value": round(cells * k / (total_ms / args.steps / 1e3) / 1e9, 3),
             "launch_ms_mean": round(statistics.mean(per), 5), "steps": args.steps}
+
+
+def run_serve_quick(args):
+    """The serving configuration with fused batches on the native core: one
+    0.25 s trace at 160,000 req/s (--steps traces, after --warmup traces at
+    2000 req/s); for the launch list of a serving run."""
+    import dataclasses
+    from paper_1706_04552_gb300.serve import ServeConfig, Server, make_trace, summarize
+    base = ServeConfig(fuse=16)
+    server = Server(base)
+    warm = dataclasses.replace(base, rate=2000.0, duration=0.05)
+    for _ in range(max(1, args.warmup)):
+        server.run(make_trace(warm))
+    cfg = dataclasses.replace(base, rate=160000.0, duration=0.25)
+    out = []
+    for _ in range(max(1, args.steps)):
+        out.append(summarize(server.run(make_trace(cfg)), cfg))
+    return {"workload": "serve_fused, 500 gaskets, 160000 req/s for 0.25 s, native core",
+            "runs": out}
 
 
 def run_stencil_quick(args, sg, torch, dev, stream):
@@ -881,6 +903,7 @@ def serving_workload():
             best = rate
         sat["modes"][name] = {"max_sustained_rps": best, "points": rows}
         del server
+    sat["profile"] = "profiles/serving_fused_launches.md"
     out["saturation"] = sat
     return out
 
