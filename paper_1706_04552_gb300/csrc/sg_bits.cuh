@@ -124,11 +124,59 @@ __device__ __forceinline__ BitRow bit_row(const uint32_t *p)
 // (l + v + r) serves the rows above and below it, the 2-cell sum (l + r) the
 // row itself, so a row costs one full adder, one half adder and the merge:
 //   count = up3 + mid2 + dn3 = s0 + 2 s1 + 4 (t1 + t2).
+//
+// For 64-tiles (three words a row) each lane instead takes whole rows, a run
+// of about three: it loads a row's three words once, forms their neighbour
+// planes in registers (the row's outermost bits take a 0 neighbour, as the
+// light cone allows), and its loads fall on distinct banks (the lanes' rows
+// are three rows, nine words, apart).  The adder tree is the same.
+struct BitRow3 {
+    uint32_t s[3], c[3];    // 3-cell sums (l + v + r) of each word: sum and carry
+    uint32_t v[3], l[3], r[3];
+};
+__device__ __forceinline__ void bit_row3(const uint32_t *p, BitRow3 &o)
+{
+    const uint32_t v0 = p[0], v1 = p[1], v2 = p[2];
+    o.v[0] = v0; o.v[1] = v1; o.v[2] = v2;
+    o.l[0] = v0 << 1;
+    o.l[1] = __funnelshift_l(v0, v1, 1);
+    o.l[2] = __funnelshift_l(v1, v2, 1);
+    o.r[0] = __funnelshift_r(v0, v1, 1);
+    o.r[1] = __funnelshift_r(v1, v2, 1);
+    o.r[2] = v2 >> 1;
+#pragma unroll
+    for (int w = 0; w < 3; ++w) full_add(o.l[w], o.v[w], o.r[w], o.s[w], o.c[w]);
+}
+
 template <int S, int KH>
 __device__ __forceinline__ void bits_ca_step(const uint32_t *src, uint32_t *dst,
                                              const uint32_t *mask, int s, int lane)
 {
     using B = BitShape<S, KH>;
+    if constexpr (B::WPR == 3) {
+        const int rows = B::ROWS - 2 * s, run = (rows + 31) / 32;
+        const int first = s + lane * run;
+        const int last = min(first + run, B::ROWS - s);
+        if (first >= last) return;
+        BitRow3 u, m, d;
+        bit_row3(src + (first - 1) * 3, u);
+        bit_row3(src + first * 3, m);
+        for (int row = first; row < last; ++row) {
+            bit_row3(src + (row + 1) * 3, d);
+#pragma unroll
+            for (int w = 0; w < 3; ++w) {
+                const uint32_t ms2 = m.l[w] ^ m.r[w], mc2 = m.l[w] & m.r[w];
+                uint32_t s0, c1, t0, t1;
+                full_add(u.s[w], ms2, d.s[w], s0, c1);
+                full_add(u.c[w], mc2, d.c[w], t0, t1);
+                const uint32_t s1 = t0 ^ c1, t2 = t0 & c1;
+                dst[row * 3 + w] = (s0 | m.v[w]) & s1 & ~(t1 | t2) & mask[row * 3 + w];
+            }
+            u = m;
+            m = d;
+        }
+        return;
+    }
     constexpr int G = 32 / B::WPR;
     const int g = lane / B::WPR, w = lane - g * B::WPR;
     if (g >= G) return;                               // idle lanes (32 not a multiple of WPR)
